@@ -1,0 +1,171 @@
+/*
+ * libhatt — Hadamard-avoiding tensor-train recompression (HaTT) on one GB300.
+ *
+ * C ABI. Every pointer argument is either host memory (marked "host") or
+ * device memory of the current CUDA device (marked "device"). The caller owns
+ * all memory, inputs, outputs and workspace; the library never allocates
+ * device memory and never synchronizes the stream, except where a function
+ * says so. `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ * stream). Every entry point returns a tt_status; no entry point aborts,
+ * exits or traps.
+ *
+ * Tensor-train layout (Section 2.2, Eq. (2.1)-(2.2)): a TT of order d has cores
+ * T_k of shape r_k x n_k x r_{k+1} (0-based k), r_0 = r_d = 1, stored
+ * row-major (C order): entry (a, i, b) of core k is cores[k][(a*n_k + i)*r_{k+1} + b].
+ * With this layout the horizontal unfolding H(T_k) (r_k x n_k r_{k+1}) and the
+ * vertical unfolding V(T_k) (r_k n_k x r_{k+1}) of Section 2.1 are plain
+ * row-major views. The Hadamard product Y ⊙ Z is the TT whose cores are the
+ * partial Kronecker products Y_k ⊠ Z_k with combined rank index alpha*s + beta
+ * (Section 2.2); it is never formed by tt_hadamard_recompress.
+ */
+#ifndef HATT_H
+#define HATT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TT_OK = 0,
+  TT_ERR_SHAPE = 1,      /* orders/mode sizes disagree, r_0 != 1 or r_d != 1, aliasing */
+  TT_ERR_RANK = 2,       /* a rank or size above the supported bound (see TT_MAX_SMALL_RANK) */
+  TT_ERR_ARG = 3,        /* null pointer, negative option, unknown precision/variant */
+  TT_ERR_WORKSPACE = 4,  /* workspace smaller than the size reported by the *_plan call */
+  TT_ERR_CUDA = 5,       /* a CUDA launch or copy failed; cudaGetLastError() has been cleared */
+  TT_ERR_NONFINITE = 6   /* reserved: a non-finite input or result was detected */
+} tt_status;
+
+/* Largest sketch / output rank the small dense factorizations accept
+ * (Gram, Cholesky and symmetric eigen problems of size rank x rank held in
+ * shared memory of one thread block). */
+#define TT_MAX_SMALL_RANK 128
+
+/* One TT tensor. Every array is caller-owned.
+ *   d      order, d >= 1
+ *   n      host[d]    mode sizes n_k >= 1
+ *   r      host[d+1]  ranks; read for inputs, written for outputs
+ *   cores  host[d]    array of device pointers; core k holds r_k*n_k*r_{k+1} doubles */
+typedef struct {
+  int32_t d;
+  const int64_t *n;
+  int64_t *r;
+  double **cores;
+} tt_t;
+
+typedef enum {
+  TT_FP64 = 0            /* every step in IEEE binary64 */
+} tt_precision;
+
+/* Options of tt_hadamard_recompress (the problem statement of Algorithm 4:
+ * two TT tensors and target ranks; plus the truncation this library adds).
+ *   max_rank     cap on the output ranks; 0 = no cap beyond the sketch rank
+ *   tol          relative Frobenius tolerance of the final truncation sweep;
+ *                0 = no tolerance truncation. The sweep keeps, at each bond, the
+ *                smallest rank whose discarded tail sum sigma_i^2 <= delta^2,
+ *                delta = tol * ||X||_F / sqrt(d-1)
+ *   sketch_rank  l before clamping; 0 = max_rank + oversample if max_rank > 0,
+ *                else the PKP rank max_k r_k s_k (exact recompression)
+ *   oversample   used when sketch_rank = 0 (>= 0)
+ *   seed         Philox4x32-10 key of the Gaussian sketch TT
+ *   precision    a tt_precision
+ *   variant      1 = HaTT-1 (HPCRL-1 sketches, Eq. (3.6)) */
+typedef struct {
+  int64_t max_rank;
+  double tol;
+  int64_t sketch_rank;
+  int64_t oversample;
+  uint64_t seed;
+  int32_t precision;
+  int32_t variant;
+} tt_opts;
+
+/* Rank plan and workspace size of tt_hadamard_recompress.
+ * Sketch ranks are clamped (l_k = min(l_req, r_k s_k, n_0..n_{k-1}, n_k..n_{d-1}),
+ * then l_k <= l_{k-1} n_{k-1} and l_k <= n_k l_{k+1}) so that every economy
+ * QR of Algorithm 4 is well posed.
+ *   Y, Z              input TTs (only d, n, r are read; cores may be NULL)
+ *   out_rank_bound    host[d+1], written: the sketch ranks l_k, which bound the
+ *                     output ranks; output core k needs l_k*n_k*l_{k+1} doubles
+ *   workspace_bytes   host, written
+ * Synchronous, host only; launches nothing. */
+int tt_hadamard_recompress_plan(const tt_t *Y, const tt_t *Z, const tt_opts *opts,
+                                int64_t *out_rank_bound, size_t *workspace_bytes);
+
+/* Recompress the Hadamard product Y ⊙ Z (Algorithm 4 with HPCRL-1 of
+ * Algorithm 3 and Eq. (3.6); core update of Eq. (3.10)) without forming the
+ * rank-r_k s_k PKP cores:
+ *   1. Gaussian sketch TT R with the planned ranks (Definition 2.1), generated
+ *      on the device from a counter-based RNG;
+ *   2. right-to-left sketches W^{(k)} = H(A_{k:d}) H(R_{k:d})^T (Eq. (3.1))
+ *      computed from the Y, Z and R cores only, each scaled to unit norm;
+ *   3. left-to-right pass: QR of C_k W^{(k)} (diag(R) >= 0), M = Q^T C_k,
+ *      C_{k+1} = M x (Y_{k+1} ⊠ Z_{k+1}) evaluated core-wise (Eq. (3.8)-(3.10));
+ *   4. if tol > 0 or max_rank is below a sketch rank, a right-to-left
+ *      truncation sweep of the left-orthogonal result.
+ *   Y, Z       inputs (Y.d == Z.d, Y.n[k] == Z.n[k], r_0 = r_d = s_0 = s_d = 1)
+ *   X          output: X->d and X->n must match; X->cores[k] must hold at least
+ *              l_k*n_k*l_{k+1} doubles (the plan's bound). On return (stream
+ *              ordered) core k holds the r_k x n_k x r_{k+1} result densely in the
+ *              prefix of its buffer, and X->r (host[d+1]) receives the ranks
+ *              through a stream-ordered device-to-host copy: read X->r after the
+ *              stream has been synchronized (pinned host memory keeps the call
+ *              asynchronous; pageable memory makes the copy block).
+ *              Output buffers must not alias input cores (TT_ERR_SHAPE).
+ *   workspace  device, at least the plan's workspace_bytes, 256-byte aligned.
+ * Without truncation the result is left-orthogonal (cores 0..d-2 have
+ * orthonormal vertical unfoldings). */
+int tt_hadamard_recompress(const tt_t *Y, const tt_t *Z, const tt_opts *opts, tt_t *X,
+                           void *workspace, size_t workspace_bytes, void *stream);
+
+/* Workspace size of tt_round and its output rank bound (min(r_k, max_rank)
+ * clamped by the mode-size products), both host outputs. */
+int tt_round_plan(const tt_t *A, int64_t max_rank, double tol, int64_t *out_rank_bound,
+                  size_t *workspace_bytes);
+
+/* TT rounding of A (Algorithm 1, Oseledets): orthogonalization sweep with QR
+ * of each vertical unfolding (left to right), then a right-to-left truncation
+ * sweep with the same rule as tt_hadamard_recompress (max_rank cap, tol with
+ * delta = tol * ||A|| / sqrt(d-1)). B is written like X above; all ranks of A
+ * must be <= TT_MAX_SMALL_RANK. */
+int tt_round(const tt_t *A, int64_t max_rank, double tol, tt_t *B, void *workspace,
+             size_t workspace_bytes, void *stream);
+
+/* Workspace of tt_dot / tt_norm (host output). */
+int tt_dot_plan(const tt_t *A, const tt_t *B, size_t *workspace_bytes);
+
+/* Inner product <A, B> = sum over all entries of A * B, by the left-to-right
+ * contraction G_k = sum_i A_k(i)^T G_{k-1} B_k(i), G_0 = 1 (the TT inner product
+ * behind the relative errors of Section 5). out: device scalar (double). */
+int tt_dot(const tt_t *A, const tt_t *B, double *out, void *workspace, size_t workspace_bytes,
+           void *stream);
+
+/* Frobenius norm ||A||_F = sqrt(<A, A>); out: device scalar. Workspace as tt_dot(A, A). */
+int tt_norm(const tt_t *A, double *out, void *workspace, size_t workspace_bytes, void *stream);
+
+/* The Gaussian sketch TT of Definition 2.1 on the device: core k
+ * (ell[k] x n[k] x ell[k+1]) gets i.i.d. N(0, 1/(ell_k n_k ell_{k+1})) entries
+ * from Philox4x32-10 (key = seed, counter = (flat index, k, pair, 0)) and the
+ * Box-Muller transform of two 52-bit uniforms. This is the sketch
+ * tt_hadamard_recompress uses internally for the same seed.
+ *   n     host[d], ell host[d+1] with ell[0] = ell[d] = 1
+ *   cores host[d] array of device pointers (ell[k]*n[k]*ell[k+1] doubles each) */
+int tt_sketch_tt(int32_t d, const int64_t *n, const int64_t *ell, uint64_t seed, uint32_t pair,
+                 double **cores, void *stream);
+
+/* Raw Philox4x32-10 blocks (Salmon et al., SC'11): out[4j..4j+3] =
+ * Philox(counter = ctr[4j..4j+3], key = (key0, key1)) for j < count.
+ * ctr, out: device uint32 arrays of 4*count words. */
+int tt_philox4x32_10(const uint32_t *ctr, uint32_t key0, uint32_t key1, uint32_t *out,
+                     int64_t count, void *stream);
+
+/* Static description of a status code (never NULL). */
+const char *tt_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HATT_H */

@@ -1,0 +1,282 @@
+"""Thin ctypes binding of libhatt (include/hatt.h).
+
+Argument marshalling only: torch supplies device memory and the current CUDA
+stream; every arithmetic step runs in the library's CUDA kernels. The functions
+keep the C names. If the compiled library is missing this module raises at
+load time: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libhatt.so")
+
+TT_OK = 0
+TT_FP64 = 0
+TT_MAX_SMALL_RANK = 128
+
+
+class TTStruct(ctypes.Structure):
+    _fields_ = [
+        ("d", ctypes.c_int32),
+        ("n", ctypes.POINTER(ctypes.c_int64)),
+        ("r", ctypes.POINTER(ctypes.c_int64)),
+        ("cores", ctypes.POINTER(ctypes.c_void_p)),
+    ]
+
+
+class OptsStruct(ctypes.Structure):
+    _fields_ = [
+        ("max_rank", ctypes.c_int64),
+        ("tol", ctypes.c_double),
+        ("sketch_rank", ctypes.c_int64),
+        ("oversample", ctypes.c_int64),
+        ("seed", ctypes.c_uint64),
+        ("precision", ctypes.c_int32),
+        ("variant", ctypes.c_int32),
+    ]
+
+
+class HattError(RuntimeError):
+    def __init__(self, fn: str, status: int, msg: str):
+        super().__init__(f"{fn} failed: status {status} ({msg})")
+        self.status = status
+
+
+_lib = None
+
+EXPORTS = ("tt_hadamard_recompress_plan", "tt_hadamard_recompress", "tt_round_plan", "tt_round",
+           "tt_dot_plan", "tt_dot", "tt_norm", "tt_sketch_tt", "tt_philox4x32_10",
+           "tt_status_string")
+
+
+def load(path: Optional[str] = None):
+    """Load libhatt.so (once). Raises if it has not been built."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libhatt.so not found at {p}; build it with "
+                           "`python -m paper_2410_04385_gb300.build` (needs nvcc)")
+    lib = ctypes.CDLL(p)
+    P = ctypes.POINTER
+    vp = ctypes.c_void_p
+    lib.tt_status_string.restype = ctypes.c_char_p
+    lib.tt_status_string.argtypes = [ctypes.c_int]
+    lib.tt_hadamard_recompress_plan.argtypes = [P(TTStruct), P(TTStruct), P(OptsStruct),
+                                                P(ctypes.c_int64), P(ctypes.c_size_t)]
+    lib.tt_hadamard_recompress.argtypes = [P(TTStruct), P(TTStruct), P(OptsStruct), P(TTStruct),
+                                           vp, ctypes.c_size_t, vp]
+    lib.tt_round_plan.argtypes = [P(TTStruct), ctypes.c_int64, ctypes.c_double, P(ctypes.c_int64),
+                                  P(ctypes.c_size_t)]
+    lib.tt_round.argtypes = [P(TTStruct), ctypes.c_int64, ctypes.c_double, P(TTStruct), vp,
+                             ctypes.c_size_t, vp]
+    lib.tt_dot_plan.argtypes = [P(TTStruct), P(TTStruct), P(ctypes.c_size_t)]
+    lib.tt_dot.argtypes = [P(TTStruct), P(TTStruct), vp, vp, ctypes.c_size_t, vp]
+    lib.tt_norm.argtypes = [P(TTStruct), vp, vp, ctypes.c_size_t, vp]
+    lib.tt_sketch_tt.argtypes = [ctypes.c_int32, P(ctypes.c_int64), P(ctypes.c_int64),
+                                 ctypes.c_uint64, ctypes.c_uint32, P(ctypes.c_void_p), vp]
+    lib.tt_philox4x32_10.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint32, vp, ctypes.c_int64, vp]
+    for name in EXPORTS:
+        getattr(lib, name)
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    return load().tt_status_string(int(status)).decode()
+
+
+def _check(fn: str, status: int):
+    if status != TT_OK:
+        raise HattError(fn, status, status_string(status))
+
+
+def _stream_ptr(stream: Optional[torch.cuda.Stream]):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class TT:
+    """Host-side descriptor (tt_t) of a TT given as a list of CUDA float64 cores
+    of shapes (r_k, n_k, r_{k+1}), or of shapes only (cores=None)."""
+
+    def __init__(self, cores: Optional[Sequence[torch.Tensor]] = None, n=None, r=None):
+        if cores is not None:
+            for c in cores:
+                if c.dtype != torch.float64 or not c.is_cuda or not c.is_contiguous():
+                    raise ValueError("cores must be contiguous CUDA float64 tensors")
+            n = [int(c.shape[1]) for c in cores]
+            r = [int(cores[0].shape[0])] + [int(c.shape[2]) for c in cores]
+        self.d = len(n)
+        self.n_arr = (ctypes.c_int64 * self.d)(*n)
+        self.r_arr = (ctypes.c_int64 * (self.d + 1))(*r)
+        self.core_arr = (ctypes.c_void_p * self.d)()
+        self.cores = list(cores) if cores is not None else None
+        if cores is not None:
+            for k, c in enumerate(cores):
+                self.core_arr[k] = c.data_ptr()
+        self.s = TTStruct(self.d, self.n_arr, self.r_arr, self.core_arr)
+
+    def set_core_ptrs(self, ptrs):
+        for k, p in enumerate(ptrs):
+            self.core_arr[k] = p
+
+    @property
+    def n(self):
+        return [int(v) for v in self.n_arr]
+
+    @property
+    def r(self):
+        return [int(v) for v in self.r_arr]
+
+    def ref(self):
+        return ctypes.byref(self.s)
+
+
+def make_opts(max_rank=0, tol=0.0, sketch_rank=0, oversample=10, seed=0, precision=TT_FP64,
+              variant=1):
+    return OptsStruct(int(max_rank), float(tol), int(sketch_rank), int(oversample),
+                      int(seed) & 0xFFFFFFFFFFFFFFFF, int(precision), int(variant))
+
+
+class HadamardRecompressor:
+    """Plans once and owns the output buffers and workspace, so repeated calls
+    (benchmarks, time stepping) allocate nothing. `run` enqueues on `stream`."""
+
+    def __init__(self, Y: Sequence[torch.Tensor], Z: Sequence[torch.Tensor], **opts):
+        lib = load()
+        self.Yd = TT(Y)
+        self.Zd = TT(Z)
+        self.opts = make_opts(**opts)
+        d = self.Yd.d
+        self.bound = (ctypes.c_int64 * (d + 1))()
+        ws = ctypes.c_size_t()
+        _check("tt_hadamard_recompress_plan",
+               lib.tt_hadamard_recompress_plan(self.Yd.ref(), self.Zd.ref(), ctypes.byref(self.opts),
+                                               self.bound, ctypes.byref(ws)))
+        self.workspace_bytes = int(ws.value)
+        dev = Y[0].device
+        self.workspace = torch.empty(max(self.workspace_bytes, 1), dtype=torch.uint8, device=dev)
+        n = self.Yd.n
+        b = [int(v) for v in self.bound]
+        self.out_bufs = [torch.empty(b[k] * n[k] * b[k + 1], dtype=torch.float64, device=dev)
+                         for k in range(d)]
+        self.Xd = TT(n=n, r=b)
+        self.Xd.set_core_ptrs([t.data_ptr() for t in self.out_bufs])
+
+    def rebind(self, Y: Sequence[torch.Tensor], Z: Sequence[torch.Tensor]):
+        """Point at new input cores of the same shapes."""
+        self.Yd.set_core_ptrs([c.data_ptr() for c in Y])
+        self.Zd.set_core_ptrs([c.data_ptr() for c in Z])
+
+    def run(self, stream=None):
+        st = load().tt_hadamard_recompress(self.Yd.ref(), self.Zd.ref(), ctypes.byref(self.opts),
+                                           self.Xd.ref(), ctypes.c_void_p(self.workspace.data_ptr()),
+                                           self.workspace_bytes, _stream_ptr(stream))
+        _check("tt_hadamard_recompress", st)
+
+    def result(self) -> List[torch.Tensor]:
+        """Output cores as views (call after the stream has completed)."""
+        r = self.Xd.r
+        n = self.Xd.n
+        return [self.out_bufs[k][: r[k] * n[k] * r[k + 1]].view(r[k], n[k], r[k + 1])
+                for k in range(self.Xd.d)]
+
+
+def tt_hadamard_recompress(Y, Z, max_rank=0, tol=0.0, sketch_rank=0, oversample=10, seed=0,
+                           stream=None) -> List[torch.Tensor]:
+    """HaTT-1 recompression of Y ⊙ Z; returns the output cores (synchronizes)."""
+    h = HadamardRecompressor(Y, Z, max_rank=max_rank, tol=tol, sketch_rank=sketch_rank,
+                             oversample=oversample, seed=seed)
+    h.run(stream)
+    (stream or torch.cuda.current_stream()).synchronize()
+    return [c.clone() for c in h.result()]
+
+
+def tt_round(A, max_rank=0, tol=0.0, stream=None) -> List[torch.Tensor]:
+    lib = load()
+    Ad = TT(A)
+    d = Ad.d
+    bound = (ctypes.c_int64 * (d + 1))()
+    ws = ctypes.c_size_t()
+    _check("tt_round_plan", lib.tt_round_plan(Ad.ref(), int(max_rank), float(tol), bound,
+                                              ctypes.byref(ws)))
+    dev = A[0].device
+    work = torch.empty(max(int(ws.value), 1), dtype=torch.uint8, device=dev)
+    n = Ad.n
+    b = [int(v) for v in bound]
+    bufs = [torch.empty(b[k] * n[k] * b[k + 1], dtype=torch.float64, device=dev) for k in range(d)]
+    Bd = TT(n=n, r=b)
+    Bd.set_core_ptrs([t.data_ptr() for t in bufs])
+    _check("tt_round", lib.tt_round(Ad.ref(), int(max_rank), float(tol), Bd.ref(),
+                                    ctypes.c_void_p(work.data_ptr()), int(ws.value),
+                                    _stream_ptr(stream)))
+    (stream or torch.cuda.current_stream()).synchronize()
+    r = Bd.r
+    return [bufs[k][: r[k] * n[k] * r[k + 1]].view(r[k], n[k], r[k + 1]).clone() for k in range(d)]
+
+
+def _dot_common(fn, A, B, stream):
+    lib = load()
+    Ad = TT(A)
+    Bd = TT(B)
+    ws = ctypes.c_size_t()
+    _check("tt_dot_plan", lib.tt_dot_plan(Ad.ref(), Bd.ref(), ctypes.byref(ws)))
+    dev = A[0].device
+    work = torch.empty(max(int(ws.value), 1), dtype=torch.uint8, device=dev)
+    out = torch.empty(1, dtype=torch.float64, device=dev)
+    if fn == "tt_dot":
+        st = lib.tt_dot(Ad.ref(), Bd.ref(), ctypes.c_void_p(out.data_ptr()),
+                        ctypes.c_void_p(work.data_ptr()), int(ws.value), _stream_ptr(stream))
+    else:
+        st = lib.tt_norm(Ad.ref(), ctypes.c_void_p(out.data_ptr()),
+                         ctypes.c_void_p(work.data_ptr()), int(ws.value), _stream_ptr(stream))
+    _check(fn, st)
+    (stream or torch.cuda.current_stream()).synchronize()
+    return out
+
+
+def tt_dot(A, B, stream=None) -> torch.Tensor:
+    """<A, B> as a 1-element CUDA tensor."""
+    return _dot_common("tt_dot", A, B, stream)
+
+
+def tt_norm(A, stream=None) -> torch.Tensor:
+    """||A||_F as a 1-element CUDA tensor."""
+    return _dot_common("tt_norm", A, A, stream)
+
+
+def tt_sketch_tt(n, ell, seed=0, pair=0, device="cuda", stream=None) -> List[torch.Tensor]:
+    """Gaussian sketch TT of Definition 2.1, generated by the library."""
+    lib = load()
+    d = len(n)
+    cores = [torch.empty((int(ell[k]), int(n[k]), int(ell[k + 1])), dtype=torch.float64,
+                         device=device) for k in range(d)]
+    ptrs = (ctypes.c_void_p * d)(*[c.data_ptr() for c in cores])
+    _check("tt_sketch_tt", lib.tt_sketch_tt(d, (ctypes.c_int64 * d)(*n),
+                                            (ctypes.c_int64 * (d + 1))(*ell), int(seed),
+                                            int(pair), ptrs, _stream_ptr(stream)))
+    (stream or torch.cuda.current_stream()).synchronize()
+    return cores
+
+
+def tt_philox4x32_10(ctr: torch.Tensor, key0: int, key1: int, stream=None) -> torch.Tensor:
+    """Raw Philox4x32-10 blocks; ctr is an int32 CUDA tensor of shape (count, 4)
+    holding the counter words' bit patterns. Returns the same shape."""
+    if ctr.dtype != torch.int32 or ctr.dim() != 2 or ctr.shape[1] != 4 or not ctr.is_cuda:
+        raise ValueError("ctr must be an int32 CUDA tensor of shape (count, 4)")
+    ctr = ctr.contiguous()
+    out = torch.empty_like(ctr)
+    _check("tt_philox4x32_10", load().tt_philox4x32_10(
+        ctypes.c_void_p(ctr.data_ptr()), int(key0) & 0xFFFFFFFF, int(key1) & 0xFFFFFFFF,
+        ctypes.c_void_p(out.data_ptr()), int(ctr.shape[0]), _stream_ptr(stream)))
+    (stream or torch.cuda.current_stream()).synchronize()
+    return out

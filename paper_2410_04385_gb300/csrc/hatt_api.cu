@@ -1,0 +1,752 @@
+// C-ABI entry points of libhatt: argument checks, rank plans, workspace
+// layout and the launch sequences of HaTT-1 (Algorithms 3 and 4), TT rounding
+// (Algorithm 1) and the TT inner product.
+//
+// Every sequence is written once and run twice: a planning pass that only
+// measures buffers and scratch (no launches) and an execution pass that carves
+// the caller's workspace identically and enqueues the kernels on the caller's
+// stream. No device memory is allocated and the stream is never synchronized.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "hatt.h"
+#include "hatt_internal.cuh"
+
+using hatt::Gemm;
+typedef long long ll;
+
+namespace {
+
+// ---------------------------------------------------------------- helpers ---
+
+struct Ws {
+  bool exec = false;
+  char *base = nullptr;
+  size_t off = 0;
+  template <class T>
+  T *take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T *p = exec ? reinterpret_cast<T *>(base + off) : nullptr;
+    off += std::max<size_t>(count, 1) * sizeof(T);
+    return p;
+  }
+};
+
+// Runs a launch sequence in planning or execution mode.
+struct Runner {
+  bool exec = false;
+  cudaStream_t st = nullptr;
+  size_t scratch_need = 0;       // doubles
+  double *scratch = nullptr;
+  cudaError_t err = cudaSuccess;
+
+  bool live() const { return exec && err == cudaSuccess; }
+  void check(cudaError_t e) {
+    if (err == cudaSuccess && e != cudaSuccess) err = e;
+  }
+  void gemm(const Gemm &g) {
+    if (!exec) {
+      scratch_need = std::max(scratch_need, hatt::gemm_scratch_doubles(g));
+      return;
+    }
+    if (err == cudaSuccess) check(hatt::gemm_f64(g, scratch, st));
+  }
+  void qr(double *S, int m, int c, ll ld, int *flags) {
+    if (!exec) {
+      scratch_need = std::max(scratch_need, hatt::qr_scratch_doubles(m, c));
+      return;
+    }
+    if (err == cudaSuccess) check(hatt::qr_inplace(S, m, c, ld, scratch, flags, st));
+  }
+  void trunc(double *Xk, int la, int n, int lb, double *Xkm1, int lm, int nm, int cap,
+             const double *delta2, ll *ranks, int k) {
+    if (!exec) {
+      scratch_need = std::max(scratch_need, hatt::trunc_scratch_doubles(la, n, lb, lm, nm));
+      return;
+    }
+    if (err == cudaSuccess)
+      check(hatt::trunc_step(Xk, la, n, lb, Xkm1, lm, nm, cap, delta2, ranks, k, scratch, st));
+  }
+};
+
+int from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return TT_OK;
+  cudaGetLastError();   // clear a sticky launch error of this thread
+  return TT_ERR_CUDA;
+}
+
+bool overlap(const void *a, size_t na, const void *b, size_t nb) {
+  const char *pa = (const char *)a, *pb = (const char *)b;
+  return pa < pb + nb && pb < pa + na;
+}
+
+const ll kIntMax = (1LL << 31) - 1;
+
+// Basic structural checks of one TT descriptor (host arrays only).
+int check_tt(const tt_t *A, bool need_cores) {
+  if (!A || !A->n || !A->r) return TT_ERR_ARG;
+  if (A->d < 1) return TT_ERR_SHAPE;
+  if (A->d > hatt::kMaxOrder) return TT_ERR_RANK;
+  if (need_cores && !A->cores) return TT_ERR_ARG;
+  if (A->r[0] != 1 || A->r[A->d] != 1) return TT_ERR_SHAPE;
+  for (int k = 0; k < A->d; ++k) {
+    if (A->n[k] < 1 || A->r[k + 1] < 1) return TT_ERR_SHAPE;
+    if (A->n[k] > kIntMax || A->r[k + 1] > kIntMax) return TT_ERR_RANK;
+    if (need_cores && !A->cores[k]) return TT_ERR_ARG;
+    if ((double)A->r[k] * A->n[k] * A->r[k + 1] > 1e15) return TT_ERR_RANK;
+  }
+  return TT_OK;
+}
+
+// Rank clamps shared by HaTT and rounding: l_k = min(l_req, cap_k, products of
+// mode sizes on either side), then l_k <= l_{k-1} n_{k-1} and l_k <= n_k l_{k+1}.
+std::vector<ll> clamp_ranks(int d, const int64_t *n, const std::vector<ll> &cap, ll lreq) {
+  std::vector<ll> l(d + 1, 1);
+  const ll big = 1LL << 40;   // saturating products: any rank bound is far below this
+  auto smul = [big](ll a, ll b) { return (a > big / b) ? big : std::min(big, a * b); };
+  for (int k = 1; k < d; ++k) {
+    ll left = 1, right = 1;
+    for (int j = 0; j < k; ++j) left = smul(left, (ll)n[j]);
+    for (int j = k; j < d; ++j) right = smul(right, (ll)n[j]);
+    l[k] = std::min(std::min(lreq, cap[k]), std::min(left, right));
+  }
+  for (int k = 1; k < d; ++k) l[k] = std::min(l[k], smul(l[k - 1], (ll)n[k - 1]));
+  for (int k = d - 1; k >= 1; --k) l[k] = std::min(l[k], smul((ll)n[k], l[k + 1]));
+  return l;
+}
+
+// ------------------------------------------------------------ HaTT-1 run ---
+
+struct HattArgs {
+  int d;
+  const int64_t *n, *r, *s;
+  std::vector<ll> ell;
+  double *const *Y;
+  double *const *Z;
+  double *const *Xout;
+  bool trunc;
+  int cap;
+  double tol;
+  uint64_t seed;
+};
+
+struct HattBufs {
+  double *R, *W, *winv, *T1, *T2, *Ca, *Cb, *Mb, *U1, *Xpad, *partials, *delta2;
+  ll *ranks;
+  int *flags;
+  unsigned int *ticket;
+  std::vector<ll> Roff, Woff, Xoff;
+};
+
+HattBufs carve_hatt(Ws &ws, const HattArgs &a) {
+  HattBufs b;
+  const int d = a.d;
+  const auto &n = a.n;
+  const auto &r = a.r;
+  const auto &s = a.s;
+  const auto &l = a.ell;
+  b.Roff.assign(d + 1, 0);
+  b.Xoff.assign(d + 1, 0);
+  for (int k = 0; k < d; ++k) {
+    b.Roff[k + 1] = b.Roff[k] + l[k] * n[k] * l[k + 1];
+    b.Xoff[k + 1] = b.Xoff[k] + l[k] * n[k] * l[k + 1];
+  }
+  b.Woff.assign(d + 2, 0);   // W[k] for k = 1..d at Woff[k]
+  for (int k = 1; k <= d; ++k) b.Woff[k + 1] = b.Woff[k] + (ll)r[k] * s[k] * l[k];
+  ll t1 = 1, t2 = 1, cmax = 1, mmax = 1, umax = 1;
+  for (int k = 1; k < d; ++k) {
+    t1 = std::max(t1, (ll)n[k] * r[k + 1] * s[k + 1] * l[k]);
+    t2 = std::max(t2, (ll)n[k] * r[k + 1] * s[k] * l[k]);
+  }
+  for (int k = 0; k < d; ++k) cmax = std::max(cmax, l[k] * n[k] * (ll)r[k + 1] * s[k + 1]);
+  for (int k = 0; k + 1 < d; ++k) {
+    mmax = std::max(mmax, l[k + 1] * (ll)r[k + 1] * s[k + 1]);
+    umax = std::max(umax, l[k + 1] * (ll)r[k + 1] * n[k + 1] * s[k + 2]);
+  }
+  b.R = ws.take<double>(b.Roff[d]);
+  b.W = ws.take<double>(b.Woff[d + 1]);
+  b.winv = ws.take<double>(d + 2);
+  b.T1 = ws.take<double>(t1);
+  b.T2 = ws.take<double>(t2);
+  b.Ca = ws.take<double>(cmax);
+  b.Cb = ws.take<double>(cmax);
+  b.Mb = ws.take<double>(mmax);
+  b.U1 = ws.take<double>(umax);
+  b.Xpad = a.trunc ? ws.take<double>(b.Xoff[d]) : nullptr;
+  b.partials = ws.take<double>(1024);
+  b.delta2 = ws.take<double>(1);
+  b.ranks = ws.take<ll>(d + 1);
+  b.flags = ws.take<int>(8);
+  b.ticket = ws.take<unsigned int>(1);
+  return b;
+}
+
+void run_hatt(Runner &run, const HattArgs &a, const HattBufs &b) {
+  const int d = a.d;
+  const auto &n = a.n;
+  const auto &r = a.r;
+  const auto &s = a.s;
+  const auto &l = a.ell;
+  auto Wk = [&](int k) { return run.exec ? b.W + b.Woff[k] : nullptr; };
+  auto Xk = [&](int k) -> double * {
+    if (!run.exec) return nullptr;
+    return a.trunc ? b.Xpad + b.Xoff[k] : a.Xout[k];
+  };
+
+  if (d == 1) {   // the single core Y_1(i) Z_1(i)
+    if (run.live()) run.check(hatt::pkp_first(a.Y[0], a.Z[0], (int)n[0], 1, 1, a.Xout[0], run.st));
+    return;
+  }
+
+  // A1: sketch cores R_k (Definition 2.1)
+  if (run.live()) {
+    hatt::SketchTable t;
+    t.d = d;
+    t.seed = a.seed;
+    t.pair = 0;
+    for (int k = 0; k <= d; ++k) t.offset[k] = b.Roff[k];
+    for (int k = 0; k < d; ++k) {
+      t.a[k] = (int)l[k];
+      t.n[k] = (int)n[k];
+      t.b[k] = (int)l[k + 1];
+    }
+    run.check(hatt::sketch_fill(t, b.R, run.st));
+    run.check(hatt::set_value(Wk(d), 1, 1.0, run.st));          // W^{(d)} = [1]
+    run.check(hatt::set_value(b.winv + d, 1, 1.0, run.st));
+    run.check(cudaMemsetAsync(b.ticket, 0, sizeof(unsigned int), run.st));
+  }
+
+  // A2/A3: HPCRL-1, W^{(k)} from W^{(k+1)} and cores k of Y, Z, R (Eq. (3.6))
+  for (int k = d - 1; k >= 1; --k) {
+    const int r0 = (int)r[k], r1 = (int)r[k + 1], s0 = (int)s[k], s1 = (int)s[k + 1];
+    const int l0 = (int)l[k], l1 = (int)l[k + 1], nk = (int)n[k];
+    const double *Rk = b.R + b.Roff[k];
+    {   // S1: T1[i][x][lam] = sum_g W[x][g] R_k[lam][i][g] / ||W||
+      Gemm g;
+      g.M = r1 * s1; g.N = l0; g.K = l1;
+      g.batch = nk; g.bdiv = 1;
+      g.A = Wk(k + 1); g.sA1 = 0; g.sAm = l1; g.sAk = 1;
+      g.B = Rk; g.sB1 = l1; g.sBk = 1; g.sBn = (ll)nk * l1;
+      g.C = b.T1; g.sC1 = (ll)r1 * s1 * l0; g.sCm = l0; g.sCn = 1;
+      g.alpha_dev = b.winv ? b.winv + (k + 1) : nullptr;
+      run.gemm(g);
+    }
+    {   // S2: T2[i][a'][b][lam] = sum_b' Z_k[b][i][b'] T1[i][a'][b'][lam]
+      Gemm g;
+      g.M = s0; g.N = l0; g.K = s1;
+      g.batch = nk * r1; g.bdiv = r1;
+      g.A = a.Y ? a.Z[k] : nullptr; g.sA1 = s1; g.sA2 = 0; g.sAm = (ll)nk * s1; g.sAk = 1;
+      g.B = b.T1; g.sB1 = (ll)r1 * s1 * l0; g.sB2 = (ll)s1 * l0; g.sBk = l0; g.sBn = 1;
+      g.C = b.T2; g.sC1 = (ll)r1 * s0 * l0; g.sC2 = (ll)s0 * l0; g.sCm = l0; g.sCn = 1;
+      run.gemm(g);
+    }
+    {   // S3: W[a][b][lam] = sum_{i,a'} Y_k[a][i][a'] T2[i][a'][b][lam]
+      Gemm g;
+      g.M = r0; g.N = s0 * l0; g.K = nk * r1;
+      g.A = a.Y ? a.Y[k] : nullptr; g.sAm = (ll)nk * r1; g.sAk = 1;
+      g.B = b.T2; g.sBk = (ll)s0 * l0; g.sBn = 1;
+      g.C = Wk(k); g.sCm = (ll)s0 * l0; g.sCn = 1;
+      run.gemm(g);
+    }
+    if (run.live())
+      run.check(hatt::inv_norm(Wk(k), (ll)r0 * s0 * l0, b.winv + k, b.partials, b.ticket, run.st));
+  }
+
+  // A4-A8: left-to-right pass (Algorithm 4)
+  double *C = b.Ca, *Cn = b.Cb;
+  if (run.live())
+    run.check(hatt::pkp_first(a.Y[0], a.Z[0], (int)n[0], (int)r[1], (int)s[1], C, run.st));
+  for (int k = 0; k + 1 < d; ++k) {
+    const ll m = l[k] * n[k];
+    const int L = (int)l[k + 1];
+    const int r1 = (int)r[k + 1], s1 = (int)s[k + 1], r2 = (int)r[k + 2], s2 = (int)s[k + 2];
+    const int n1 = (int)n[k + 1];
+    const int rs = r1 * s1;
+    double *Q = Xk(k);
+    {   // A5: S = C_k W^{(k+1)} / ||W||
+      Gemm g;
+      g.M = (int)m; g.N = L; g.K = rs;
+      g.A = C; g.sAm = rs; g.sAk = 1;
+      g.B = Wk(k + 1); g.sBk = L; g.sBn = 1;
+      g.C = Q; g.sCm = L; g.sCn = 1;
+      g.alpha_dev = b.winv ? b.winv + (k + 1) : nullptr;
+      run.gemm(g);
+    }
+    run.qr(Q, (int)m, L, L, b.flags);                // A6
+    {   // A7: M = Q^T C_k
+      Gemm g;
+      g.M = L; g.N = rs; g.K = (int)m;
+      g.A = Q; g.sAm = 1; g.sAk = L;
+      g.B = C; g.sBk = rs; g.sBn = 1;
+      g.C = b.Mb; g.sCm = rs; g.sCn = 1;
+      run.gemm(g);
+    }
+    {   // A8 stage 1: U1[(g,a)][(i,b')] = sum_b M[g][a][b] Z_{k+1}[b][i][b']
+      Gemm g;
+      g.M = L * r1; g.N = n1 * s2; g.K = s1;
+      g.A = b.Mb; g.sAm = s1; g.sAk = 1;
+      g.B = a.Z ? a.Z[k + 1] : nullptr; g.sBk = (ll)n1 * s2; g.sBn = 1;
+      g.C = b.U1; g.sCm = (ll)n1 * s2; g.sCn = 1;
+      run.gemm(g);
+    }
+    double *dst = (k + 2 == d) ? Xk(d - 1) : Cn;
+    {   // A8 stage 2: C_{k+1}[g][i][a'][b'] = sum_a Y_{k+1}[a][i][a'] U1[g][a][i][b']
+      Gemm g;
+      g.M = r2; g.N = s2; g.K = r1;
+      g.batch = L * n1; g.bdiv = n1;
+      g.A = a.Y ? a.Y[k + 1] : nullptr; g.sA1 = 0; g.sA2 = r2; g.sAm = 1; g.sAk = (ll)n1 * r2;
+      g.B = b.U1; g.sB1 = (ll)r1 * n1 * s2; g.sB2 = s2; g.sBk = (ll)n1 * s2; g.sBn = 1;
+      g.C = dst; g.sC1 = (ll)n1 * r2 * s2; g.sC2 = (ll)r2 * s2; g.sCm = s2; g.sCn = 1;
+      run.gemm(g);
+    }
+    std::swap(C, Cn);
+  }
+
+  if (!a.trunc) return;
+  // A9: right-to-left truncation of the left-orthogonal result (padded)
+  if (run.live()) {
+    run.check(hatt::set_ranks(b.ranks, l.data(), d + 1, run.st));
+    run.check(hatt::trunc_delta2(Xk(d - 1), l[d - 1] * n[d - 1], a.tol, d, b.delta2, b.partials,
+                                 b.ticket, run.st));
+  }
+  for (int k = d - 1; k >= 1; --k)
+    run.trunc(Xk(k), (int)l[k], (int)n[k], (int)l[k + 1], Xk(k - 1), (int)l[k - 1], (int)n[k - 1],
+              a.cap, b.delta2, b.ranks, k);
+  if (run.live())
+    for (int k = 0; k < d; ++k)
+      run.check(hatt::compact_core(Xk(k), a.Xout[k], (int)l[k], (int)n[k], (int)l[k + 1], b.ranks,
+                                   k, run.st));
+}
+
+// Planning + argument checks shared by plan and execute.
+int prepare_hatt(const tt_t *Y, const tt_t *Z, const tt_opts *o, bool need_cores, HattArgs &a) {
+  int st = check_tt(Y, need_cores);
+  if (st != TT_OK) return st;
+  st = check_tt(Z, need_cores);
+  if (st != TT_OK) return st;
+  if (!o) return TT_ERR_ARG;
+  if (Y->d != Z->d) return TT_ERR_SHAPE;
+  for (int k = 0; k < Y->d; ++k)
+    if (Y->n[k] != Z->n[k]) return TT_ERR_SHAPE;
+  if (o->max_rank < 0 || o->sketch_rank < 0 || o->oversample < 0 || !(o->tol >= 0.0) ||
+      !std::isfinite(o->tol))
+    return TT_ERR_ARG;
+  if (o->precision != TT_FP64) return TT_ERR_ARG;
+  if (o->variant != 1) return TT_ERR_ARG;
+  const int d = Y->d;
+  a.d = d;
+  a.n = Y->n;
+  a.r = Y->r;
+  a.s = Z->r;
+  std::vector<ll> rs(d + 1);
+  ll pkp = 1;
+  for (int k = 0; k <= d; ++k) {
+    rs[k] = (ll)Y->r[k] * Z->r[k];
+    pkp = std::max(pkp, rs[k]);
+  }
+  ll lreq = o->sketch_rank > 0 ? o->sketch_rank
+                               : (o->max_rank > 0 ? o->max_rank + o->oversample : pkp);
+  a.ell = clamp_ranks(d, Y->n, rs, std::max<ll>(lreq, 1));
+  for (int k = 0; k <= d; ++k)
+    if (a.ell[k] > hatt::kMaxSmall) return TT_ERR_RANK;
+  // every GEMM dimension must fit in int
+  for (int k = 0; k < d; ++k) {
+    if (a.ell[k] * Y->n[k] > kIntMax) return TT_ERR_RANK;
+    if ((ll)Y->r[k + 1] * Z->r[k + 1] * Y->n[k] * std::max<ll>(a.ell[k], 1) > 4e9) return TT_ERR_RANK;
+  }
+  a.cap = (int)std::min<ll>(o->max_rank, hatt::kMaxSmall);
+  a.tol = o->tol;
+  a.seed = o->seed;
+  bool below = false;
+  for (int k = 1; k < d; ++k) below = below || (o->max_rank > 0 && a.ell[k] > o->max_rank);
+  a.trunc = d > 1 && (o->tol > 0.0 || below);
+  return TT_OK;
+}
+
+// ------------------------------------------------------------- rounding ---
+
+struct RoundArgs {
+  int d;
+  const int64_t *n, *r;
+  std::vector<ll> b;      // bound ranks after the left-to-right QR sweep
+  double *const *A;
+  double *const *Bout;
+  int cap;
+  double tol;
+};
+
+struct RoundBufs {
+  double *Xpad, *Ca, *Cb, *Mb, *partials, *delta2;
+  ll *ranks;
+  int *flags;
+  unsigned int *ticket;
+  std::vector<ll> Xoff;
+};
+
+RoundBufs carve_round(Ws &ws, const RoundArgs &a) {
+  RoundBufs u;
+  const int d = a.d;
+  u.Xoff.assign(d + 1, 0);
+  ll cmax = 1, mmax = 1;
+  for (int k = 0; k < d; ++k) {
+    u.Xoff[k + 1] = u.Xoff[k] + a.b[k] * a.n[k] * a.b[k + 1];
+    cmax = std::max(cmax, a.b[k] * a.n[k] * (ll)a.r[k + 1]);
+    mmax = std::max(mmax, a.b[k + 1] * (ll)a.r[k + 1]);
+  }
+  u.Xpad = ws.take<double>(u.Xoff[d]);
+  u.Ca = ws.take<double>(cmax);
+  u.Cb = ws.take<double>(cmax);
+  u.Mb = ws.take<double>(mmax);
+  u.partials = ws.take<double>(1024);
+  u.delta2 = ws.take<double>(1);
+  u.ranks = ws.take<ll>(d + 1);
+  u.flags = ws.take<int>(8);
+  u.ticket = ws.take<unsigned int>(1);
+  return u;
+}
+
+void run_round(Runner &run, const RoundArgs &a, const RoundBufs &u) {
+  const int d = a.d;
+  const auto &n = a.n;
+  const auto &r = a.r;
+  const auto &bnd = a.b;
+  auto Xk = [&](int k) { return run.exec ? u.Xpad + u.Xoff[k] : nullptr; };
+  if (run.live()) {
+    run.check(cudaMemsetAsync(u.ticket, 0, sizeof(unsigned int), run.st));
+    run.check(hatt::copy_f64(a.A[0], u.Ca, n[0] * (ll)r[1], run.st));
+  }
+  double *C = u.Ca, *Cn = u.Cb;
+  for (int k = 0; k + 1 < d; ++k) {
+    const ll m = bnd[k] * n[k];
+    const int cols = (int)r[k + 1];
+    const int c = (int)bnd[k + 1];
+    const int n1 = (int)n[k + 1], r2 = (int)r[k + 2];
+    double *Q = Xk(k);
+    const double *Msrc;
+    if (c == cols) {
+      if (run.live()) run.check(hatt::copy_f64(C, Q, m * cols, run.st));
+      run.qr(Q, (int)m, c, c, u.flags);
+      Gemm g;   // M = Q^T C
+      g.M = c; g.N = cols; g.K = (int)m;
+      g.A = Q; g.sAm = 1; g.sAk = c;
+      g.B = C; g.sBk = cols; g.sBn = 1;
+      g.C = u.Mb; g.sCm = cols; g.sCn = 1;
+      run.gemm(g);
+      Msrc = u.Mb;
+    } else {   // wide unfolding: Q = I, the whole core moves right
+      if (run.live()) run.check(hatt::set_identity(Q, (int)m, run.st));
+      Msrc = C;
+    }
+    double *dst = (k + 2 == d) ? Xk(d - 1) : Cn;
+    Gemm g;   // C_{k+1} = M H(A_{k+1})
+    g.M = c; g.N = n1 * r2; g.K = cols;
+    g.A = Msrc; g.sAm = cols; g.sAk = 1;
+    g.B = a.A ? a.A[k + 1] : nullptr; g.sBk = (ll)n1 * r2; g.sBn = 1;
+    g.C = dst; g.sCm = (ll)n1 * r2; g.sCn = 1;
+    run.gemm(g);
+    std::swap(C, Cn);
+  }
+  if (run.live()) {
+    run.check(hatt::set_ranks(u.ranks, bnd.data(), d + 1, run.st));
+    run.check(hatt::trunc_delta2(Xk(d - 1), bnd[d - 1] * n[d - 1], a.tol, d, u.delta2, u.partials,
+                                 u.ticket, run.st));
+  }
+  for (int k = d - 1; k >= 1; --k)
+    run.trunc(Xk(k), (int)bnd[k], (int)n[k], (int)bnd[k + 1], Xk(k - 1), (int)bnd[k - 1],
+              (int)n[k - 1], a.cap, u.delta2, u.ranks, k);
+  if (run.live())
+    for (int k = 0; k < d; ++k)
+      run.check(hatt::compact_core(Xk(k), a.Bout[k], (int)bnd[k], (int)n[k], (int)bnd[k + 1],
+                                   u.ranks, k, run.st));
+}
+
+int prepare_round(const tt_t *A, ll max_rank, double tol, bool need_cores, RoundArgs &a) {
+  int st = check_tt(A, need_cores);
+  if (st != TT_OK) return st;
+  if (max_rank < 0 || !(tol >= 0.0) || !std::isfinite(tol)) return TT_ERR_ARG;
+  const int d = A->d;
+  a.d = d;
+  a.n = A->n;
+  a.r = A->r;
+  a.b.assign(d + 1, 1);
+  for (int k = 0; k + 1 < d; ++k) a.b[k + 1] = std::min<ll>(A->r[k + 1], a.b[k] * A->n[k]);
+  for (int k = 0; k <= d; ++k)
+    if (a.b[k] > hatt::kMaxSmall || A->r[k] > hatt::kMaxSmall) return TT_ERR_RANK;
+  for (int k = 0; k < d; ++k)
+    if (a.b[k] * A->n[k] > kIntMax) return TT_ERR_RANK;
+  a.cap = (int)std::min<ll>(max_rank, hatt::kMaxSmall);
+  a.tol = tol;
+  return TT_OK;
+}
+
+// ----------------------------------------------------------------- dot ---
+
+struct DotBufs {
+  double *Ga, *Gb, *T;
+};
+
+DotBufs carve_dot(Ws &ws, const tt_t *A, const tt_t *B) {
+  DotBufs u;
+  ll g = 1, t = 1;
+  for (int k = 0; k <= A->d; ++k) g = std::max(g, (ll)A->r[k] * B->r[k]);
+  for (int k = 0; k < A->d; ++k) t = std::max(t, (ll)A->r[k] * A->n[k] * B->r[k + 1]);
+  u.Ga = ws.take<double>(g);
+  u.Gb = ws.take<double>(g);
+  u.T = ws.take<double>(t);
+  return u;
+}
+
+void run_dot(Runner &run, const tt_t *A, const tt_t *B, const DotBufs &u, double *out) {
+  double *G = u.Ga, *Gn = u.Gb;
+  if (run.live()) run.check(hatt::set_value(G, 1, 1.0, run.st));
+  for (int k = 0; k < A->d; ++k) {
+    const int a0 = (int)A->r[k], a1 = (int)A->r[k + 1];
+    const int b0 = (int)B->r[k], b1 = (int)B->r[k + 1], nk = (int)A->n[k];
+    {   // T = G H(B_k)
+      Gemm g;
+      g.M = a0; g.N = nk * b1; g.K = b0;
+      g.A = G; g.sAm = b0; g.sAk = 1;
+      g.B = B->cores ? B->cores[k] : nullptr; g.sBk = (ll)nk * b1; g.sBn = 1;
+      g.C = u.T; g.sCm = (ll)nk * b1; g.sCn = 1;
+      run.gemm(g);
+    }
+    {   // G' = V(A_k)^T V(T)
+      Gemm g;
+      g.M = a1; g.N = b1; g.K = a0 * nk;
+      g.A = A->cores ? A->cores[k] : nullptr; g.sAm = 1; g.sAk = a1;
+      g.B = u.T; g.sBk = b1; g.sBn = 1;
+      g.C = (k + 1 == A->d) ? out : Gn; g.sCm = b1; g.sCn = 1;
+      run.gemm(g);
+    }
+    std::swap(G, Gn);
+  }
+}
+
+int prepare_dot(const tt_t *A, const tt_t *B, bool need_cores) {
+  int st = check_tt(A, need_cores);
+  if (st != TT_OK) return st;
+  st = check_tt(B, need_cores);
+  if (st != TT_OK) return st;
+  if (A->d != B->d) return TT_ERR_SHAPE;
+  for (int k = 0; k < A->d; ++k) {
+    if (A->n[k] != B->n[k]) return TT_ERR_SHAPE;
+    if ((ll)A->r[k] * A->n[k] > kIntMax || (ll)B->r[k + 1] * B->n[k] > kIntMax) return TT_ERR_RANK;
+  }
+  return TT_OK;
+}
+
+template <class Carve, class Run>
+size_t measure(Carve carve, Run runf) {
+  Ws ws;
+  Runner run;
+  auto bufs = carve(ws);
+  runf(run, bufs);
+  ws.take<double>(run.scratch_need);
+  return ws.off + 256;
+}
+
+template <class Carve, class Run>
+int execute(void *workspace, size_t wsb, cudaStream_t st, Carve carve, Run runf) {
+  // planning pass: scratch size
+  Ws pws;
+  Runner plan;
+  auto pb = carve(pws);
+  runf(plan, pb);
+  // execution pass on the caller's workspace
+  Ws ws;
+  ws.exec = true;
+  ws.base = (char *)workspace;
+  auto bufs = carve(ws);
+  Runner run;
+  run.exec = true;
+  run.st = st;
+  run.scratch = ws.take<double>(plan.scratch_need);
+  if (ws.off > wsb) return TT_ERR_WORKSPACE;
+  runf(run, bufs);
+  return from_cuda(run.err);
+}
+
+bool aligned(const void *p) { return ((uintptr_t)p & 255u) == 0; }
+
+}  // namespace
+
+// ===================================================================== ABI ===
+
+extern "C" {
+
+const char *tt_status_string(int status) {
+  switch (status) {
+    case TT_OK: return "ok";
+    case TT_ERR_SHAPE: return "shape mismatch (orders, mode sizes, boundary ranks or aliasing)";
+    case TT_ERR_RANK: return "rank or size above the supported bound";
+    case TT_ERR_ARG: return "invalid argument (null pointer or option)";
+    case TT_ERR_WORKSPACE: return "workspace too small or misaligned";
+    case TT_ERR_CUDA: return "CUDA launch or copy failed";
+    case TT_ERR_NONFINITE: return "non-finite value";
+    default: return "unknown status";
+  }
+}
+
+int tt_hadamard_recompress_plan(const tt_t *Y, const tt_t *Z, const tt_opts *opts,
+                                int64_t *out_rank_bound, size_t *workspace_bytes) {
+  if (!out_rank_bound || !workspace_bytes) return TT_ERR_ARG;
+  HattArgs a;
+  int st = prepare_hatt(Y, Z, opts, false, a);
+  if (st != TT_OK) return st;
+  for (int k = 0; k <= a.d; ++k) out_rank_bound[k] = a.ell[k];
+  a.Y = nullptr;
+  a.Z = nullptr;
+  a.Xout = nullptr;
+  *workspace_bytes = measure([&](Ws &ws) { return carve_hatt(ws, a); },
+                             [&](Runner &run, const HattBufs &b) { run_hatt(run, a, b); });
+  return TT_OK;
+}
+
+int tt_hadamard_recompress(const tt_t *Y, const tt_t *Z, const tt_opts *opts, tt_t *X,
+                           void *workspace, size_t workspace_bytes, void *stream) {
+  HattArgs a;
+  int st = prepare_hatt(Y, Z, opts, true, a);
+  if (st != TT_OK) return st;
+  if (!X || !X->cores || !X->r || !X->n) return TT_ERR_ARG;
+  if (X->d != Y->d) return TT_ERR_SHAPE;
+  for (int k = 0; k < X->d; ++k) {
+    if (X->n[k] != Y->n[k]) return TT_ERR_SHAPE;
+    if (!X->cores[k]) return TT_ERR_ARG;
+  }
+  if (!workspace || !aligned(workspace)) return TT_ERR_WORKSPACE;
+  // outputs must not overlap inputs
+  for (int k = 0; k < a.d; ++k) {
+    const size_t xb = (size_t)a.ell[k] * a.n[k] * a.ell[k + 1] * sizeof(double);
+    for (int j = 0; j < a.d; ++j) {
+      const size_t yb = (size_t)Y->r[j] * Y->n[j] * Y->r[j + 1] * sizeof(double);
+      const size_t zb = (size_t)Z->r[j] * Z->n[j] * Z->r[j + 1] * sizeof(double);
+      if (overlap(X->cores[k], xb, Y->cores[j], yb) || overlap(X->cores[k], xb, Z->cores[j], zb))
+        return TT_ERR_SHAPE;
+    }
+  }
+  a.Y = Y->cores;
+  a.Z = Z->cores;
+  a.Xout = X->cores;
+  cudaStream_t strm = (cudaStream_t)stream;
+  HattBufs bufs_for_ranks;
+  st = execute(workspace, workspace_bytes, strm,
+               [&](Ws &ws) {
+                 HattBufs b = carve_hatt(ws, a);
+                 if (ws.exec) bufs_for_ranks = b;
+                 return b;
+               },
+               [&](Runner &run, const HattBufs &b) { run_hatt(run, a, b); });
+  if (st != TT_OK) return st;
+  if (a.trunc) {
+    cudaError_t e = cudaMemcpyAsync(X->r, bufs_for_ranks.ranks, (a.d + 1) * sizeof(int64_t),
+                                    cudaMemcpyDeviceToHost, strm);
+    if (e != cudaSuccess) return from_cuda(e);
+  } else {
+    for (int k = 0; k <= a.d; ++k) X->r[k] = a.ell[k];
+  }
+  return TT_OK;
+}
+
+int tt_round_plan(const tt_t *A, int64_t max_rank, double tol, int64_t *out_rank_bound,
+                  size_t *workspace_bytes) {
+  if (!out_rank_bound || !workspace_bytes) return TT_ERR_ARG;
+  RoundArgs a;
+  int st = prepare_round(A, max_rank, tol, false, a);
+  if (st != TT_OK) return st;
+  for (int k = 0; k <= a.d; ++k) out_rank_bound[k] = a.b[k];
+  a.A = nullptr;
+  a.Bout = nullptr;
+  *workspace_bytes = measure([&](Ws &ws) { return carve_round(ws, a); },
+                             [&](Runner &run, const RoundBufs &u) { run_round(run, a, u); });
+  return TT_OK;
+}
+
+int tt_round(const tt_t *A, int64_t max_rank, double tol, tt_t *B, void *workspace,
+             size_t workspace_bytes, void *stream) {
+  RoundArgs a;
+  int st = prepare_round(A, max_rank, tol, true, a);
+  if (st != TT_OK) return st;
+  if (!B || !B->cores || !B->r || !B->n) return TT_ERR_ARG;
+  if (B->d != A->d) return TT_ERR_SHAPE;
+  for (int k = 0; k < A->d; ++k) {
+    if (B->n[k] != A->n[k]) return TT_ERR_SHAPE;
+    if (!B->cores[k]) return TT_ERR_ARG;
+  }
+  if (!workspace || !aligned(workspace)) return TT_ERR_WORKSPACE;
+  for (int k = 0; k < a.d; ++k) {
+    const size_t bb = (size_t)a.b[k] * a.n[k] * a.b[k + 1] * sizeof(double);
+    for (int j = 0; j < a.d; ++j) {
+      const size_t ab = (size_t)A->r[j] * A->n[j] * A->r[j + 1] * sizeof(double);
+      if (overlap(B->cores[k], bb, A->cores[j], ab)) return TT_ERR_SHAPE;
+    }
+  }
+  a.A = A->cores;
+  a.Bout = B->cores;
+  cudaStream_t strm = (cudaStream_t)stream;
+  RoundBufs keep;
+  st = execute(workspace, workspace_bytes, strm,
+               [&](Ws &ws) {
+                 RoundBufs u = carve_round(ws, a);
+                 if (ws.exec) keep = u;
+                 return u;
+               },
+               [&](Runner &run, const RoundBufs &u) { run_round(run, a, u); });
+  if (st != TT_OK) return st;
+  cudaError_t e = cudaMemcpyAsync(B->r, keep.ranks, (a.d + 1) * sizeof(int64_t),
+                                  cudaMemcpyDeviceToHost, strm);
+  return from_cuda(e);
+}
+
+int tt_dot_plan(const tt_t *A, const tt_t *B, size_t *workspace_bytes) {
+  if (!workspace_bytes) return TT_ERR_ARG;
+  int st = prepare_dot(A, B, false);
+  if (st != TT_OK) return st;
+  tt_t a0 = *A, b0 = *B;
+  a0.cores = nullptr;
+  b0.cores = nullptr;
+  *workspace_bytes = measure([&](Ws &ws) { return carve_dot(ws, &a0, &b0); },
+                             [&](Runner &run, const DotBufs &u) { run_dot(run, &a0, &b0, u, nullptr); });
+  return TT_OK;
+}
+
+int tt_dot(const tt_t *A, const tt_t *B, double *out, void *workspace, size_t workspace_bytes,
+           void *stream) {
+  int st = prepare_dot(A, B, true);
+  if (st != TT_OK) return st;
+  if (!out) return TT_ERR_ARG;
+  if (!workspace || !aligned(workspace)) return TT_ERR_WORKSPACE;
+  return execute(workspace, workspace_bytes, (cudaStream_t)stream,
+                 [&](Ws &ws) { return carve_dot(ws, A, B); },
+                 [&](Runner &run, const DotBufs &u) { run_dot(run, A, B, u, out); });
+}
+
+int tt_norm(const tt_t *A, double *out, void *workspace, size_t workspace_bytes, void *stream) {
+  int st = tt_dot(A, A, out, workspace, workspace_bytes, stream);
+  if (st != TT_OK) return st;
+  return from_cuda(hatt::sqrt_scalar(out, out, (cudaStream_t)stream));
+}
+
+int tt_sketch_tt(int32_t d, const int64_t *n, const int64_t *ell, uint64_t seed, uint32_t pair,
+                 double **cores, void *stream) {
+  if (!n || !ell || !cores) return TT_ERR_ARG;
+  if (d < 1) return TT_ERR_SHAPE;
+  if (d > hatt::kMaxOrder) return TT_ERR_RANK;
+  if (ell[0] != 1 || ell[d] != 1) return TT_ERR_SHAPE;
+  for (int k = 0; k < d; ++k) {
+    if (n[k] < 1 || ell[k + 1] < 1) return TT_ERR_SHAPE;
+    if ((double)ell[k] * n[k] * ell[k + 1] >= 4294967296.0) return TT_ERR_RANK;
+    if (!cores[k]) return TT_ERR_ARG;
+  }
+  return from_cuda(hatt::sketch_fill_ptrs(d, n, ell, seed, pair, cores, (cudaStream_t)stream));
+}
+
+int tt_philox4x32_10(const uint32_t *ctr, uint32_t key0, uint32_t key1, uint32_t *out,
+                     int64_t count, void *stream) {
+  if (count < 0) return TT_ERR_ARG;
+  if (count == 0) return TT_OK;
+  if (!ctr || !out) return TT_ERR_ARG;
+  return from_cuda(hatt::philox_raw(ctr, key0, key1, out, count, (cudaStream_t)stream));
+}
+
+}  // extern "C"

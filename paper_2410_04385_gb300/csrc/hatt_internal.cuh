@@ -1,0 +1,103 @@
+// Internal declarations shared by the libhatt CUDA sources.
+// Each kernel lives with its launch helper in one .cu file; the helpers below
+// are the only cross-file interface (plain host functions, no relocatable
+// device code).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+namespace hatt {
+
+constexpr int kMaxSmall = 128;   // TT_MAX_SMALL_RANK
+constexpr int kMaxOrder = 512;   // largest d handled by the parameter tables
+
+// ------------------------------------------------------------------ GEMM ---
+// C[b](m, n) = alpha * (alpha_dev ? *alpha_dev : 1) * sum_k A[b](m, k) B[b](k, n)
+//              + beta * C[b](m, n)
+// with element offsets
+//   A[b](m, k) = A[b1*sA1 + b2*sA2 + m*sAm + k*sAk],   b1 = b / bdiv, b2 = b % bdiv
+//   B[b](k, n) = B[b1*sB1 + b2*sB2 + k*sBk + n*sBn]
+//   C[b](m, n) = C[b1*sC1 + b2*sC2 + m*sCm + n*sCn]
+// beta == 0 never reads C. When the planner splits K, partial sums go to a
+// workspace buffer and a second kernel reduces them in a fixed order, so the
+// result is bitwise reproducible.
+struct Gemm {
+  int M = 0, N = 0, K = 0;
+  int batch = 1, bdiv = 1;
+  long long sA1 = 0, sA2 = 0, sAm = 0, sAk = 0;
+  long long sB1 = 0, sB2 = 0, sBk = 0, sBn = 0;
+  long long sC1 = 0, sC2 = 0, sCm = 0, sCn = 0;
+  const double *A = nullptr, *B = nullptr;
+  double *C = nullptr;
+  double alpha = 1.0, beta = 0.0;
+  const double *alpha_dev = nullptr;
+  const int *skip_dev = nullptr;   // if set and *skip_dev != 0 the launch does nothing
+};
+
+// Doubles of split-K scratch this GEMM needs (0 if it runs unsplit).
+size_t gemm_scratch_doubles(const Gemm &g);
+// Enqueue; `scratch` must hold gemm_scratch_doubles(g) doubles.
+cudaError_t gemm_f64(const Gemm &g, double *scratch, cudaStream_t st);
+
+// ------------------------------------------------------------ sketch RNG ---
+struct SketchTable {
+  int d;
+  uint64_t seed;
+  uint32_t pair;
+  long long offset[kMaxOrder + 1];   // element offset of core k inside `base`
+  int a[kMaxOrder], n[kMaxOrder], b[kMaxOrder];
+};
+// Fill the sketch cores (contiguous at `base`, core k at base + offset[k]).
+cudaError_t sketch_fill(const SketchTable &t, double *base, cudaStream_t st);
+// Fill per-core pointers (used by the public tt_sketch_tt).
+cudaError_t sketch_fill_ptrs(int d, const int64_t *n, const int64_t *ell, uint64_t seed,
+                             uint32_t pair, double *const *cores, cudaStream_t st);
+cudaError_t philox_raw(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out,
+                       long long count, cudaStream_t st);
+
+// ----------------------------------------------------------------- misc ---
+// out[0] = 1 / ||x||_F (1 if the norm is 0); `partials` holds >= 1024 doubles,
+// `ticket` one unsigned int that must be 0 on entry (the kernel resets it).
+cudaError_t inv_norm(const double *x, long long count, double *out, double *partials,
+                     unsigned int *ticket, cudaStream_t st);
+// First core of the Hadamard product: C[0, i, a*s + b] = Y[0, i, a] * Z[0, i, b].
+cudaError_t pkp_first(const double *Y, const double *Z, int n, int r1, int s1, double *C,
+                      cudaStream_t st);
+cudaError_t set_value(double *x, long long count, double v, cudaStream_t st);
+// X = I (m x m, row-major).
+cudaError_t set_identity(double *X, int m, cudaStream_t st);
+cudaError_t copy_f64(const double *src, double *dst, long long count, cudaStream_t st);
+// dst[(a*n + i)*rb + b] = src[(a*n + i)*lb + b] for a < ra, b < rb, with ra, rb
+// read from ranks_dev[k], ranks_dev[k+1] (device int64) and bounds la x n x lb.
+cudaError_t compact_core(const double *src, double *dst, int la, int n, int lb,
+                         const long long *ranks_dev, int k, cudaStream_t st);
+// out = sqrt(max(x, 0)) for a device scalar.
+cudaError_t sqrt_scalar(const double *x, double *out, cudaStream_t st);
+
+// --------------------------------------------------------------- QR ---
+// In-place orthonormalization of the m x c row-major matrix S (leading
+// dimension ldS >= c) by repeated Cholesky QR passes. Needs qr_scratch_doubles.
+size_t qr_scratch_doubles(int m, int c);
+cudaError_t qr_inplace(double *S, int m, int c, long long ldS, double *scratch, int *flags,
+                       cudaStream_t st);
+
+// ------------------------------------------------------------ truncation ---
+size_t trunc_scratch_doubles(int la, int n, int lb, int lm, int nm);
+// One right-to-left truncation step on core k of a padded left-orthogonal TT.
+//   Xk   : la x n x lb padded core (columns >= ranks_dev[k+1] are zero)
+//   Xkm1 : lm x nm x la padded core k-1
+// Chooses rho = ranks_dev[k] <= min(la, cap) by the tolerance rule with
+// delta2_dev[0] = delta^2, replaces Xk by its rho orthonormal right factor and
+// multiplies the left factor into Xkm1; rows/cols beyond rho are zeroed.
+cudaError_t trunc_step(double *Xk, int la, int n, int lb, double *Xkm1, int lm, int nm,
+                       int cap, const double *delta2_dev, long long *ranks_dev, int k,
+                       double *scratch, cudaStream_t st);
+// delta2_dev = (tol * ||x|| )^2 / (d-1) for a device vector x.
+cudaError_t trunc_delta2(const double *x, long long count, double tol, int d, double *delta2_dev,
+                         double *partials, unsigned int *ticket, cudaStream_t st);
+cudaError_t set_ranks(long long *ranks_dev, const long long *ranks_host, int count,
+                      cudaStream_t st);
+
+}  // namespace hatt

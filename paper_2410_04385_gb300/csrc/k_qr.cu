@@ -1,0 +1,229 @@
+// Economy QR of the tall sketch S = C_k W^{(k)} (Algorithm 4) on GB300.
+//
+// Householder QR is a chain of rank-1 updates and would run on one SM at the
+// FP64 rate of a single SM (~8 GFLOP/s on GB300). Cholesky QR instead spends
+// almost all of its flops in two SM-parallel products (the Gram S^T S and
+// S R^{-1}); only a c x c Cholesky factorization and triangular inverse run in
+// one block. A pass is
+//     G = S^T S,  R^T R = G (+ shift),  S <- S R^{-1}
+// and passes repeat until G = I to working accuracy (Cholesky QR2 needs two
+// passes for cond(S) < ~1e8). When the unshifted factorization breaks down
+// (cond(S) >~ 1e8, or exactly dependent columns as in Y ⊙ Y or exact
+// low-rank products), the pass uses the shift s = 11 (m c + c (c + 1)) u tr(G)
+// of shifted Cholesky QR (Fukaya, Kannan, Nakatsukasa, Yamamoto, Yanagisawa,
+// SIAM J. Sci. Comput. 2020); each shifted pass lifts the smallest singular
+// values towards 1, so later passes converge. A column that is exactly zero
+// stays zero (its Gram row and column vanish), which leaves a partial
+// isometry whose zero columns carry nothing into the next core.
+//
+// All passes are launched unconditionally (fixed launch sequence, capturable
+// in a CUDA graph); a device flag set by the convergence test turns the
+// remaining launches into no-ops.
+#include <algorithm>
+#include "hatt_internal.cuh"
+
+namespace hatt {
+namespace {
+
+constexpr int kPasses = 4;
+constexpr int kCholThreads = 256;
+constexpr int kTrmmThreads = 256;
+constexpr int kTrmmRows = 16;
+
+// flags[0]: converged; flags[1]: number of shifted passes; flags[2]: passes run
+__global__ void __launch_bounds__(kCholThreads)
+chol_inv_kernel(const double *Gg, double *Rinv, int c, int m, int *flags) {
+  if (flags[0]) return;
+  extern __shared__ double sm[];
+  const int ld = c + 1;
+  double *G = sm;                       // c x ld, upper triangle becomes R
+  __shared__ double s_diag_max, s_trace, s_dev;
+  __shared__ int s_fail;
+  const int tid = threadIdx.x;
+
+  // -- convergence test: G = I to working accuracy, except columns that are
+  // exactly zero (a zero column stays zero through every pass). The test is
+  // absolute on purpose: S of any scale (HaTT sketches of long chains reach
+  // 1e-20 and below) is never mistaken for a converged basis.
+  if (tid == 0) { s_dev = 0.0; s_diag_max = 0.0; s_trace = 0.0; }
+  __syncthreads();
+  double dev = 0.0, dmax = 0.0, tr = 0.0;
+  for (int e = tid; e < c * c; e += kCholThreads) {
+    const int i = e / c, j = e % c;
+    const double v = Gg[e];
+    G[i * ld + j] = v;
+    if (i == j) {
+      dmax = fmax(dmax, v);
+      tr += v;
+      dev = fmax(dev, (v == 0.0) ? 0.0 : fabs(v - 1.0));
+    } else {
+      dev = fmax(dev, fabs(v));
+    }
+  }
+  // block reductions (max of dev / dmax, sum of tr) through shared atomics on bit patterns
+  {
+    __shared__ double red[kCholThreads];
+    red[tid] = dev;
+    __syncthreads();
+    for (int w = kCholThreads / 2; w > 0; w >>= 1) {
+      if (tid < w) red[tid] = fmax(red[tid], red[tid + w]);
+      __syncthreads();
+    }
+    if (tid == 0) s_dev = red[0];
+    __syncthreads();
+    red[tid] = dmax;
+    __syncthreads();
+    for (int w = kCholThreads / 2; w > 0; w >>= 1) {
+      if (tid < w) red[tid] = fmax(red[tid], red[tid + w]);
+      __syncthreads();
+    }
+    if (tid == 0) s_diag_max = red[0];
+    __syncthreads();
+    red[tid] = tr;
+    __syncthreads();
+    for (int w = kCholThreads / 2; w > 0; w >>= 1) {
+      if (tid < w) red[tid] += red[tid + w];
+      __syncthreads();
+    }
+    if (tid == 0) s_trace = red[0];
+    __syncthreads();
+  }
+  const double u = 1.1102230246251565e-16;
+  if (s_dev <= 8.0 * c * u) {
+    if (tid == 0) flags[0] = 1;
+    return;
+  }
+  if (tid == 0) flags[2] += 1;
+
+  // -- Cholesky: first unshifted, then shifted if a pivot is not safely positive
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    double shift = 0.0;
+    if (attempt == 1) {
+      shift = 11.0 * ((double)m * c + (double)c * (c + 1)) * u * s_trace;
+      if (!(shift > 0.0)) shift = 1e-300;
+      for (int e = tid; e < c * c; e += kCholThreads) {
+        const int i = e / c, j = e % c;
+        G[i * ld + j] = Gg[e] + (i == j ? shift : 0.0);
+      }
+      if (tid == 0) flags[1] += 1;
+    }
+    if (tid == 0) s_fail = 0;
+    __syncthreads();
+    const double floor_piv = (attempt == 0) ? (double)c * u * s_diag_max : 0.0;
+    for (int j = 0; j < c; ++j) {
+      if (tid == 0) {
+        double piv = G[j * ld + j];
+        if (!(piv > floor_piv)) {
+          if (attempt == 0) s_fail = 1;
+          piv = fmax(shift, 1e-300);          // shifted attempt: never divide by zero
+        }
+        G[j * ld + j] = sqrt(piv);
+      }
+      __syncthreads();
+      if (s_fail) break;
+      const double rjj = G[j * ld + j];
+      for (int l = j + 1 + tid; l < c; l += kCholThreads) G[j * ld + l] /= rjj;
+      __syncthreads();
+      const int rem = c - j - 1;
+      for (int e = tid; e < rem * rem; e += kCholThreads) {
+        const int i = j + 1 + e / rem, l = j + 1 + e % rem;
+        if (l >= i) G[i * ld + l] = fma(-G[j * ld + i], G[j * ld + l], G[i * ld + l]);
+      }
+      __syncthreads();
+    }
+    __syncthreads();
+    if (!s_fail) break;
+  }
+
+  // -- triangular inverse, row by row from the bottom: Rinv[i][j], j >= i.
+  // Rows of Rinv are written to global memory and read back by the same block
+  // (__syncthreads orders the block's global writes before later reads).
+  for (int e = tid; e < c * c; e += kCholThreads) {
+    const int i = e / c, j = e % c;
+    if (j < i) Rinv[e] = 0.0;
+  }
+  for (int i = c - 1; i >= 0; --i) {
+    const double rii = G[i * ld + i];
+    for (int j = i + tid; j < c; j += kCholThreads) {
+      double s = (j == i) ? 1.0 : 0.0;
+      for (int l = i + 1; l <= j; ++l) s = fma(-G[i * ld + l], Rinv[l * c + j], s);
+      Rinv[i * c + j] = s / rii;
+    }
+    __syncthreads();
+  }
+}
+
+// S[r][j] <- sum_{i <= j} S[r][i] Rinv[i][j], rows owned by one block (in place).
+__global__ void __launch_bounds__(kTrmmThreads)
+trmm_rows_kernel(double *S, int m, int c, long long ldS, const double *Rinv, const int *flags) {
+  if (flags[0]) return;
+  extern __shared__ double sm[];
+  double *Rs = sm;                       // c x c
+  double *Xs = sm + c * c;               // kTrmmRows x c
+  const int r0 = blockIdx.x * kTrmmRows;
+  const int rows = min(kTrmmRows, m - r0);
+  for (int e = threadIdx.x; e < c * c; e += kTrmmThreads) Rs[e] = Rinv[e];
+  for (int e = threadIdx.x; e < rows * c; e += kTrmmThreads) {
+    const int r = e / c, j = e % c;
+    Xs[r * c + j] = S[(long long)(r0 + r) * ldS + j];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < rows * c; e += kTrmmThreads) {
+    const int r = e / c, j = e % c;
+    double s = 0.0;
+    for (int i = 0; i <= j; ++i) s = fma(Xs[r * c + i], Rs[i * c + j], s);
+    S[(long long)(r0 + r) * ldS + j] = s;
+  }
+}
+
+size_t chol_smem(int c) { return (size_t)c * (c + 1) * sizeof(double); }
+size_t trmm_smem(int c) { return (size_t)(c * c + kTrmmRows * c) * sizeof(double); }
+
+Gemm gram_desc(double *S, int m, int c, long long ldS, double *G, const int *flags) {
+  Gemm g;
+  g.M = c; g.N = c; g.K = m;
+  g.A = S; g.sAm = 1; g.sAk = ldS;       // A(i, k) = S[k][i]
+  g.B = S; g.sBk = ldS; g.sBn = 1;       // B(k, j) = S[k][j]
+  g.C = G; g.sCm = c; g.sCn = 1;
+  g.skip_dev = flags;
+  return g;
+}
+
+}  // namespace
+
+size_t qr_scratch_doubles(int m, int c) {
+  Gemm g = gram_desc(nullptr, m, c, c, nullptr, nullptr);
+  return (size_t)2 * c * c + gemm_scratch_doubles(g);
+}
+
+cudaError_t qr_inplace(double *S, int m, int c, long long ldS, double *scratch, int *flags,
+                       cudaStream_t st) {
+  if (c <= 0 || m <= 0) return cudaSuccess;
+  if (c > kMaxSmall) return cudaErrorInvalidValue;
+  double *G = scratch;
+  double *Rinv = scratch + (size_t)c * c;
+  double *gs = scratch + (size_t)2 * c * c;
+  cudaError_t e = cudaMemsetAsync(flags, 0, 3 * sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)chol_smem(kMaxSmall));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(trmm_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)trmm_smem(kMaxSmall));
+  if (e != cudaSuccess) return e;
+  const Gemm gd = gram_desc(S, m, c, ldS, G, flags);
+  const int blocks = (m + kTrmmRows - 1) / kTrmmRows;
+  for (int p = 0; p < kPasses; ++p) {
+    e = gemm_f64(gd, gs, st);
+    if (e != cudaSuccess) return e;
+    chol_inv_kernel<<<1, kCholThreads, chol_smem(c), st>>>(G, Rinv, c, m, flags);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    trmm_rows_kernel<<<blocks, kTrmmThreads, trmm_smem(c), st>>>(S, m, c, ldS, Rinv, flags);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace hatt

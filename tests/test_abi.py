@@ -1,0 +1,175 @@
+"""Host-side tests of the C ABI: the library loads, exports every symbol that
+include/hatt.h declares, and its planning / argument checks (host code only,
+no kernel launches) agree with the oracle's rank plan."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import hatt as ohatt
+from paper_2410_04385_gb300 import binding as B
+from paper_2410_04385_gb300 import build as libbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(B.LIB_PATH):
+        libbuild.build()
+    return B.load()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "hatt.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(tt_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_header_declares_the_path_entry_points():
+    names = declared_functions()
+    for want in ("tt_hadamard_recompress", "tt_round", "tt_dot", "tt_norm"):
+        assert want in names
+    assert len(names) >= 10
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    nm_names = set(B.EXPORTS)
+    assert set(declared_functions()) <= nm_names
+
+
+def test_status_strings(lib):
+    for st in range(0, 7):
+        assert len(B.status_string(st)) > 0
+    assert B.status_string(99) == "unknown status"
+
+
+def _plan(Yr, Zr, n, **opts):
+    Yd = B.TT(n=n, r=Yr)
+    Zd = B.TT(n=n, r=Zr)
+    o = B.make_opts(**opts)
+    d = len(n)
+    bound = (ctypes.c_int64 * (d + 1))()
+    ws = ctypes.c_size_t()
+    st = B.load().tt_hadamard_recompress_plan(Yd.ref(), Zd.ref(), ctypes.byref(o), bound,
+                                              ctypes.byref(ws))
+    return st, [int(v) for v in bound], int(ws.value)
+
+
+def test_plan_matches_oracle_small_workload(lib):
+    n = [8] * 6
+    st, bound, ws = _plan([1, 2, 2, 2, 2, 2, 1], [1, 5, 5, 5, 5, 5, 1], n, max_rank=10, tol=1e-12,
+                          sketch_rank=12)
+    assert st == 0
+    assert bound == [1, 8, 10, 10, 10, 8, 1]
+    assert ws > 0
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_plan_matches_oracle_random(lib, seed):
+    rng = np.random.default_rng(seed)
+    d = int(rng.integers(1, 8))
+    n = [int(v) for v in rng.integers(1, 9, size=d)]
+    r = [1] + [int(v) for v in rng.integers(1, 9, size=d - 1)] + [1]
+    s = [1] + [int(v) for v in rng.integers(1, 9, size=d - 1)] + [1]
+    mr = int(rng.integers(0, 20))
+    sk = int(rng.integers(0, 40))
+    st, bound, ws = _plan(r, s, n, max_rank=mr, sketch_rank=sk, oversample=5)
+    assert st == 0
+    lreq = ohatt.requested_sketch_rank(r, s, mr, sk, 5)
+    assert bound == ohatt.plan_ranks(n, r, s, lreq)
+
+
+@pytest.mark.parametrize("d,n,r,lreq", [(20, 32, 20, 50), (50, 64, 40, 90), (300, 2, 3, 9)])
+def test_plan_long_chains_saturate_mode_products(lib, d, n, r, lreq):
+    rk = [1] + [r] * (d - 1) + [1]
+    st, bound, ws = _plan(rk, rk, [n] * d, sketch_rank=lreq)
+    assert st == 0
+    assert bound == ohatt.plan_ranks([n] * d, rk, rk, lreq)
+    assert min(bound) >= 1
+
+
+def test_plan_workspace_grows_with_size(lib):
+    small = _plan([1] + [4] * 5 + [1], [1] + [4] * 5 + [1], [8] * 6, sketch_rank=8)[2]
+    big = _plan([1] + [20] * 19 + [1], [1] + [20] * 19 + [1], [32] * 20, max_rank=40,
+                sketch_rank=50)[2]
+    assert big > small > 0
+
+
+@pytest.mark.parametrize("case,expect", [
+    ("order_mismatch", 1), ("mode_mismatch", 1), ("boundary_rank", 1), ("zero_mode", 1),
+    ("negative_opt", 3), ("bad_precision", 3), ("bad_variant", 3), ("rank_too_big", 2),
+])
+def test_plan_rejects_bad_arguments(lib, case, expect):
+    n = [4, 4, 4]
+    Yr, Zr = [1, 3, 3, 1], [1, 2, 2, 1]
+    opts = dict(sketch_rank=4)
+    if case == "order_mismatch":
+        Yd, Zd = B.TT(n=n, r=Yr), B.TT(n=[4, 4], r=[1, 2, 1])
+    elif case == "mode_mismatch":
+        Yd, Zd = B.TT(n=n, r=Yr), B.TT(n=[4, 5, 4], r=Zr)
+    elif case == "boundary_rank":
+        Yd, Zd = B.TT(n=n, r=[2, 3, 3, 1]), B.TT(n=n, r=Zr)
+    elif case == "zero_mode":
+        Yd, Zd = B.TT(n=[4, 0, 4], r=Yr), B.TT(n=[4, 0, 4], r=Zr)
+    elif case == "rank_too_big":
+        Yd = B.TT(n=[64] * 4, r=[1, 64, 64, 64, 1])
+        Zd = B.TT(n=[64] * 4, r=[1, 64, 64, 64, 1])
+        opts = dict(sketch_rank=200)
+    else:
+        Yd, Zd = B.TT(n=n, r=Yr), B.TT(n=n, r=Zr)
+        if case == "negative_opt":
+            opts = dict(max_rank=-1)
+        elif case == "bad_precision":
+            opts = dict(precision=7)
+        elif case == "bad_variant":
+            opts = dict(variant=5)
+    o = B.make_opts(**opts)
+    bound = (ctypes.c_int64 * 8)()
+    ws = ctypes.c_size_t()
+    st = B.load().tt_hadamard_recompress_plan(Yd.ref(), Zd.ref(), ctypes.byref(o), bound,
+                                              ctypes.byref(ws))
+    assert st == expect
+
+
+def test_execute_rejects_small_workspace_before_launching(lib):
+    # fake, never-dereferenced device addresses: the size check precedes any launch
+    n = [4, 4, 4]
+    Yd = B.TT(n=n, r=[1, 3, 3, 1])
+    Zd = B.TT(n=n, r=[1, 2, 2, 1])
+    Xd = B.TT(n=n, r=[1, 4, 4, 1])
+    base = 1 << 40
+    Yd.set_core_ptrs([base + k * (1 << 20) for k in range(3)])
+    Zd.set_core_ptrs([base + (3 + k) * (1 << 20) for k in range(3)])
+    Xd.set_core_ptrs([base + (6 + k) * (1 << 20) for k in range(3)])
+    o = B.make_opts(sketch_rank=4)
+    st = B.load().tt_hadamard_recompress(Yd.ref(), Zd.ref(), ctypes.byref(o), Xd.ref(),
+                                         ctypes.c_void_p(base + (1 << 30)), 16, None)
+    assert st == 4
+    # misaligned workspace
+    st = B.load().tt_hadamard_recompress(Yd.ref(), Zd.ref(), ctypes.byref(o), Xd.ref(),
+                                         ctypes.c_void_p(base + (1 << 30) + 8), 1 << 30, None)
+    assert st == 4
+    # output aliasing an input core
+    Xd.set_core_ptrs([base, base + (7 << 20), base + (8 << 20)])
+    st = B.load().tt_hadamard_recompress(Yd.ref(), Zd.ref(), ctypes.byref(o), Xd.ref(),
+                                         ctypes.c_void_p(base + (1 << 30)), 1 << 30, None)
+    assert st == 1
+
+
+def test_round_and_dot_plans(lib):
+    n = [5, 6, 7]
+    Ad = B.TT(n=n, r=[1, 4, 9, 1])
+    bound = (ctypes.c_int64 * 4)()
+    ws = ctypes.c_size_t()
+    assert B.load().tt_round_plan(Ad.ref(), 0, 1e-8, bound, ctypes.byref(ws)) == 0
+    assert [int(v) for v in bound] == [1, 4, 9, 1]
+    assert ws.value > 0
+    Bd = B.TT(n=n, r=[1, 2, 3, 1])
+    assert B.load().tt_dot_plan(Ad.ref(), Bd.ref(), ctypes.byref(ws)) == 0
+    Cd = B.TT(n=[5, 6, 8], r=[1, 2, 3, 1])
+    assert B.load().tt_dot_plan(Ad.ref(), Cd.ref(), ctypes.byref(ws)) == 1
