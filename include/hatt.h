@@ -161,6 +161,12 @@ int tt_sketch_tt(int32_t d, const int64_t *n, const int64_t *ell, uint64_t seed,
 int tt_philox4x32_10(const uint32_t *ctr, uint32_t key0, uint32_t key1, uint32_t *out,
                      int64_t count, void *stream);
 
+/* Number of CUDA kernels this library has enqueued in the calling process
+ * since it was loaded (all entry points, all threads). A diagnostic with no
+ * counterpart in the paper: the difference around a call is that call's
+ * launch count. Host only; never fails. */
+int64_t tt_launch_count(void);
+
 /* Static description of a status code (never NULL). */
 const char *tt_status_string(int status);
 

@@ -52,7 +52,7 @@ _lib = None
 
 EXPORTS = ("tt_hadamard_recompress_plan", "tt_hadamard_recompress", "tt_round_plan", "tt_round",
            "tt_dot_plan", "tt_dot", "tt_norm", "tt_sketch_tt", "tt_philox4x32_10",
-           "tt_status_string")
+           "tt_launch_count", "tt_status_string")
 
 
 def load(path: Optional[str] = None):
@@ -83,11 +83,18 @@ def load(path: Optional[str] = None):
     lib.tt_sketch_tt.argtypes = [ctypes.c_int32, P(ctypes.c_int64), P(ctypes.c_int64),
                                  ctypes.c_uint64, ctypes.c_uint32, P(ctypes.c_void_p), vp]
     lib.tt_philox4x32_10.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint32, vp, ctypes.c_int64, vp]
+    lib.tt_launch_count.restype = ctypes.c_int64
+    lib.tt_launch_count.argtypes = []
     for name in EXPORTS:
         getattr(lib, name)
     if path is None:
         _lib = lib
     return lib
+
+
+def launch_count() -> int:
+    """Kernels enqueued by libhatt in this process so far."""
+    return int(load().tt_launch_count())
 
 
 def status_string(status: int) -> str:
@@ -108,7 +115,8 @@ class TT:
     """Host-side descriptor (tt_t) of a TT given as a list of CUDA float64 cores
     of shapes (r_k, n_k, r_{k+1}), or of shapes only (cores=None)."""
 
-    def __init__(self, cores: Optional[Sequence[torch.Tensor]] = None, n=None, r=None):
+    def __init__(self, cores: Optional[Sequence[torch.Tensor]] = None, n=None, r=None,
+                 pinned_ranks: bool = False):
         if cores is not None:
             for c in cores:
                 if c.dtype != torch.float64 or not c.is_cuda or not c.is_contiguous():
@@ -117,7 +125,14 @@ class TT:
             r = [int(cores[0].shape[0])] + [int(c.shape[2]) for c in cores]
         self.d = len(n)
         self.n_arr = (ctypes.c_int64 * self.d)(*n)
-        self.r_arr = (ctypes.c_int64 * (self.d + 1))(*r)
+        if pinned_ranks:
+            # page-locked rank array: the library's device-to-host rank copy is
+            # then asynchronous and can be captured in a CUDA graph
+            self.r_pinned = torch.tensor(list(r), dtype=torch.int64).pin_memory()
+            self.r_arr = ctypes.cast(self.r_pinned.data_ptr(), ctypes.POINTER(ctypes.c_int64))
+        else:
+            self.r_pinned = None
+            self.r_arr = (ctypes.c_int64 * (self.d + 1))(*r)
         self.core_arr = (ctypes.c_void_p * self.d)()
         self.cores = list(cores) if cores is not None else None
         if cores is not None:
@@ -135,7 +150,7 @@ class TT:
 
     @property
     def r(self):
-        return [int(v) for v in self.r_arr]
+        return [int(self.r_arr[k]) for k in range(self.d + 1)]
 
     def ref(self):
         return ctypes.byref(self.s)
@@ -169,8 +184,9 @@ class HadamardRecompressor:
         b = [int(v) for v in self.bound]
         self.out_bufs = [torch.empty(b[k] * n[k] * b[k + 1], dtype=torch.float64, device=dev)
                          for k in range(d)]
-        self.Xd = TT(n=n, r=b)
+        self.Xd = TT(n=n, r=b, pinned_ranks=True)
         self.Xd.set_core_ptrs([t.data_ptr() for t in self.out_bufs])
+        self.graph = None
 
     def rebind(self, Y: Sequence[torch.Tensor], Z: Sequence[torch.Tensor]):
         """Point at new input cores of the same shapes."""
@@ -182,6 +198,24 @@ class HadamardRecompressor:
                                            self.Xd.ref(), ctypes.c_void_p(self.workspace.data_ptr()),
                                            self.workspace_bytes, _stream_ptr(stream))
         _check("tt_hadamard_recompress", st)
+
+    def capture(self):
+        """Capture one call in a CUDA graph (the library's launch sequence is
+        fixed and allocation-free); replay with `replay()`."""
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.run(s)                      # warm-up outside capture
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.run()
+        self.graph = g
+        return g
+
+    def replay(self):
+        self.graph.replay()
 
     def result(self) -> List[torch.Tensor]:
         """Output cores as views (call after the stream has completed)."""

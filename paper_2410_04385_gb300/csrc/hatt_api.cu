@@ -7,6 +7,7 @@
 // the caller's workspace identically and enqueues the kernels on the caller's
 // stream. No device memory is allocated and the stream is never synchronized.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <vector>
 
@@ -15,6 +16,14 @@
 
 using hatt::Gemm;
 typedef long long ll;
+
+namespace hatt {
+namespace {
+std::atomic<long long> g_launches{0};
+}
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace hatt
 
 namespace {
 
@@ -740,6 +749,8 @@ int tt_sketch_tt(int32_t d, const int64_t *n, const int64_t *ell, uint64_t seed,
   }
   return from_cuda(hatt::sketch_fill_ptrs(d, n, ell, seed, pair, cores, (cudaStream_t)stream));
 }
+
+int64_t tt_launch_count(void) { return (int64_t)hatt::launch_count(); }
 
 int tt_philox4x32_10(const uint32_t *ctr, uint32_t key0, uint32_t key1, uint32_t *out,
                      int64_t count, void *stream) {

@@ -11,6 +11,11 @@
 namespace hatt {
 
 constexpr int kMaxSmall = 128;   // TT_MAX_SMALL_RANK
+
+// Process-wide count of kernels enqueued by this library (each launch site
+// calls note_launch once).
+void note_launch();
+long long launch_count();
 constexpr int kMaxOrder = 512;   // largest d handled by the parameter tables
 
 // ------------------------------------------------------------------ GEMM ---

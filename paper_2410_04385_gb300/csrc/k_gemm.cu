@@ -1,14 +1,21 @@
 // Batched, arbitrarily strided FP64 GEMM for the small contractions of HaTT.
 //
-// On GB300 the FP64 pipe delivers ~1.2 TFLOP/s (about two DFMA lanes per SM
-// per clock) against ~73 TFLOP/s of FP32, so an FP64 contraction is bound by
-// DFMA issue, not by memory: a 256-thread block with a 4x4 (or smaller)
-// register tile and 16-deep shared-memory staging keeps the FP64 pipe fed.
-// What matters is that every launch covers all 152 SMs: the planner picks the
-// tile that wastes the fewest lanes and splits K until the grid has at least
-// two blocks per SM. Split-K partial sums are reduced in a fixed order by a
-// second kernel (no atomics), so results are bitwise reproducible.
+// On GB300 the FP64 pipe delivers ~1.2 TFLOP/s, about two DFMA lanes per SM
+// per clock, against ~73 TFLOP/s of FP32. A warp-wide DFMA therefore occupies
+// the SM's FP64 unit for ~16 clocks while the two shared-memory operand loads
+// it needs take ~3 wavefronts: an FP64 contraction is bound by DFMA issue, and
+// register blocking buys nothing. What costs time is every padded output lane
+// and every idle SM. So:
+//   * a block computes a bm x bn output tile of any shape (bm, bn <= 128,
+//     bm*bn <= 4096), its outputs dealt linearly to 256 threads; tiles are
+//     chosen to divide M and N (e.g. 80 x 50 for a 1600 x 50 product), so
+//     almost no lane computes padding;
+//   * K is split until the grid has about four blocks per SM (wave
+//     quantization < 25%); split-K partial sums are reduced in a fixed order by
+//     a second kernel (no atomics), so results are bitwise reproducible.
 #include <algorithm>
+#include <mutex>
+#include <vector>
 #include "hatt_internal.cuh"
 
 namespace hatt {
@@ -16,21 +23,22 @@ namespace {
 
 constexpr int kBK = 16;
 constexpr int kThreads = 256;
-constexpr int kTargetBlocks = 2 * 152;
+constexpr int kMaxTile = 128;            // bm, bn <= kMaxTile
+constexpr int kMaxOut = 16;              // outputs per thread -> bm*bn <= 4096
+constexpr int kTargetBlocks = 4 * 152;
 
 struct Launch {
-  int bm, bn, tiles_m, tiles_n, ksplit, kchunk;
+  int bm, bn, tiles_m, tiles_n, ksplit, kchunk, out;
 };
 
-template <int BM, int BN>
+template <int OUT>
 __global__ void __launch_bounds__(kThreads)
-gemm_f64_kernel(Gemm g, int tiles_n, int tiles_m, int ksplit, int kchunk, double *partial) {
-  constexpr int TM = BM / 16, TN = BN / 16;
+gemm_f64_kernel(Gemm g, int bm, int bn, int tiles_n, int tiles_m, int ksplit, int kchunk,
+                double *partial) {
   if (g.skip_dev && *g.skip_dev) return;
-  __shared__ double As[kBK][BM + 1];
-  __shared__ double Bs[kBK][BN + 1];
+  __shared__ double As[kBK][kMaxTile + 1];
+  __shared__ double Bs[kBK][kMaxTile + 1];
   const int tid = threadIdx.x;
-  const int tx = tid % 16, ty = tid / 16;
   // 1-D grid: block -> (n tile, m tile, split, batch), n tile fastest
   long long blk = blockIdx.x;
   const int tn_i = (int)(blk % tiles_n); blk /= tiles_n;
@@ -40,43 +48,43 @@ gemm_f64_kernel(Gemm g, int tiles_n, int tiles_m, int ksplit, int kchunk, double
   const int b1 = b / g.bdiv, b2 = b % g.bdiv;
   const double *A = g.A + b1 * g.sA1 + b2 * g.sA2;
   const double *B = g.B + b1 * g.sB1 + b2 * g.sB2;
-  const int m0 = tm_i * BM, n0 = tn_i * BN;
+  const int m0 = tm_i * bm, n0 = tn_i * bn;
   const int kbeg = ks * kchunk;
   const int kend = min(g.K, kbeg + kchunk);
+  const int outs = bm * bn;
 
-  double acc[TM][TN];
+  int om[OUT], on[OUT];
+  double acc[OUT];
 #pragma unroll
-  for (int i = 0; i < TM; ++i)
-#pragma unroll
-    for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
+  for (int q = 0; q < OUT; ++q) {
+    const int o = tid + kThreads * q;
+    om[q] = (o < outs) ? o / bn : 0;
+    on[q] = (o < outs) ? o % bn : 0;
+    acc[q] = 0.0;
+  }
+  const int nq = (outs - tid + kThreads - 1) / kThreads;   // outputs this thread owns
 
   const bool a_kfast = (g.sAk == 1);
   const bool b_nfast = (g.sBn == 1);
   for (int kt = kbeg; kt < kend; kt += kBK) {
-    for (int e = tid; e < BM * kBK; e += kThreads) {
+    for (int e = tid; e < bm * kBK; e += kThreads) {
       int mm, kk;
-      if (a_kfast) { mm = e / kBK; kk = e % kBK; } else { kk = e / BM; mm = e % BM; }
+      if (a_kfast) { mm = e / kBK; kk = e % kBK; } else { kk = e / bm; mm = e % bm; }
       const int gm = m0 + mm, gk = kt + kk;
       As[kk][mm] = (gm < g.M && gk < kend) ? A[gm * g.sAm + gk * g.sAk] : 0.0;
     }
-    for (int e = tid; e < BN * kBK; e += kThreads) {
+    for (int e = tid; e < bn * kBK; e += kThreads) {
       int nn, kk;
-      if (b_nfast) { kk = e / BN; nn = e % BN; } else { nn = e / kBK; kk = e % kBK; }
+      if (b_nfast) { kk = e / bn; nn = e % bn; } else { nn = e / kBK; kk = e % kBK; }
       const int gn = n0 + nn, gk = kt + kk;
       Bs[kk][nn] = (gn < g.N && gk < kend) ? B[gk * g.sBk + gn * g.sBn] : 0.0;
     }
     __syncthreads();
-#pragma unroll
+#pragma unroll 4
     for (int kk = 0; kk < kBK; ++kk) {
-      double av[TM], bv[TN];
 #pragma unroll
-      for (int i = 0; i < TM; ++i) av[i] = As[kk][ty + 16 * i];
-#pragma unroll
-      for (int j = 0; j < TN; ++j) bv[j] = Bs[kk][tx + 16 * j];
-#pragma unroll
-      for (int i = 0; i < TM; ++i)
-#pragma unroll
-        for (int j = 0; j < TN; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+      for (int q = 0; q < OUT; ++q)
+        if (q < nq) acc[q] = fma(As[kk][om[q]], Bs[kk][on[q]], acc[q]);
     }
     __syncthreads();
   }
@@ -84,31 +92,23 @@ gemm_f64_kernel(Gemm g, int tiles_n, int tiles_m, int ksplit, int kchunk, double
   if (ksplit > 1) {
     double *P = partial + ((long long)b * ksplit + ks) * g.M * (long long)g.N;
 #pragma unroll
-    for (int i = 0; i < TM; ++i) {
-      const int gm = m0 + ty + 16 * i;
-      if (gm >= g.M) continue;
-#pragma unroll
-      for (int j = 0; j < TN; ++j) {
-        const int gn = n0 + tx + 16 * j;
-        if (gn < g.N) P[(long long)gm * g.N + gn] = acc[i][j];
-      }
+    for (int q = 0; q < OUT; ++q) {
+      if (q >= nq) break;
+      const int gm = m0 + om[q], gn = n0 + on[q];
+      if (gm < g.M && gn < g.N) P[(long long)gm * g.N + gn] = acc[q];
     }
     return;
   }
   const double alpha = g.alpha * (g.alpha_dev ? *g.alpha_dev : 1.0);
   double *C = g.C + b1 * g.sC1 + b2 * g.sC2;
 #pragma unroll
-  for (int i = 0; i < TM; ++i) {
-    const int gm = m0 + ty + 16 * i;
-    if (gm >= g.M) continue;
-#pragma unroll
-    for (int j = 0; j < TN; ++j) {
-      const int gn = n0 + tx + 16 * j;
-      if (gn >= g.N) continue;
-      double *c = C + gm * g.sCm + gn * g.sCn;
-      const double v = alpha * acc[i][j];
-      *c = (g.beta != 0.0) ? fma(g.beta, *c, v) : v;
-    }
+  for (int q = 0; q < OUT; ++q) {
+    if (q >= nq) break;
+    const int gm = m0 + om[q], gn = n0 + on[q];
+    if (gm >= g.M || gn >= g.N) continue;
+    double *c = C + gm * g.sCm + gn * g.sCn;
+    const double v = alpha * acc[q];
+    *c = (g.beta != 0.0) ? fma(g.beta, *c, v) : v;
   }
 }
 
@@ -133,46 +133,102 @@ gemm_reduce_kernel(Gemm g, int ksplit, const double *partial) {
   }
 }
 
-int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+long long ceil_div(long long a, long long b) { return (a + b - 1) / b; }
 
-Launch plan(const Gemm &g) {
-  static const int sizes[3] = {16, 32, 64};
-  Launch best{64, 64, 0, 0, 1, 0};
-  double best_cost = 1e300;
-  for (int bm : sizes) {
-    for (int bn : sizes) {
-      const int tm = ceil_div(g.M, bm), tn = ceil_div(g.N, bn);
-      // padded lanes issue DFMAs too: cost = padded outputs; prefer bigger tiles on ties
-      const double cost = (double)tm * bm * tn * bn * (1.0 + 0.02 * (64.0 / bm + 64.0 / bn));
-      if (cost < best_cost) {
-        best_cost = cost;
-        best.bm = bm;
-        best.bn = bn;
-        best.tiles_m = tm;
-        best.tiles_n = tn;
-      }
+// Tile edge for a dimension X with edge cap `cap`: X itself if it fits, else
+// the edge in [cap/2, cap] with the least padding (larger on ties).
+int tile_edge(int X, int cap) {
+  if (X <= cap) return X;
+  int best = cap;
+  long long best_pad = ceil_div(X, cap) * cap;
+  for (int t = cap - 1; t >= std::max(1, cap / 2); --t) {
+    const long long pad = ceil_div(X, t) * t;
+    if (pad < best_pad) {
+      best_pad = pad;
+      best = t;
     }
   }
-  const long long blocks = (long long)best.tiles_m * best.tiles_n * g.batch;
-  int ksplit = 1;
-  if (blocks < kTargetBlocks && g.K > 4 * kBK) {
-    ksplit = ceil_div(kTargetBlocks, blocks);
-    ksplit = std::min(ksplit, ceil_div(g.K, 4 * kBK));   // at least 64 of K per split
-    ksplit = std::max(ksplit, 1);
-  }
-  int kchunk = ceil_div(g.K, ksplit);
-  kchunk = ceil_div(kchunk, kBK) * kBK;
-  ksplit = ceil_div(g.K, kchunk);
-  best.ksplit = std::max(ksplit, 1);
-  best.kchunk = std::max(kchunk, kBK);
   return best;
 }
 
-template <int BM, int BN>
+// Analytic launch model (clocks of the busiest SM) used to pick the tile and
+// the K split:
+//   FP64: a block's padded DFMAs at two lanes per clock, times the number of
+//         blocks the busiest SM receives (wave quantization over 152 SMs);
+//   latency: ~450 clocks per 16-deep k-tile (staging + two barriers), hidden
+//         up to 4 blocks per SM;
+//   split-K: the reduce kernel (~2500 clocks plus its partial-sum traffic).
+double model_clocks(const Gemm &g, int bm, int bn, long long ksplit) {
+  const long long tiles = ceil_div(g.M, bm) * ceil_div(g.N, bn) * (long long)g.batch;
+  const long long kchunk = ceil_div(ceil_div(g.K, ksplit), kBK) * kBK;
+  const long long blocks = tiles * ceil_div(g.K, kchunk);
+  const long long per_sm = ceil_div(blocks, 152);
+  const double dfma = (double)bm * bn * kchunk;
+  const double ktiles = (double)kchunk / kBK;
+  double t = per_sm * (dfma / 2.0) + ceil_div(per_sm, 4) * ktiles * 450.0 + 1500.0;
+  if (ksplit > 1) t += 2500.0 + (double)ksplit * g.M * g.N * g.batch * 8.0 / 2500.0;
+  return t;
+}
+
+Launch plan_search(const Gemm &g) {
+  static const int caps[5] = {128, 64, 32, 16, 8};
+  double best = 1e300;
+  Launch L{};
+  for (int cn : caps) {
+    const int bn = tile_edge(g.N, cn);
+    for (int cm : caps) {
+      const int bm = tile_edge(g.M, std::min(cm, kThreads * kMaxOut / bn));
+      const long long tiles = ceil_div(g.M, bm) * ceil_div(g.N, bn) * (long long)g.batch;
+      const long long kmax = ceil_div(g.K, kBK);
+      long long cands[12];
+      int nc = 0;
+      for (long long s = 1; s <= kmax && nc < 10; s *= 2) cands[nc++] = s;
+      cands[nc++] = std::min(kmax, std::max<long long>(1, ceil_div(kTargetBlocks, tiles)));
+      cands[nc++] = std::min(kmax, std::max<long long>(1, ceil_div(152, tiles)));
+      for (int i = 0; i < nc; ++i) {
+        const double t = model_clocks(g, bm, bn, cands[i]);
+        if (t < best) {
+          best = t;
+          L.bm = bm;
+          L.bn = bn;
+          L.ksplit = (int)cands[i];
+        }
+      }
+    }
+  }
+  L.tiles_m = (int)ceil_div(g.M, L.bm);
+  L.tiles_n = (int)ceil_div(g.N, L.bn);
+  const int need = (int)ceil_div((long long)L.bm * L.bn, kThreads);
+  L.out = need <= 1 ? 1 : need <= 2 ? 2 : need <= 4 ? 4 : need <= 8 ? 8 : need <= 12 ? 12 : 16;
+  const long long kchunk = ceil_div(ceil_div(g.K, L.ksplit), kBK) * kBK;
+  L.kchunk = (int)std::max<long long>(kchunk, kBK);
+  L.ksplit = (int)ceil_div(g.K, L.kchunk);
+  return L;
+}
+
+// Plans are cached per shape (the HaTT sequence repeats a few dozen shapes).
+Launch plan(const Gemm &g) {
+  struct Entry { int M, N, K, batch; Launch L; };
+  static std::mutex mu;
+  static std::vector<Entry> cache;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    for (const Entry &e : cache)
+      if (e.M == g.M && e.N == g.N && e.K == g.K && e.batch == g.batch) return e.L;
+  }
+  const Launch L = plan_search(g);
+  std::lock_guard<std::mutex> lock(mu);
+  if (cache.size() < 4096) cache.push_back({g.M, g.N, g.K, g.batch, L});
+  return L;
+}
+
+template <int OUT>
 void launch_tile(const Gemm &g, const Launch &L, double *scratch, cudaStream_t st) {
   const long long blocks = (long long)L.tiles_n * L.tiles_m * L.ksplit * g.batch;
-  gemm_f64_kernel<BM, BN><<<(unsigned)blocks, kThreads, 0, st>>>(g, L.tiles_n, L.tiles_m,
-                                                                 L.ksplit, L.kchunk, scratch);
+  gemm_f64_kernel<OUT><<<(unsigned)blocks, kThreads, 0, st>>>(g, L.bm, L.bn, L.tiles_n,
+                                                             L.tiles_m, L.ksplit, L.kchunk,
+                                                             scratch);
+  note_launch();
 }
 
 }  // namespace
@@ -192,22 +248,20 @@ cudaError_t gemm_f64(const Gemm &g, double *scratch, cudaStream_t st) {
   if (L.ksplit > 1 && scratch == nullptr) return cudaErrorInvalidValue;
   if ((long long)L.tiles_n * L.tiles_m * L.ksplit * g.batch >= (1LL << 31))
     return cudaErrorInvalidConfiguration;
-  switch (L.bm * 100 + L.bn) {
-    case 1616: launch_tile<16, 16>(g, L, scratch, st); break;
-    case 1632: launch_tile<16, 32>(g, L, scratch, st); break;
-    case 1664: launch_tile<16, 64>(g, L, scratch, st); break;
-    case 3216: launch_tile<32, 16>(g, L, scratch, st); break;
-    case 3232: launch_tile<32, 32>(g, L, scratch, st); break;
-    case 3264: launch_tile<32, 64>(g, L, scratch, st); break;
-    case 6416: launch_tile<64, 16>(g, L, scratch, st); break;
-    case 6432: launch_tile<64, 32>(g, L, scratch, st); break;
-    default:   launch_tile<64, 64>(g, L, scratch, st); break;
+  switch (L.out) {
+    case 1: launch_tile<1>(g, L, scratch, st); break;
+    case 2: launch_tile<2>(g, L, scratch, st); break;
+    case 4: launch_tile<4>(g, L, scratch, st); break;
+    case 8: launch_tile<8>(g, L, scratch, st); break;
+    case 12: launch_tile<12>(g, L, scratch, st); break;
+    default: launch_tile<16>(g, L, scratch, st); break;
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || L.ksplit == 1) return e;
   const long long total = (long long)g.M * g.N * g.batch;
   const int blocks = (int)std::min<long long>((total + kThreads - 1) / kThreads, 4 * 152);
   gemm_reduce_kernel<<<blocks, kThreads, 0, st>>>(g, L.ksplit, scratch);
+  note_launch();
   return cudaGetLastError();
 }
 

@@ -181,6 +181,7 @@ cudaError_t sketch_fill(const SketchTable &t, double *base, cudaStream_t st) {
   const long long total = t.offset[t.d];
   if (total <= 0) return cudaSuccess;
   sketch_kernel<<<grid_for(total), kThreads, 0, st>>>(t, base);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -191,6 +192,7 @@ cudaError_t sketch_fill_ptrs(int d, const int64_t *n, const int64_t *ell, uint64
     if (total <= 0) continue;
     sketch_core_kernel<<<grid_for(total), kThreads, 0, st>>>(
         cores[k], (int)ell[k], (int)n[k], (int)ell[k + 1], (uint32_t)k, pair, seed);
+    note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -201,6 +203,7 @@ cudaError_t philox_raw(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *
                        long long count, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
   philox_raw_kernel<<<grid_for(count), kThreads, 0, st>>>(ctr, k0, k1, out, count);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -208,6 +211,7 @@ cudaError_t inv_norm(const double *x, long long count, double *out, double *part
                      unsigned int *ticket, cudaStream_t st) {
   const int blocks = (int)std::max<long long>(1, std::min<long long>((count + kThreads - 1) / kThreads, 2 * 152));
   inv_norm_kernel<<<blocks, kThreads, 0, st>>>(x, count, out, partials, ticket);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -215,12 +219,14 @@ cudaError_t pkp_first(const double *Y, const double *Z, int n, int r1, int s1, d
                       cudaStream_t st) {
   const long long total = (long long)n * r1 * s1;
   pkp_first_kernel<<<grid_for(total), kThreads, 0, st>>>(Y, Z, n, r1, s1, C);
+  note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t set_value(double *x, long long count, double v, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
   set_kernel<<<grid_for(count), kThreads, 0, st>>>(x, count, v);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -228,12 +234,14 @@ cudaError_t set_identity(double *X, int m, cudaStream_t st) {
   const long long total = (long long)m * m;
   if (total <= 0) return cudaSuccess;
   eye_kernel<<<grid_for(total), kThreads, 0, st>>>(X, m);
+  note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t copy_f64(const double *src, double *dst, long long count, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
   copy_kernel<<<grid_for(count), kThreads, 0, st>>>(src, dst, count);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -241,11 +249,13 @@ cudaError_t compact_core(const double *src, double *dst, int la, int n, int lb,
                          const long long *ranks_dev, int k, cudaStream_t st) {
   const long long total = (long long)la * n * lb;
   compact_kernel<<<grid_for(total), kThreads, 0, st>>>(src, dst, la, n, lb, ranks_dev, k);
+  note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t sqrt_scalar(const double *x, double *out, cudaStream_t st) {
   sqrt_kernel<<<1, 1, 0, st>>>(x, out);
+  note_launch();
   return cudaGetLastError();
 }
 

@@ -29,15 +29,46 @@ constexpr int kPasses = 4;
 constexpr int kCholThreads = 256;
 constexpr int kTrmmThreads = 256;
 constexpr int kTrmmRows = 16;
+constexpr size_t kCholSmemMax = 200 * 1024;   // dynamic shared memory of the Cholesky block
 
-// flags[0]: converged; flags[1]: number of shifted passes; flags[2]: passes run
+// G (c x (c+1)) plus, when it fits, R^{-1} (c x c)
+__host__ __device__ constexpr size_t chol_smem_doubles(int c, bool with_inv) {
+  return (size_t)c * (c + 1) + (with_inv ? (size_t)c * c : 0);
+}
+
+// 1/sqrt(x) for finite x > 0: range reduction x = m 2^e with e even, an FP32
+// seed for m, then two Newton-Raphson steps y <- y (3 - m y^2) / 2 in FP64
+// (each squares the relative error: 2^-23 -> 2^-46 -> below FP64 rounding).
+// A handful of dependent FP64 multiply-adds instead of the long FP64 sqrt and
+// divide sequences, which sit on the Cholesky critical path once per column.
+__device__ __forceinline__ double rsqrt_newton(double x) {
+  int e;
+  double m = frexp(x, &e);                 // m in [0.5, 1)
+  if (e & 1) { m *= 2.0; e -= 1; }         // m in [0.5, 2), e even
+  double y = (double)rsqrtf((float)m);
+  y = y * fma(-0.5 * m, y * y, 1.5);
+  y = y * fma(-0.5 * m, y * y, 1.5);
+  return ldexp(y, -e / 2);
+}
+
+// Flag words (reset at the start of every QR):
+//   flags[0] done:      no further pass is needed (read by the Gram GEMM and
+//                       this kernel at the start of every later pass)
+//   flags[1] skip_trmm: the S <- S R^{-1} launch of this pass is a no-op
+//   flags[2] passes applied, flags[3] shifted passes (diagnostics)
 __global__ void __launch_bounds__(kCholThreads)
-chol_inv_kernel(const double *Gg, double *Rinv, int c, int m, int *flags) {
-  if (flags[0]) return;
+chol_inv_kernel(const double *Gg, double *Rinv_g, int c, int m, int *flags) {
+  if (flags[0]) {
+    if (threadIdx.x == 0) flags[1] = 1;
+    return;
+  }
   extern __shared__ double sm[];
   const int ld = c + 1;
-  double *G = sm;                       // c x ld, upper triangle becomes R
+  double *G = sm;                                   // c x ld, upper triangle becomes R
+  const bool inv_in_smem = chol_smem_doubles(c, true) * sizeof(double) <= kCholSmemMax;
+  double *Ri = inv_in_smem ? sm + c * ld : Rinv_g;  // R^{-1}, ld = c
   __shared__ double s_diag_max, s_trace, s_dev;
+  __shared__ double s_rinv[kMaxSmall];              // 1 / R_jj
   __shared__ int s_fail;
   const int tid = threadIdx.x;
 
@@ -45,8 +76,6 @@ chol_inv_kernel(const double *Gg, double *Rinv, int c, int m, int *flags) {
   // exactly zero (a zero column stays zero through every pass). The test is
   // absolute on purpose: S of any scale (HaTT sketches of long chains reach
   // 1e-20 and below) is never mistaken for a converged basis.
-  if (tid == 0) { s_dev = 0.0; s_diag_max = 0.0; s_trace = 0.0; }
-  __syncthreads();
   double dev = 0.0, dmax = 0.0, tr = 0.0;
   for (int e = tid; e < c * c; e += kCholThreads) {
     const int i = e / c, j = e % c;
@@ -60,7 +89,6 @@ chol_inv_kernel(const double *Gg, double *Rinv, int c, int m, int *flags) {
       dev = fmax(dev, fabs(v));
     }
   }
-  // block reductions (max of dev / dmax, sum of tr) through shared atomics on bit patterns
   {
     __shared__ double red[kCholThreads];
     red[tid] = dev;
@@ -89,11 +117,18 @@ chol_inv_kernel(const double *Gg, double *Rinv, int c, int m, int *flags) {
     __syncthreads();
   }
   const double u = 1.1102230246251565e-16;
-  if (s_dev <= 8.0 * c * u) {
-    if (tid == 0) flags[0] = 1;
+  if (s_dev <= 8.0 * c * u) {              // already orthonormal: nothing to apply
+    if (tid == 0) { flags[0] = 1; flags[1] = 1; }
     return;
   }
-  if (tid == 0) flags[2] += 1;
+  if (tid == 0) {
+    flags[1] = 0;
+    flags[2] += 1;
+    // ||G - I||_max <= 0.1/c puts every eigenvalue of G in [0.9, 1.1]
+    // (Gerschgorin): one more Cholesky QR pass orthonormalizes to working
+    // accuracy, so this pass is the last one
+    if (s_dev <= 0.1 / c) flags[0] = 1;
+  }
 
   // -- Cholesky: first unshifted, then shifted if a pivot is not safely positive
   for (int attempt = 0; attempt < 2; ++attempt) {
@@ -105,7 +140,7 @@ chol_inv_kernel(const double *Gg, double *Rinv, int c, int m, int *flags) {
         const int i = e / c, j = e % c;
         G[i * ld + j] = Gg[e] + (i == j ? shift : 0.0);
       }
-      if (tid == 0) flags[1] += 1;
+      if (tid == 0) flags[3] += 1;
     }
     if (tid == 0) s_fail = 0;
     __syncthreads();
@@ -117,12 +152,14 @@ chol_inv_kernel(const double *Gg, double *Rinv, int c, int m, int *flags) {
           if (attempt == 0) s_fail = 1;
           piv = fmax(shift, 1e-300);          // shifted attempt: never divide by zero
         }
-        G[j * ld + j] = sqrt(piv);
+        const double y = rsqrt_newton(piv);
+        G[j * ld + j] = piv * y;              // R_jj = sqrt(piv)
+        s_rinv[j] = y;
       }
       __syncthreads();
       if (s_fail) break;
-      const double rjj = G[j * ld + j];
-      for (int l = j + 1 + tid; l < c; l += kCholThreads) G[j * ld + l] /= rjj;
+      const double yj = s_rinv[j];
+      for (int l = j + 1 + tid; l < c; l += kCholThreads) G[j * ld + l] *= yj;
       __syncthreads();
       const int rem = c - j - 1;
       for (int e = tid; e < rem * rem; e += kCholThreads) {
@@ -135,28 +172,28 @@ chol_inv_kernel(const double *Gg, double *Rinv, int c, int m, int *flags) {
     if (!s_fail) break;
   }
 
-  // -- triangular inverse, row by row from the bottom: Rinv[i][j], j >= i.
-  // Rows of Rinv are written to global memory and read back by the same block
-  // (__syncthreads orders the block's global writes before later reads).
+  // -- triangular inverse, row by row from the bottom: Ri[i][j], j >= i
   for (int e = tid; e < c * c; e += kCholThreads) {
     const int i = e / c, j = e % c;
-    if (j < i) Rinv[e] = 0.0;
+    if (j < i) Ri[e] = 0.0;
   }
   for (int i = c - 1; i >= 0; --i) {
-    const double rii = G[i * ld + i];
+    const double yi = s_rinv[i];
     for (int j = i + tid; j < c; j += kCholThreads) {
       double s = (j == i) ? 1.0 : 0.0;
-      for (int l = i + 1; l <= j; ++l) s = fma(-G[i * ld + l], Rinv[l * c + j], s);
-      Rinv[i * c + j] = s / rii;
+      for (int l = i + 1; l <= j; ++l) s = fma(-G[i * ld + l], Ri[l * c + j], s);
+      Ri[i * c + j] = s * yi;
     }
     __syncthreads();
   }
+  if (inv_in_smem)
+    for (int e = tid; e < c * c; e += kCholThreads) Rinv_g[e] = Ri[e];
 }
 
 // S[r][j] <- sum_{i <= j} S[r][i] Rinv[i][j], rows owned by one block (in place).
 __global__ void __launch_bounds__(kTrmmThreads)
 trmm_rows_kernel(double *S, int m, int c, long long ldS, const double *Rinv, const int *flags) {
-  if (flags[0]) return;
+  if (flags[1]) return;
   extern __shared__ double sm[];
   double *Rs = sm;                       // c x c
   double *Xs = sm + c * c;               // kTrmmRows x c
@@ -176,7 +213,10 @@ trmm_rows_kernel(double *S, int m, int c, long long ldS, const double *Rinv, con
   }
 }
 
-size_t chol_smem(int c) { return (size_t)c * (c + 1) * sizeof(double); }
+size_t chol_smem(int c) {
+  const size_t with_inv = chol_smem_doubles(c, true) * sizeof(double);
+  return with_inv <= kCholSmemMax ? with_inv : chol_smem_doubles(c, false) * sizeof(double);
+}
 size_t trmm_smem(int c) { return (size_t)(c * c + kTrmmRows * c) * sizeof(double); }
 
 Gemm gram_desc(double *S, int m, int c, long long ldS, double *G, const int *flags) {
@@ -203,10 +243,10 @@ cudaError_t qr_inplace(double *S, int m, int c, long long ldS, double *scratch, 
   double *G = scratch;
   double *Rinv = scratch + (size_t)c * c;
   double *gs = scratch + (size_t)2 * c * c;
-  cudaError_t e = cudaMemsetAsync(flags, 0, 3 * sizeof(int), st);
+  cudaError_t e = cudaMemsetAsync(flags, 0, 4 * sizeof(int), st);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)chol_smem(kMaxSmall));
+                           (int)kCholSmemMax);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(trmm_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)trmm_smem(kMaxSmall));
@@ -217,9 +257,11 @@ cudaError_t qr_inplace(double *S, int m, int c, long long ldS, double *scratch, 
     e = gemm_f64(gd, gs, st);
     if (e != cudaSuccess) return e;
     chol_inv_kernel<<<1, kCholThreads, chol_smem(c), st>>>(G, Rinv, c, m, flags);
+    note_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     trmm_rows_kernel<<<blocks, kTrmmThreads, trmm_smem(c), st>>>(S, m, c, ldS, Rinv, flags);
+    note_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -28,11 +28,23 @@
 namespace hatt {
 namespace {
 
-constexpr int kJacThreads = 512;
-constexpr int kMaxSweeps = 30;
+constexpr int kJacThreads = 256;
+constexpr int kMaxSweeps = 12;
 constexpr int kOaThreads = 1024;
 constexpr int kThreads = 256;
 constexpr int kRefineSteps = 3;
+
+// 1/x for finite nonzero x: x = m 2^e with |m| in [0.5, 1), FP32 seed for 1/m,
+// two Newton-Raphson steps y <- y (2 - m y) in FP64 (relative error 2^-23 ->
+// 2^-46 -> FP64 rounding). Cheaper on GB300's FP64 unit than an IEEE divide.
+__device__ __forceinline__ double rcp_newton(double x) {
+  int e;
+  const double m = frexp(x, &e);
+  double y = (double)__frcp_rn((float)m);
+  y = y * fma(-m, y, 2.0);
+  y = y * fma(-m, y, 2.0);
+  return ldexp(y, -e);
+}
 
 __device__ double block_sum(double v, double *red) {
   const int tid = threadIdx.x;
@@ -49,15 +61,21 @@ __device__ double block_sum(double v, double *red) {
 
 // Cyclic Jacobi (round-robin ordering, c/2 disjoint rotations per round) on
 // the trace-scaled Gram matrix in FP32. Output: U (c x c, FP64, columns =
-// eigenvectors sorted by decreasing eigenvalue).
+// eigenvectors sorted by decreasing eigenvalue). A round computes its c/2
+// rotations once, then applies both sides at once, 2 x 2 block by 2 x 2 block,
+// from one copy of A into the other (J^T A J restricted to the rows of pair j
+// and the columns of pair j' depends only on that block), so a round costs two
+// barriers. The result only seeds the FP64 refinement, which converges
+// quadratically from an off-diagonal mass of ~1e-7 of the total.
 __global__ void __launch_bounds__(kJacThreads)
 jacobi_eig32_kernel(const double *G, int c, double *U) {
   extern __shared__ float fs[];
   const int ld = c + 1;
-  float *A = fs;                 // c x ld
-  float *V = fs + c * ld;        // c x ld
-  float *rc = V + c * ld;        // rotation cosines   [c/2 + 1]
-  float *rs = rc + (c / 2 + 1);  // rotation sines
+  float *Ab0 = fs;                // c x ld
+  float *Ab1 = fs + c * ld;       // c x ld
+  float *V = fs + 2 * c * ld;     // c x ld
+  float *rc = V + c * ld;         // rotation cosines   [c/2 + 1]
+  float *rs = rc + (c / 2 + 1);   // rotation sines
   int *pp = (int *)(rs + (c / 2 + 1));
   int *pq = pp + (c / 2 + 1);
   __shared__ double red[kJacThreads];
@@ -69,14 +87,14 @@ jacobi_eig32_kernel(const double *G, int c, double *U) {
   const double scale = tr > 0.0 ? 1.0 / tr : 1.0;
   for (int e = tid; e < c * c; e += kJacThreads) {
     const int i = e / c, j = e % c;
-    A[i * ld + j] = (float)(0.5 * (G[i * c + j] + G[j * c + i]) * scale);
+    Ab0[i * ld + j] = (float)(0.5 * (G[i * c + j] + G[j * c + i]) * scale);
     V[i * ld + j] = (i == j) ? 1.0f : 0.0f;
   }
   __syncthreads();
+  float *A = Ab0, *An = Ab1;
   const int N = c + (c & 1);       // players of the round-robin (a dummy if c is odd)
   const int P = N / 2;
   for (int sweep = 0; sweep < kMaxSweeps && N > 1; ++sweep) {
-    // convergence: off-diagonal mass relative to the total
     double off = 0.0, tot = 0.0;
     for (int e = tid; e < c * c; e += kJacThreads) {
       const int i = e / c, j = e % c;
@@ -86,9 +104,10 @@ jacobi_eig32_kernel(const double *G, int c, double *U) {
     }
     off = block_sum(off, red);
     tot = block_sum(tot, red);
-    if (off <= 1e-13 * tot || tot == 0.0) break;
+    if (off <= 1e-7 * tot || tot == 0.0) break;
     for (int round = 0; round < N - 1; ++round) {
-      for (int j = tid; j < P; j += kJacThreads) {
+      if (tid < P) {
+        const int j = tid;
         int p, q;
         if (j == 0) { p = round % (N - 1); q = N - 1; }
         else { p = (round + j) % (N - 1); q = (round - j + (N - 1)) % (N - 1); }
@@ -98,40 +117,45 @@ jacobi_eig32_kernel(const double *G, int c, double *U) {
           const float apq = A[p * ld + q];
           const float app = A[p * ld + p], aqq = A[q * ld + q];
           if (fabsf(apq) > 1e-30f && fabsf(apq) > 1e-9f * sqrtf(fabsf(app * aqq))) {
-            const float tau = (aqq - app) / (2.0f * apq);
-            const float t = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
-            cs = rsqrtf(1.0f + t * t);
+            const float tau = __fdividef(aqq - app, 2.0f * apq);
+            const float t = __fdividef(copysignf(1.0f, tau), fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f)));
+            cs = rsqrtf(fmaf(t, t, 1.0f));
             sn = t * cs;
           }
         }
         rc[j] = cs; rs[j] = sn; pp[j] = p; pq[j] = q;
       }
       __syncthreads();
-      // columns: A <- A J, V <- V J
-      for (int e = tid; e < P * c; e += kJacThreads) {
-        const int j = e / c, i = e % c;
+      // A' = J^T A J block by block: rows of pair j, columns of pair jj
+      for (int t = tid; t < P * P; t += kJacThreads) {
+        const int j = t / P, jj = t % P;
+        const int p = pp[j], q = pq[j], p2 = pp[jj], q2 = pq[jj];
+        const float cs = rc[j], sn = rs[j], cs2 = rc[jj], sn2 = rs[jj];
+        const bool hq = q < c, hq2 = q2 < c;
+        const float a = A[p * ld + p2];
+        const float b = hq2 ? A[p * ld + q2] : 0.0f;
+        const float cc = hq ? A[q * ld + p2] : 0.0f;
+        const float dd = (hq && hq2) ? A[q * ld + q2] : 0.0f;
+        const float a1 = cs2 * a - sn2 * b, b1 = sn2 * a + cs2 * b;
+        const float c1 = cs2 * cc - sn2 * dd, d1 = sn2 * cc + cs2 * dd;
+        An[p * ld + p2] = cs * a1 - sn * c1;
+        if (hq2) An[p * ld + q2] = cs * b1 - sn * d1;
+        if (hq) An[q * ld + p2] = sn * a1 + cs * c1;
+        if (hq && hq2) An[q * ld + q2] = sn * b1 + cs * d1;
+      }
+      // V <- V J (columns of each pair, in place; pairs are disjoint)
+      for (int t = tid; t < P * c; t += kJacThreads) {
+        const int j = t / c, i = t % c;
         const int p = pp[j], q = pq[j];
-        if (q >= c || rs[j] == 0.0f) continue;
-        const float cs = rc[j], sn = rs[j];
-        const float a = A[i * ld + p], b = A[i * ld + q];
-        A[i * ld + p] = cs * a - sn * b;
-        A[i * ld + q] = sn * a + cs * b;
+        const float sn = rs[j];
+        if (q >= c || sn == 0.0f) continue;
+        const float cs = rc[j];
         const float va = V[i * ld + p], vb = V[i * ld + q];
         V[i * ld + p] = cs * va - sn * vb;
         V[i * ld + q] = sn * va + cs * vb;
       }
       __syncthreads();
-      // rows: A <- J^T A
-      for (int e = tid; e < P * c; e += kJacThreads) {
-        const int j = e / c, l = e % c;
-        const int p = pp[j], q = pq[j];
-        if (q >= c || rs[j] == 0.0f) continue;
-        const float cs = rc[j], sn = rs[j];
-        const float a = A[p * ld + l], b = A[q * ld + l];
-        A[p * ld + l] = cs * a - sn * b;
-        A[q * ld + l] = sn * a + cs * b;
-      }
-      __syncthreads();
+      float *tmp = A; A = An; An = tmp;
     }
   }
   // sort eigenvalues (diagonal) in decreasing order; ties by index
@@ -184,7 +208,7 @@ oa_update_kernel(const double *UtU, const double *S, const double *G, int c, int
     const double r = (i == j ? 1.0 : 0.0) - UtU[e];
     double E;
     if (!orth_only && i != j && fabs(lam[i] - lam[j]) > delta)
-      E = (S[e] + lam[j] * r) / (lam[j] - lam[i]);
+      E = fma(lam[j], r, S[e]) * rcp_newton(lam[j] - lam[i]);
     else
       E = 0.5 * r;
     Eout[e] = E + (i == j ? 1.0 : 0.0);
@@ -306,7 +330,7 @@ __global__ void set_ranks_kernel(RankTable t, long long *ranks) {
 
 size_t jac_smem(int c) {
   const int P = c / 2 + 1;
-  return (size_t)2 * c * (c + 1) * sizeof(float) + 2 * P * sizeof(float) + 2 * P * sizeof(int);
+  return (size_t)3 * c * (c + 1) * sizeof(float) + 2 * P * sizeof(float) + 2 * P * sizeof(int);
 }
 
 struct Layout {
@@ -392,6 +416,7 @@ cudaError_t trunc_step(double *Xk, int la, int n, int lb, double *Xkm1, int lm, 
   HATT_TRY(cudaFuncSetAttribute(jacobi_eig32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)jac_smem(kMaxSmall)));
   jacobi_eig32_kernel<<<1, kJacThreads, jac_smem(la), st>>>(L.G, la, L.U0);
+  note_launch();
   HATT_TRY(cudaGetLastError());
   double *U = L.U0, *Un = L.U1;
   for (int it = 0; it <= kRefineSteps; ++it) {
@@ -402,21 +427,26 @@ cudaError_t trunc_step(double *Xk, int la, int n, int lb, double *Xkm1, int lm, 
       HATT_TRY(gemm_f64(g_tn(U, L.T, la, la, la, L.S, la), L.gs, st));
     }
     oa_update_kernel<<<1, kOaThreads, 0, st>>>(L.UtU, L.S, L.G, la, orth_only, L.E);
+    note_launch();
     HATT_TRY(cudaGetLastError());
     HATT_TRY(gemm_f64(g_nn(U, L.E, la, la, la, Un), L.gs, st));
     std::swap(U, Un);
   }
   HATT_TRY(gemm_f64(g_tn(U, Xk, la, N, N, L.B1, N), L.gs, st));
   rownorm_kernel<<<la, kThreads, 0, st>>>(L.B1, N, L.e);
+  note_launch();
   HATT_TRY(cudaGetLastError());
   rank_kernel<<<1, kThreads, 0, st>>>(L.e, la, cap, delta2_dev, ranks_dev, k, L.perm, L.sigma);
+  note_launch();
   HATT_TRY(cudaGetLastError());
   const long long tot = (long long)la * N;
   const int blocks = (int)std::min<long long>((tot + kThreads - 1) / kThreads, 8 * 152);
   newcore_kernel<<<blocks, kThreads, 0, st>>>(L.B1, la, N, L.perm, L.sigma, ranks_dev, k, Xk);
+  note_launch();
   HATT_TRY(cudaGetLastError());
   kmat_kernel<<<(la * la + kThreads - 1) / kThreads, kThreads, 0, st>>>(U, la, L.perm, L.sigma,
                                                                          ranks_dev, k, L.K);
+  note_launch();
   HATT_TRY(cudaGetLastError());
   HATT_TRY(gemm_f64(g_nn(Xkm1, L.K, mrows, la, la, L.tmp), L.gs, st));
   HATT_TRY(copy_f64(L.tmp, Xkm1, mrows * la, st));
@@ -428,6 +458,7 @@ cudaError_t trunc_delta2(const double *x, long long count, double tol, int d, do
                          double *partials, unsigned int *ticket, cudaStream_t st) {
   const int blocks = (int)std::max<long long>(1, std::min<long long>((count + kThreads - 1) / kThreads, 2 * 152));
   delta2_kernel<<<blocks, kThreads, 0, st>>>(x, count, tol, d, delta2_dev, partials, ticket);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -438,6 +469,7 @@ cudaError_t set_ranks(long long *ranks_dev, const long long *ranks_host, int cou
   t.count = count;
   for (int i = 0; i < count; ++i) t.r[i] = ranks_host[i];
   set_ranks_kernel<<<1, 256, 0, st>>>(t, ranks_dev);
+  note_launch();
   return cudaGetLastError();
 }
 

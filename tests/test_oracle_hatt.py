@@ -270,3 +270,17 @@ def test_speedup_closed_form_vs_randorth():
         ro = (d - 2) * n * (4 * r ** 2 * s ** 2 * l + 6 * r * s * l ** 2)
         sp = ro / flops.table41_hatt1(d, n, r, s, l)
         assert np.isclose(sp, (4 * r + 6) / 14)
+
+
+def test_package_cost_model_agrees_with_oracle_flop_model():
+    from paper_2410_04385_gb300 import costmodel
+    rng = np.random.default_rng(5)
+    for _ in range(5):
+        d = int(rng.integers(2, 12))
+        n = [int(v) for v in rng.integers(1, 40, size=d)]
+        r = [1] + [int(v) for v in rng.integers(1, 30, size=d - 1)] + [1]
+        s = [1] + [int(v) for v in rng.integers(1, 30, size=d - 1)] + [1]
+        ell = hatt.plan_ranks(n, r, s, int(rng.integers(1, 80)))
+        a = costmodel.hatt1_flops(n, r, s, ell)
+        b = flops.hatt1_flops(n, r, s, ell)
+        assert np.allclose(a, b, rtol=1e-12)
