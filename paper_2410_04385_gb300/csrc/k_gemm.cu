@@ -80,11 +80,21 @@ gemm_f64_kernel(Gemm g, int bm, int bn, int tiles_n, int tiles_m, int ksplit, in
       Bs[kk][nn] = (gn < g.N && gk < kend) ? B[gk * g.sBk + gn * g.sBn] : 0.0;
     }
     __syncthreads();
+    // exact depth: a ragged last k-tile issues no DFMAs on zero padding
+    const int kdepth = min(kBK, kend - kt);
+    if (kdepth == kBK) {
 #pragma unroll 4
-    for (int kk = 0; kk < kBK; ++kk) {
+      for (int kk = 0; kk < kBK; ++kk) {
 #pragma unroll
-      for (int q = 0; q < OUT; ++q)
-        if (q < nq) acc[q] = fma(As[kk][om[q]], Bs[kk][on[q]], acc[q]);
+        for (int q = 0; q < OUT; ++q)
+          if (q < nq) acc[q] = fma(As[kk][om[q]], Bs[kk][on[q]], acc[q]);
+      }
+    } else {
+      for (int kk = 0; kk < kdepth; ++kk) {
+#pragma unroll
+        for (int q = 0; q < OUT; ++q)
+          if (q < nq) acc[q] = fma(As[kk][om[q]], Bs[kk][on[q]], acc[q]);
+      }
     }
     __syncthreads();
   }
@@ -163,8 +173,8 @@ double model_clocks(const Gemm &g, int bm, int bn, long long ksplit) {
   const long long kchunk = ceil_div(ceil_div(g.K, ksplit), kBK) * kBK;
   const long long blocks = tiles * ceil_div(g.K, kchunk);
   const long long per_sm = ceil_div(blocks, 152);
-  const double dfma = (double)bm * bn * kchunk;
-  const double ktiles = (double)kchunk / kBK;
+  const double dfma = (double)bm * bn * std::min<long long>(kchunk, g.K);
+  const double ktiles = (double)ceil_div(std::min<long long>(kchunk, g.K), kBK);
   double t = per_sm * (dfma / 2.0) + ceil_div(per_sm, 4) * ktiles * 450.0 + 1500.0;
   if (ksplit > 1) t += 2500.0 + (double)ksplit * g.M * g.N * g.batch * 8.0 / 2500.0;
   return t;

@@ -71,6 +71,7 @@ chol_inv_kernel(const double *Gg, double *Rinv_g, int c, int m, int *flags) {
   __shared__ double s_rinv[kMaxSmall];              // 1 / R_jj
   __shared__ int s_fail;
   const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;           // 16 x 16 grid (kCholThreads = 256)
 
   // -- convergence test: G = I to working accuracy, except columns that are
   // exactly zero (a zero column stays zero through every pass). The test is
@@ -161,10 +162,10 @@ chol_inv_kernel(const double *Gg, double *Rinv_g, int c, int m, int *flags) {
       const double yj = s_rinv[j];
       for (int l = j + 1 + tid; l < c; l += kCholThreads) G[j * ld + l] *= yj;
       __syncthreads();
-      const int rem = c - j - 1;
-      for (int e = tid; e < rem * rem; e += kCholThreads) {
-        const int i = j + 1 + e / rem, l = j + 1 + e % rem;
-        if (l >= i) G[i * ld + l] = fma(-G[j * ld + i], G[j * ld + l], G[i * ld + l]);
+      // trailing update of the upper triangle on a 16 x 16 thread grid
+      for (int i = j + 1 + ty; i < c; i += 16) {
+        const double rji = G[j * ld + i];
+        for (int l = i + tx; l < c; l += 16) G[i * ld + l] = fma(-rji, G[j * ld + l], G[i * ld + l]);
       }
       __syncthreads();
     }
@@ -172,17 +173,22 @@ chol_inv_kernel(const double *Gg, double *Rinv_g, int c, int m, int *flags) {
     if (!s_fail) break;
   }
 
-  // -- triangular inverse, row by row from the bottom: Ri[i][j], j >= i
+  // -- triangular inverse, row by row from the bottom: Ri[i][j], j >= i.
+  // One warp per entry: the lanes split the dot product sum_l R_il Ri_lj and
+  // reduce with shuffles, so a row costs a few shuffle rounds instead of a
+  // dependent chain of up to c FP64 multiply-adds.
   for (int e = tid; e < c * c; e += kCholThreads) {
     const int i = e / c, j = e % c;
     if (j < i) Ri[e] = 0.0;
   }
+  const int warp = tid >> 5, lane = tid & 31;
   for (int i = c - 1; i >= 0; --i) {
     const double yi = s_rinv[i];
-    for (int j = i + tid; j < c; j += kCholThreads) {
-      double s = (j == i) ? 1.0 : 0.0;
-      for (int l = i + 1; l <= j; ++l) s = fma(-G[i * ld + l], Ri[l * c + j], s);
-      Ri[i * c + j] = s * yi;
+    for (int j = i + warp; j < c; j += kCholThreads / 32) {
+      double s = 0.0;
+      for (int l = i + 1 + lane; l <= j; l += 32) s = fma(G[i * ld + l], Ri[l * c + j], s);
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) Ri[i * c + j] = ((j == i) ? 1.0 - s : -s) * yi;
     }
     __syncthreads();
   }

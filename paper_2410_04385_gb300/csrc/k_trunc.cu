@@ -94,20 +94,30 @@ jacobi_eig32_kernel(const double *G, int c, double *U) {
   float *A = Ab0, *An = Ab1;
   const int N = c + (c & 1);       // players of the round-robin (a dummy if c is odd)
   const int P = N / 2;
+  // 16 x 16 thread grid: items are walked without integer division
+  const int tx = tid % 16, ty = tid / 16;
+  __shared__ float wsum[2][kJacThreads / 32];
   for (int sweep = 0; sweep < kMaxSweeps && N > 1; ++sweep) {
-    double off = 0.0, tot = 0.0;
-    for (int e = tid; e < c * c; e += kJacThreads) {
-      const int i = e / c, j = e % c;
-      const double v = A[i * ld + j];
-      tot += v * v;
-      if (i != j) off += v * v;
+    float offf = 0.0f, totf = 0.0f;
+    for (int i = ty; i < c; i += 16)
+      for (int j = tx; j < c; j += 16) {
+        const float v = A[i * ld + j];
+        totf = fmaf(v, v, totf);
+        if (i != j) offf = fmaf(v, v, offf);
+      }
+    for (int o = 16; o > 0; o >>= 1) {
+      offf += __shfl_xor_sync(0xffffffffu, offf, o);
+      totf += __shfl_xor_sync(0xffffffffu, totf, o);
     }
-    off = block_sum(off, red);
-    tot = block_sum(tot, red);
+    if ((tid & 31) == 0) { wsum[0][tid >> 5] = offf; wsum[1][tid >> 5] = totf; }
+    __syncthreads();
+    float off = 0.0f, tot = 0.0f;
+    for (int w = 0; w < kJacThreads / 32; ++w) { off += wsum[0][w]; tot += wsum[1][w]; }
+    __syncthreads();
     // squared off-diagonal mass <= 1e-11 of the total: a relative residual of
     // ~3e-6, from which three FP64 refinement steps reach working accuracy even
     // for closely spaced eigenvalues (FP32 reaches it in ~6 sweeps at c = 50)
-    if (off <= 1e-11 * tot || tot == 0.0) break;
+    if (off <= 1e-11f * tot || tot == 0.0f) break;
     for (int round = 0; round < N - 1; ++round) {
       if (tid < P) {
         const int j = tid;
@@ -120,9 +130,11 @@ jacobi_eig32_kernel(const double *G, int c, double *U) {
           const float apq = A[p * ld + q];
           const float app = A[p * ld + p], aqq = A[q * ld + q];
           if (fabsf(apq) > 1e-30f && fabsf(apq) > 1e-9f * sqrtf(fabsf(app * aqq))) {
-            const float tau = __fdividef(aqq - app, 2.0f * apq);
-            const float t = __fdividef(copysignf(1.0f, tau), fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f)));
-            cs = rsqrtf(fmaf(t, t, 1.0f));
+            // correctly rounded divide / sqrt: c^2 + s^2 = 1 to FP32 rounding,
+            // so rotations stay orthogonal and the stop test is reachable
+            const float tau = (aqq - app) / (2.0f * apq);
+            const float t = copysignf(1.0f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f)));
+            cs = 1.0f / sqrtf(fmaf(t, t, 1.0f));
             sn = t * cs;
           }
         }
@@ -130,32 +142,37 @@ jacobi_eig32_kernel(const double *G, int c, double *U) {
       }
       __syncthreads();
       // A' = J^T A J block by block: rows of pair j, columns of pair jj
-      for (int t = tid; t < P * P; t += kJacThreads) {
-        const int j = t / P, jj = t % P;
-        const int p = pp[j], q = pq[j], p2 = pp[jj], q2 = pq[jj];
-        const float cs = rc[j], sn = rs[j], cs2 = rc[jj], sn2 = rs[jj];
-        const bool hq = q < c, hq2 = q2 < c;
-        const float a = A[p * ld + p2];
-        const float b = hq2 ? A[p * ld + q2] : 0.0f;
-        const float cc = hq ? A[q * ld + p2] : 0.0f;
-        const float dd = (hq && hq2) ? A[q * ld + q2] : 0.0f;
-        const float a1 = cs2 * a - sn2 * b, b1 = sn2 * a + cs2 * b;
-        const float c1 = cs2 * cc - sn2 * dd, d1 = sn2 * cc + cs2 * dd;
-        An[p * ld + p2] = cs * a1 - sn * c1;
-        if (hq2) An[p * ld + q2] = cs * b1 - sn * d1;
-        if (hq) An[q * ld + p2] = sn * a1 + cs * c1;
-        if (hq && hq2) An[q * ld + q2] = sn * b1 + cs * d1;
+      for (int j = ty; j < P; j += 16) {
+        const int p = pp[j], q = pq[j];
+        const float cs = rc[j], sn = rs[j];
+        const bool hq = q < c;
+        for (int jj = tx; jj < P; jj += 16) {
+          const int p2 = pp[jj], q2 = pq[jj];
+          const float cs2 = rc[jj], sn2 = rs[jj];
+          const bool hq2 = q2 < c;
+          const float a = A[p * ld + p2];
+          const float b = hq2 ? A[p * ld + q2] : 0.0f;
+          const float cc = hq ? A[q * ld + p2] : 0.0f;
+          const float dd = (hq && hq2) ? A[q * ld + q2] : 0.0f;
+          const float a1 = cs2 * a - sn2 * b, b1 = sn2 * a + cs2 * b;
+          const float c1 = cs2 * cc - sn2 * dd, d1 = sn2 * cc + cs2 * dd;
+          An[p * ld + p2] = cs * a1 - sn * c1;
+          if (hq2) An[p * ld + q2] = cs * b1 - sn * d1;
+          if (hq) An[q * ld + p2] = sn * a1 + cs * c1;
+          if (hq && hq2) An[q * ld + q2] = sn * b1 + cs * d1;
+        }
       }
       // V <- V J (columns of each pair, in place; pairs are disjoint)
-      for (int t = tid; t < P * c; t += kJacThreads) {
-        const int j = t / c, i = t % c;
+      for (int j = ty; j < P; j += 16) {
         const int p = pp[j], q = pq[j];
         const float sn = rs[j];
         if (q >= c || sn == 0.0f) continue;
         const float cs = rc[j];
-        const float va = V[i * ld + p], vb = V[i * ld + q];
-        V[i * ld + p] = cs * va - sn * vb;
-        V[i * ld + q] = sn * va + cs * vb;
+        for (int i = tx; i < c; i += 16) {
+          const float va = V[i * ld + p], vb = V[i * ld + q];
+          V[i * ld + p] = cs * va - sn * vb;
+          V[i * ld + q] = sn * va + cs * vb;
+        }
       }
       __syncthreads();
       float *tmp = A; A = An; An = tmp;
@@ -181,41 +198,67 @@ jacobi_eig32_kernel(const double *G, int c, double *U) {
 // rotated by a quotient of two rounding errors.
 // With orth_only set, every pair is treated as clustered: E = (I - U^T U)/2,
 // one Newton-Schulz orthonormalization step (S and G are not read).
+//
+// The quotient of a separated pair is formed in FP32 after scaling numerator
+// and denominator by 1/||G||_F (the denominator exceeds 64 c u ||G||, so it
+// stays in range): E only enters as U (I + E), so a relative error of 1e-7 in
+// E adds 1e-7 * ||E|| to an error that the step squares anyway.
+__device__ __forceinline__ double warp_sum_d(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 __global__ void __launch_bounds__(kOaThreads)
 oa_update_kernel(const double *UtU, const double *S, const double *G, int c, int orth_only,
                  double *Eout) {
-  __shared__ double red[kOaThreads];
+  __shared__ double wred[3][kOaThreads / 32];
   __shared__ double lam[kMaxSmall];
+  __shared__ double s_delta, s_inv;
   const int tid = threadIdx.x;
-  double delta = 0.0;
   if (!orth_only) {
     for (int i = tid; i < c; i += kOaThreads) lam[i] = S[i * c + i] / UtU[i * c + i];
     __syncthreads();
     double g2 = 0.0, r2 = 0.0, sd2 = 0.0;
-    for (int e = tid; e < c * c; e += kOaThreads) {
-      const int i = e / c, j = e % c;
-      const double r = (i == j ? 1.0 : 0.0) - UtU[e];
-      const double sd = S[e] - (i == j ? lam[i] : 0.0);
-      g2 += G[e] * G[e];
-      r2 += r * r;
-      sd2 += sd * sd;
+    for (int i = tid / 32; i < c; i += kOaThreads / 32)
+      for (int j = tid % 32; j < c; j += 32) {
+        const int e = i * c + j;
+        const double r = (i == j ? 1.0 : 0.0) - UtU[e];
+        const double sd = S[e] - (i == j ? lam[i] : 0.0);
+        g2 = fma(G[e], G[e], g2);
+        r2 = fma(r, r, r2);
+        sd2 = fma(sd, sd, sd2);
+      }
+    g2 = warp_sum_d(g2);
+    r2 = warp_sum_d(r2);
+    sd2 = warp_sum_d(sd2);
+    if ((tid & 31) == 0) { wred[0][tid >> 5] = g2; wred[1][tid >> 5] = r2; wred[2][tid >> 5] = sd2; }
+    __syncthreads();
+    if (tid == 0) {
+      double a = 0.0, b = 0.0, s = 0.0;
+      for (int w = 0; w < kOaThreads / 32; ++w) { a += wred[0][w]; b += wred[1][w]; s += wred[2][w]; }
+      const double u = 1.1102230246251565e-16;
+      const double gn = sqrt(a);
+      s_delta = fmax(2.0 * (sqrt(s) + gn * sqrt(b)), 64.0 * c * u * gn);
+      s_inv = gn > 0.0 ? rcp_newton(gn) : 1.0;
     }
-    g2 = block_sum(g2, red);
-    r2 = block_sum(r2, red);
-    sd2 = block_sum(sd2, red);
-    const double u = 1.1102230246251565e-16;
-    delta = fmax(2.0 * (sqrt(sd2) + sqrt(g2) * sqrt(r2)), 64.0 * c * u * sqrt(g2));
+    __syncthreads();
   }
-  for (int e = tid; e < c * c; e += kOaThreads) {
-    const int i = e / c, j = e % c;
-    const double r = (i == j ? 1.0 : 0.0) - UtU[e];
-    double E;
-    if (!orth_only && i != j && fabs(lam[i] - lam[j]) > delta)
-      E = fma(lam[j], r, S[e]) * rcp_newton(lam[j] - lam[i]);
-    else
-      E = 0.5 * r;
-    Eout[e] = E + (i == j ? 1.0 : 0.0);
-  }
+  const double delta = orth_only ? 0.0 : s_delta;
+  const double inv = orth_only ? 1.0 : s_inv;
+  for (int i = tid / 32; i < c; i += kOaThreads / 32)
+    for (int j = tid % 32; j < c; j += 32) {
+      const int e = i * c + j;
+      const double r = (i == j ? 1.0 : 0.0) - UtU[e];
+      double E;
+      if (!orth_only && i != j && fabs(lam[i] - lam[j]) > delta) {
+        const float num = (float)(fma(lam[j], r, S[e]) * inv);
+        const float den = (float)((lam[j] - lam[i]) * inv);
+        E = (double)__fdividef(num, den);
+      } else {
+        E = 0.5 * r;
+      }
+      Eout[e] = E + (i == j ? 1.0 : 0.0);
+    }
 }
 
 __global__ void __launch_bounds__(kThreads)
