@@ -51,8 +51,8 @@ class HattError(RuntimeError):
 _lib = None
 
 EXPORTS = ("tt_hadamard_recompress_plan", "tt_hadamard_recompress", "tt_round_plan", "tt_round",
-           "tt_dot_plan", "tt_dot", "tt_norm", "tt_sketch_tt", "tt_philox4x32_10",
-           "tt_launch_count", "tt_status_string")
+           "tt_dot_plan", "tt_dot", "tt_dot_noalloc", "tt_norm", "tt_sketch_tt",
+           "tt_philox4x32_10", "tt_launch_count", "tt_status_string")
 
 
 def load(path: Optional[str] = None):
@@ -79,6 +79,7 @@ def load(path: Optional[str] = None):
                              ctypes.c_size_t, vp]
     lib.tt_dot_plan.argtypes = [P(TTStruct), P(TTStruct), P(ctypes.c_size_t)]
     lib.tt_dot.argtypes = [P(TTStruct), P(TTStruct), vp, vp, ctypes.c_size_t, vp]
+    lib.tt_dot_noalloc.argtypes = [P(TTStruct), P(TTStruct), vp, vp]
     lib.tt_norm.argtypes = [P(TTStruct), vp, vp, ctypes.c_size_t, vp]
     lib.tt_sketch_tt.argtypes = [ctypes.c_int32, P(ctypes.c_int64), P(ctypes.c_int64),
                                  ctypes.c_uint64, ctypes.c_uint32, P(ctypes.c_void_p), vp]
@@ -281,6 +282,20 @@ def _dot_common(fn, A, B, stream):
 def tt_dot(A, B, stream=None) -> torch.Tensor:
     """<A, B> as a 1-element CUDA tensor."""
     return _dot_common("tt_dot", A, B, stream)
+
+
+def tt_dot_noalloc(A, B, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """<A, B> through tt_dot_noalloc: no device allocation inside the library
+    (its scratch is a fixed per-GPU array). `out` may be preallocated so that
+    the call allocates nothing on the Python side either."""
+    Ad = TT(A)
+    Bd = TT(B)
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=A[0].device)
+    _check("tt_dot_noalloc", load().tt_dot_noalloc(Ad.ref(), Bd.ref(),
+                                                   ctypes.c_void_p(out.data_ptr()),
+                                                   _stream_ptr(stream)))
+    return out
 
 
 def tt_norm(A, stream=None) -> torch.Tensor:

@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "hatt.h"
@@ -580,9 +581,56 @@ bool aligned(const void *p) { return ((uintptr_t)p & 255u) == 0; }
 
 }  // namespace
 
+// ------------------------------------------------- allocation-free dot ---
+// Scratch of tt_dot_noalloc: one fixed array in the device memory of every GPU
+// that loads this library, held until the process exits. In host code the
+// symbol is only a handle: its device address comes from cudaGetSymbolAddress,
+// looked up once per device (with that device current) and cached.
+constexpr size_t kNoAllocScratchBytes = (size_t)8 << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+cudaError_t noalloc_scratch_address(void **ptr) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = p;
+  }
+  *ptr = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+}  // namespace
+
 // ===================================================================== ABI ===
 
 extern "C" {
+
+int tt_dot_noalloc(const tt_t *A, const tt_t *B, double *out, void *stream) {
+  int st = prepare_dot(A, B, true);
+  if (st != TT_OK) return st;
+  if (!out) return TT_ERR_ARG;
+  const size_t need = measure([&](Ws &ws) { return carve_dot(ws, A, B); },
+                              [&](Runner &run, const DotBufs &u) { run_dot(run, A, B, u, nullptr); });
+  if (need > kNoAllocScratchBytes) return TT_ERR_WORKSPACE;
+  void *scratch = nullptr;
+  cudaError_t e = noalloc_scratch_address(&scratch);
+  if (e != cudaSuccess) return from_cuda(e);
+  // every scratch buffer is written before it is read (the Gram seed G_0 = 1
+  // is set by a kernel), so leftovers of an earlier call never matter
+  return execute(scratch, kNoAllocScratchBytes, (cudaStream_t)stream,
+                 [&](Ws &ws) { return carve_dot(ws, A, B); },
+                 [&](Runner &run, const DotBufs &u) { run_dot(run, A, B, u, out); });
+}
 
 const char *tt_status_string(int status) {
   switch (status) {
