@@ -2,9 +2,9 @@
 //
 // Householder QR is a chain of rank-1 updates and would run on one SM at the
 // FP64 rate of a single SM (~8 GFLOP/s on GB300). Cholesky QR instead spends
-// almost all of its flops in two SM-parallel products (the Gram S^T S and
-// S R^{-1}); only a c x c Cholesky factorization and triangular inverse run in
-// one block. A pass is
+// almost all of its flops in two SM-parallel steps (the Gram S^T S, and
+// S R^{-1} as a forward substitution with one warp per row of S); only the
+// c x c Cholesky factorization runs in one block. A pass is
 //     G = S^T S,  R^T R = G (+ shift),  S <- S R^{-1}
 // and passes repeat until G = I to working accuracy (Cholesky QR2 needs two
 // passes for cond(S) < ~1e8). When the unshifted factorization breaks down
@@ -27,14 +27,7 @@ namespace {
 
 constexpr int kPasses = 4;
 constexpr int kCholThreads = 256;
-constexpr int kTrmmThreads = 256;
-constexpr int kTrmmRows = 16;
-constexpr size_t kCholSmemMax = 200 * 1024;   // dynamic shared memory of the Cholesky block
-
-// G (c x (c+1)) plus, when it fits, R^{-1} (c x c)
-__host__ __device__ constexpr size_t chol_smem_doubles(int c, bool with_inv) {
-  return (size_t)c * (c + 1) + (with_inv ? (size_t)c * c : 0);
-}
+constexpr int kTrsmThreads = 256;
 
 // 1/sqrt(x) for finite x > 0: range reduction x = m 2^e with e even, an FP32
 // seed for m, then two Newton-Raphson steps y <- y (3 - m y^2) / 2 in FP64
@@ -54,10 +47,10 @@ __device__ __forceinline__ double rsqrt_newton(double x) {
 // Flag words (reset at the start of every QR):
 //   flags[0] done:      no further pass is needed (read by the Gram GEMM and
 //                       this kernel at the start of every later pass)
-//   flags[1] skip_trmm: the S <- S R^{-1} launch of this pass is a no-op
+//   flags[1] skip_apply: the S <- S R^{-1} launch of this pass is a no-op
 //   flags[2] passes applied, flags[3] shifted passes (diagnostics)
 __global__ void __launch_bounds__(kCholThreads)
-chol_inv_kernel(const double *Gg, double *Rinv_g, int c, int m, int *flags) {
+chol_inv_kernel(const double *Gg, double *Ut_g, double *y_g, int c, int m, int *flags) {
   if (flags[0]) {
     if (threadIdx.x == 0) flags[1] = 1;
     return;
@@ -65,8 +58,6 @@ chol_inv_kernel(const double *Gg, double *Rinv_g, int c, int m, int *flags) {
   extern __shared__ double sm[];
   const int ld = c + 1;
   double *G = sm;                                   // c x ld, upper triangle becomes R
-  const bool inv_in_smem = chol_smem_doubles(c, true) * sizeof(double) <= kCholSmemMax;
-  double *Ri = inv_in_smem ? sm + c * ld : Rinv_g;  // R^{-1}, ld = c
   __shared__ double s_diag_max, s_trace, s_dev;
   __shared__ double s_rinv[kMaxSmall];              // 1 / R_jj
   __shared__ int s_fail;
@@ -173,57 +164,57 @@ chol_inv_kernel(const double *Gg, double *Rinv_g, int c, int m, int *flags) {
     if (!s_fail) break;
   }
 
-  // -- triangular inverse, row by row from the bottom: Ri[i][j], j >= i.
-  // One warp per entry: the lanes split the dot product sum_l R_il Ri_lj and
-  // reduce with shuffles, so a row costs a few shuffle rounds instead of a
-  // dependent chain of up to c FP64 multiply-adds.
-  for (int e = tid; e < c * c; e += kCholThreads) {
-    const int i = e / c, j = e % c;
-    if (j < i) Ri[e] = 0.0;
-  }
-  const int warp = tid >> 5, lane = tid & 31;
-  for (int i = c - 1; i >= 0; --i) {
-    const double yi = s_rinv[i];
-    for (int j = i + warp; j < c; j += kCholThreads / 32) {
-      double s = 0.0;
-      for (int l = i + 1 + lane; l <= j; l += 32) s = fma(G[i * ld + l], Ri[l * c + j], s);
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) Ri[i * c + j] = ((j == i) ? 1.0 - s : -s) * yi;
-    }
-    __syncthreads();
-  }
-  if (inv_in_smem)
-    for (int e = tid; e < c * c; e += kCholThreads) Rinv_g[e] = Ri[e];
+  // -- publish R = D U~ as the unit upper triangle U~ (U~_jl = R_jl / R_jj)
+  // and y_j = 1 / R_jj; the apply kernel solves with them, so no serial
+  // triangular inverse is formed in this single block
+  for (int i = ty; i < c; i += 16)
+    for (int l = tx; l < c; l += 16)
+      Ut_g[i * c + l] = (l > i) ? G[i * ld + l] * s_rinv[i] : (l == i ? 1.0 : 0.0);
+  for (int i = tid; i < c; i += kCholThreads) y_g[i] = s_rinv[i];
 }
 
-// S[r][j] <- sum_{i <= j} S[r][i] Rinv[i][j], rows owned by one block (in place).
-__global__ void __launch_bounds__(kTrmmThreads)
-trmm_rows_kernel(double *S, int m, int c, long long ldS, const double *Rinv, const int *flags) {
+// Q = S R^{-1} = (S U~^{-1}) D^{-1}, one warp per row, in place. Lane t holds
+// columns t, t+32, t+64, t+96 of the row; step l broadcasts the finished x_l
+// and every lane updates its later columns (x_j -= x_l U~_lj). The unit
+// diagonal keeps divisions out of the chain; the final scaling by y = D^{-1}
+// is one multiply per entry.
+__global__ void __launch_bounds__(kTrsmThreads)
+trsm_rows_kernel(double *S, int m, int c, long long ldS, const double *Ut, const double *y,
+                 const int *flags) {
   if (flags[1]) return;
   extern __shared__ double sm[];
-  double *Rs = sm;                       // c x c
-  double *Xs = sm + c * c;               // kTrmmRows x c
-  const int r0 = blockIdx.x * kTrmmRows;
-  const int rows = min(kTrmmRows, m - r0);
-  for (int e = threadIdx.x; e < c * c; e += kTrmmThreads) Rs[e] = Rinv[e];
-  for (int e = threadIdx.x; e < rows * c; e += kTrmmThreads) {
-    const int r = e / c, j = e % c;
-    Xs[r * c + j] = S[(long long)(r0 + r) * ldS + j];
-  }
+  double *Us = sm;                       // c x c
+  double *ys = sm + c * c;               // c
+  for (int e = threadIdx.x; e < c * c; e += kTrsmThreads) Us[e] = Ut[e];
+  for (int e = threadIdx.x; e < c; e += kTrsmThreads) ys[e] = y[e];
   __syncthreads();
-  for (int e = threadIdx.x; e < rows * c; e += kTrmmThreads) {
-    const int r = e / c, j = e % c;
-    double s = 0.0;
-    for (int i = 0; i <= j; ++i) s = fma(Xs[r * c + i], Rs[i * c + j], s);
-    S[(long long)(r0 + r) * ldS + j] = s;
+  const int lane = threadIdx.x & 31;
+  const int warps = kTrsmThreads / 32;
+  for (int r = blockIdx.x * warps + (threadIdx.x >> 5); r < m; r += gridDim.x * warps) {
+    double *row = S + (long long)r * ldS;
+    double x0 = lane < c ? row[lane] : 0.0;
+    double x1 = lane + 32 < c ? row[lane + 32] : 0.0;
+    double x2 = lane + 64 < c ? row[lane + 64] : 0.0;
+    double x3 = lane + 96 < c ? row[lane + 96] : 0.0;
+    for (int l = 0; l < c; ++l) {
+      const int slot = l >> 5;
+      const double own = slot == 0 ? x0 : slot == 1 ? x1 : slot == 2 ? x2 : x3;
+      const double xl = __shfl_sync(0xffffffffu, own, l & 31);
+      const double *u = Us + l * c;
+      if (lane > l && lane < c) x0 = fma(-xl, u[lane], x0);
+      if (lane + 32 > l && lane + 32 < c) x1 = fma(-xl, u[lane + 32], x1);
+      if (c > 64 && lane + 64 > l && lane + 64 < c) x2 = fma(-xl, u[lane + 64], x2);
+      if (c > 96 && lane + 96 > l && lane + 96 < c) x3 = fma(-xl, u[lane + 96], x3);
+    }
+    if (lane < c) row[lane] = x0 * ys[lane];
+    if (lane + 32 < c) row[lane + 32] = x1 * ys[lane + 32];
+    if (lane + 64 < c) row[lane + 64] = x2 * ys[lane + 64];
+    if (lane + 96 < c) row[lane + 96] = x3 * ys[lane + 96];
   }
 }
 
-size_t chol_smem(int c) {
-  const size_t with_inv = chol_smem_doubles(c, true) * sizeof(double);
-  return with_inv <= kCholSmemMax ? with_inv : chol_smem_doubles(c, false) * sizeof(double);
-}
-size_t trmm_smem(int c) { return (size_t)(c * c + kTrmmRows * c) * sizeof(double); }
+size_t chol_smem(int c) { return (size_t)c * (c + 1) * sizeof(double); }
+size_t trsm_smem(int c) { return (size_t)(c * c + c) * sizeof(double); }
 
 Gemm gram_desc(double *S, int m, int c, long long ldS, double *G, const int *flags) {
   Gemm g;
@@ -239,7 +230,7 @@ Gemm gram_desc(double *S, int m, int c, long long ldS, double *G, const int *fla
 
 size_t qr_scratch_doubles(int m, int c) {
   Gemm g = gram_desc(nullptr, m, c, c, nullptr, nullptr);
-  return (size_t)2 * c * c + gemm_scratch_doubles(g);
+  return (size_t)2 * c * c + c + gemm_scratch_doubles(g);
 }
 
 cudaError_t qr_inplace(double *S, int m, int c, long long ldS, double *scratch, int *flags,
@@ -247,26 +238,27 @@ cudaError_t qr_inplace(double *S, int m, int c, long long ldS, double *scratch, 
   if (c <= 0 || m <= 0) return cudaSuccess;
   if (c > kMaxSmall) return cudaErrorInvalidValue;
   double *G = scratch;
-  double *Rinv = scratch + (size_t)c * c;
-  double *gs = scratch + (size_t)2 * c * c;
+  double *Ut = scratch + (size_t)c * c;
+  double *y = scratch + (size_t)2 * c * c;
+  double *gs = scratch + (size_t)2 * c * c + c;
   cudaError_t e = cudaMemsetAsync(flags, 0, 4 * sizeof(int), st);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)kCholSmemMax);
+                           (int)chol_smem(kMaxSmall));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(trmm_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)trmm_smem(kMaxSmall));
+  e = cudaFuncSetAttribute(trsm_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)trsm_smem(kMaxSmall));
   if (e != cudaSuccess) return e;
   const Gemm gd = gram_desc(S, m, c, ldS, G, flags);
-  const int blocks = (m + kTrmmRows - 1) / kTrmmRows;
+  const int blocks = std::max(1, std::min((m + kTrsmThreads / 32 - 1) / (kTrsmThreads / 32), 2 * 152));
   for (int p = 0; p < kPasses; ++p) {
     e = gemm_f64(gd, gs, st);
     if (e != cudaSuccess) return e;
-    chol_inv_kernel<<<1, kCholThreads, chol_smem(c), st>>>(G, Rinv, c, m, flags);
+    chol_inv_kernel<<<1, kCholThreads, chol_smem(c), st>>>(G, Ut, y, c, m, flags);
     note_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    trmm_rows_kernel<<<blocks, kTrmmThreads, trmm_smem(c), st>>>(S, m, c, ldS, Rinv, flags);
+    trsm_rows_kernel<<<blocks, kTrsmThreads, trsm_smem(c), st>>>(S, m, c, ldS, Ut, y, flags);
     note_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
