@@ -4,15 +4,18 @@
 // cores to its left orthonormal, the singular values of B are those of the
 // full unfolding at bond k. One step:
 //   1. G = B B^T                                   (FP64 GEMM, all SMs)
-//   2. eigenvectors of G by cyclic Jacobi in FP32   (one block; the FP32 pipe
-//      of GB300 is ~60x its FP64 pipe, and this is the only serial stage)
+//   2. eigenvectors of G in FP32 by tridiagonalization, bisection and inverse
+//      iteration (one block; the FP32 pipe of GB300 is ~60x its FP64 pipe, and
+//      this is the only serial stage)
 //   3. three Ogita-Aishima refinement steps in FP64 (Ogita & Aishima, "Iterative
 //      refinement for symmetric eigenvalue decomposition", JJIAM 2018):
 //      R = I - U^T U, S = U^T G U, l_i = s_ii/(1 - r_ii),
 //      E_ij = (s_ij + l_j r_ij)/(l_j - l_i) for separated pairs, r_ij/2 otherwise,
-//      U <- U (I + E); quadratic convergence from the FP32 start. A last
-//      step with E = R/2 for every pair makes U orthonormal to working
-//      accuracy whatever the eigenvalue gaps
+//      U <- U (I + E); quadratic convergence from the FP32 start. Three
+//      closing steps with E = R/2 for every pair (Newton-Schulz, each squares
+//      ||I - U^T U||) make U orthonormal to working accuracy whatever the
+//      eigenvalue gaps: on graded or tightly clustered spectra the rotations
+//      of the refinement can leave ||I - U^T U|| near 1e-2
 //   4. B1 = U^T B (FP64 GEMM); e_i = ||row_i(B1)||^2 are the energies of the
 //      directions u_i, computed from B itself (not from the squared Gram), so
 //      the discarded tail sum_{dropped} e_i is accurate to O(u ||B||^2)
@@ -28,11 +31,10 @@
 namespace hatt {
 namespace {
 
-constexpr int kJacThreads = 256;
-constexpr int kMaxSweeps = 12;
 constexpr int kOaThreads = 1024;
 constexpr int kThreads = 256;
-constexpr int kRefineSteps = 3;
+constexpr int kRefineSteps = 3;   // Ogita-Aishima steps
+constexpr int kOrthSteps = 3;     // closing Newton-Schulz steps
 
 // 1/x for finite nonzero x: x = m 2^e with |m| in [0.5, 1), FP32 seed for 1/m,
 // two Newton-Raphson steps y <- y (2 - m y) in FP64 (relative error 2^-23 ->
@@ -59,134 +61,279 @@ __device__ double block_sum(double v, double *red) {
   return r;
 }
 
-// Cyclic Jacobi (round-robin ordering, c/2 disjoint rotations per round) on
-// the trace-scaled Gram matrix in FP32. Output: U (c x c, FP64, columns =
-// eigenvectors sorted by decreasing eigenvalue). A round computes its c/2
-// rotations once, then applies both sides at once, 2 x 2 block by 2 x 2 block,
-// from one copy of A into the other (J^T A J restricted to the rows of pair j
-// and the columns of pair j' depends only on that block), so a round costs two
-// barriers. The result only seeds the FP64 refinement, which converges
-// quadratically from it.
-__global__ void __launch_bounds__(kJacThreads)
-jacobi_eig32_kernel(const double *G, int c, double *U) {
+// Symmetric eigenvectors of the trace-scaled Gram matrix in FP32, one block,
+// O(c^3) work in about 6c barrier-separated steps (cyclic Jacobi needs
+// ~6 sweeps x (c - 1) rounds of O(c^2) updates and was the slowest kernel):
+//   1. Householder tridiagonalization T = H^T A H (Golub & Van Loan 8.3.1):
+//      for column k, v = x - alpha e_1, p = beta A v, w = p - (beta/2)(v^T p) v,
+//      A <- A - v w^T - w v^T on the trailing block;
+//   2. eigenvalues of T by bisection on Sturm counts, one thread per
+//      eigenvalue (the i-th largest), from Gerschgorin bounds;
+//   3. eigenvectors of T by two steps of inverse iteration, one thread per
+//      eigenvalue, each a tridiagonal solve by Gaussian elimination with
+//      partial pivoting (Golub & Van Loan 4.3);
+//   4. modified Gram-Schmidt (twice) inside each cluster of eigenvalues closer
+//      than 1e-3 of the spectral radius, where inverse iteration alone does
+//      not give orthogonal vectors;
+//   5. back-transformation Z <- H Z by the stored reflectors.
+// Columns come out sorted by decreasing eigenvalue. The result only seeds the
+// FP64 refinement, which needs a relative residual of ~1e-5 and an orthogonal
+// start (within each cluster an arbitrary orthonormal basis is fine).
+constexpr int kEigThreads = 256;
+constexpr float kClusterRel = 1e-3f;
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Solve (T - lam I) z = b in place (b -> z), T with diagonal d, off-diagonal e.
+__device__ void tridiag_shifted_solve(const float *d, const float *e, int c, float lam,
+                                      float tiny, float *a, float *du, float *du2, float *b) {
+  for (int j = 0; j < c; ++j) {
+    a[j] = d[j] - lam;
+    du[j] = (j + 1 < c) ? e[j] : 0.0f;
+    du2[j] = 0.0f;
+  }
+  for (int j = 0; j + 1 < c; ++j) {
+    const float lo = e[j];                       // sub-diagonal entry of row j + 1
+    if (fabsf(a[j]) >= fabsf(lo)) {
+      if (a[j] == 0.0f) a[j] = tiny;
+      const float f = lo / a[j];
+      a[j + 1] -= f * du[j];
+      b[j + 1] -= f * b[j];
+    } else {                                     // swap rows j and j + 1
+      const float f = a[j] / lo;
+      a[j] = lo;
+      const float t = a[j + 1];
+      a[j + 1] = du[j] - f * t;
+      if (j + 2 < c) {
+        du2[j] = du[j + 1];
+        du[j + 1] = -f * du2[j];
+      }
+      du[j] = t;
+      const float tb = b[j];
+      b[j] = b[j + 1];
+      b[j + 1] = tb - f * b[j + 1];
+    }
+  }
+  // Back substitution. A shift equal to an eigenvalue leaves pivots near zero:
+  // they are raised to +-tiny, and whenever a component exceeds 1e18 the whole
+  // vector (solved and pending parts) is scaled by 1e-18 -- the system is
+  // linear, so only the direction of z matters -- which keeps every
+  // intermediate far from FP32 overflow.
+  for (int j = c - 1; j >= 0; --j) {
+    float t = b[j];
+    if (j + 1 < c) t -= du[j] * b[j + 1];
+    if (j + 2 < c) t -= du2[j] * b[j + 2];
+    float piv = a[j];
+    if (fabsf(piv) < tiny) piv = piv < 0.0f ? -tiny : tiny;
+    t = t / piv;
+    if (fabsf(t) > 1e18f) {
+      for (int q = 0; q < c; ++q) b[q] *= 1e-18f;
+      t *= 1e-18f;
+    }
+    b[j] = t;
+  }
+}
+
+__global__ void __launch_bounds__(kEigThreads)
+eig_tridiag32_kernel(const double *G, int c, double *U) {
   extern __shared__ float fs[];
   const int ld = c + 1;
-  float *Ab0 = fs;                // c x ld
-  float *Ab1 = fs + c * ld;       // c x ld
-  float *V = fs + 2 * c * ld;     // c x ld
-  float *rc = V + c * ld;         // rotation cosines   [c/2 + 1]
-  float *rs = rc + (c / 2 + 1);   // rotation sines
-  int *pp = (int *)(rs + (c / 2 + 1));
-  int *pq = pp + (c / 2 + 1);
-  __shared__ double red[kJacThreads];
+  float *A = fs;                 // c x ld
+  float *Z = A + c * ld;         // c x ld, eigenvectors (columns)
+  float *Vh = Z + c * ld;        // c x c, reflector k in row k (length c-k-1)
+  float *d = Vh + c * c;         // diagonal of T
+  float *e = d + c;              // off-diagonal of T
+  float *tau = e + c;            // reflector scales beta_k
+  float *lam = tau + c;          // eigenvalues, decreasing
+  float *p = lam + c;            // work vector
+  __shared__ double red[kEigThreads];
+  __shared__ float s_scal[4];
+  __shared__ int s_start[kMaxSmall + 1];
   const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int tx = tid % 16, ty = tid / 16;
 
   double tr = 0.0;
-  for (int i = tid; i < c; i += kJacThreads) tr += G[i * c + i];
+  for (int i = tid; i < c; i += kEigThreads) tr += G[i * c + i];
   tr = block_sum(tr, red);
   const double scale = tr > 0.0 ? 1.0 / tr : 1.0;
-  for (int e = tid; e < c * c; e += kJacThreads) {
-    const int i = e / c, j = e % c;
-    Ab0[i * ld + j] = (float)(0.5 * (G[i * c + j] + G[j * c + i]) * scale);
-    V[i * ld + j] = (i == j) ? 1.0f : 0.0f;
+  for (int e2 = tid; e2 < c * c; e2 += kEigThreads) {
+    const int i = e2 / c, j = e2 % c;
+    A[i * ld + j] = (float)(0.5 * (G[i * c + j] + G[j * c + i]) * scale);
   }
   __syncthreads();
-  float *A = Ab0, *An = Ab1;
-  const int N = c + (c & 1);       // players of the round-robin (a dummy if c is odd)
-  const int P = N / 2;
-  // 16 x 16 thread grid: items are walked without integer division
-  const int tx = tid % 16, ty = tid / 16;
-  __shared__ float wsum[2][kJacThreads / 32];
-  for (int sweep = 0; sweep < kMaxSweeps && N > 1; ++sweep) {
-    float offf = 0.0f, totf = 0.0f;
-    for (int i = ty; i < c; i += 16)
-      for (int j = tx; j < c; j += 16) {
-        const float v = A[i * ld + j];
-        totf = fmaf(v, v, totf);
-        if (i != j) offf = fmaf(v, v, offf);
+
+  // 1. tridiagonalization
+  for (int k = 0; k + 2 < c; ++k) {
+    const int m = c - k - 1;
+    float *v = Vh + k * c;
+    if (warp == 0) {
+      float s2 = 0.0f;
+      for (int r = lane; r < m; r += 32) {
+        const float x = A[(k + 1 + r) * ld + k];
+        s2 = fmaf(x, x, s2);
       }
-    for (int o = 16; o > 0; o >>= 1) {
-      offf += __shfl_xor_sync(0xffffffffu, offf, o);
-      totf += __shfl_xor_sync(0xffffffffu, totf, o);
+      s2 = warp_sum_f(s2);
+      const float x0 = A[(k + 1) * ld + k];
+      const bool skip = !(s2 > 1e-36f);
+      const float alpha = skip ? x0 : -copysignf(sqrtf(s2), x0);
+      const float v0 = x0 - alpha;
+      const float vtv = s2 - x0 * x0 + v0 * v0;
+      for (int r = lane; r < m; r += 32) v[r] = skip ? 0.0f : (r == 0 ? v0 : A[(k + 1 + r) * ld + k]);
+      if (lane == 0) {
+        d[k] = A[k * ld + k];
+        e[k] = alpha;
+        tau[k] = (skip || !(vtv > 0.0f)) ? 0.0f : 2.0f / vtv;
+      }
     }
-    if ((tid & 31) == 0) { wsum[0][tid >> 5] = offf; wsum[1][tid >> 5] = totf; }
     __syncthreads();
-    float off = 0.0f, tot = 0.0f;
-    for (int w = 0; w < kJacThreads / 32; ++w) { off += wsum[0][w]; tot += wsum[1][w]; }
-    __syncthreads();
-    // squared off-diagonal mass <= 1e-11 of the total: a relative residual of
-    // ~3e-6, from which three FP64 refinement steps reach working accuracy even
-    // for closely spaced eigenvalues (FP32 reaches it in ~6 sweeps at c = 50)
-    if (off <= 1e-11f * tot || tot == 0.0f) break;
-    for (int round = 0; round < N - 1; ++round) {
-      if (tid < P) {
-        const int j = tid;
-        int p, q;
-        if (j == 0) { p = round % (N - 1); q = N - 1; }
-        else { p = (round + j) % (N - 1); q = (round - j + (N - 1)) % (N - 1); }
-        if (p > q) { const int t = p; p = q; q = t; }
-        float cs = 1.0f, sn = 0.0f;
-        if (q < c) {
-          const float apq = A[p * ld + q];
-          const float app = A[p * ld + p], aqq = A[q * ld + q];
-          if (fabsf(apq) > 1e-30f && fabsf(apq) > 1e-9f * sqrtf(fabsf(app * aqq))) {
-            // correctly rounded divide / sqrt: c^2 + s^2 = 1 to FP32 rounding,
-            // so rotations stay orthogonal and the stop test is reachable
-            const float tau = (aqq - app) / (2.0f * apq);
-            const float t = copysignf(1.0f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f)));
-            cs = 1.0f / sqrtf(fmaf(t, t, 1.0f));
-            sn = t * cs;
-          }
-        }
-        rc[j] = cs; rs[j] = sn; pp[j] = p; pq[j] = q;
+    const float beta = tau[k];
+    if (beta != 0.0f) {
+      for (int i = tid; i < m; i += kEigThreads) {          // p = beta A2 v
+        const float *row = A + (k + 1 + i) * ld + (k + 1);
+        float s = 0.0f;
+        for (int j = 0; j < m; ++j) s = fmaf(row[j], v[j], s);
+        p[i] = beta * s;
       }
       __syncthreads();
-      // A' = J^T A J block by block: rows of pair j, columns of pair jj
-      for (int j = ty; j < P; j += 16) {
-        const int p = pp[j], q = pq[j];
-        const float cs = rc[j], sn = rs[j];
-        const bool hq = q < c;
-        for (int jj = tx; jj < P; jj += 16) {
-          const int p2 = pp[jj], q2 = pq[jj];
-          const float cs2 = rc[jj], sn2 = rs[jj];
-          const bool hq2 = q2 < c;
-          const float a = A[p * ld + p2];
-          const float b = hq2 ? A[p * ld + q2] : 0.0f;
-          const float cc = hq ? A[q * ld + p2] : 0.0f;
-          const float dd = (hq && hq2) ? A[q * ld + q2] : 0.0f;
-          const float a1 = cs2 * a - sn2 * b, b1 = sn2 * a + cs2 * b;
-          const float c1 = cs2 * cc - sn2 * dd, d1 = sn2 * cc + cs2 * dd;
-          An[p * ld + p2] = cs * a1 - sn * c1;
-          if (hq2) An[p * ld + q2] = cs * b1 - sn * d1;
-          if (hq) An[q * ld + p2] = sn * a1 + cs * c1;
-          if (hq && hq2) An[q * ld + q2] = sn * b1 + cs * d1;
-        }
+      if (warp == 0) {
+        float s = 0.0f;
+        for (int r = lane; r < m; r += 32) s = fmaf(v[r], p[r], s);
+        s = warp_sum_f(s);
+        if (lane == 0) s_scal[0] = 0.5f * beta * s;
       }
-      // V <- V J (columns of each pair, in place; pairs are disjoint)
-      for (int j = ty; j < P; j += 16) {
-        const int p = pp[j], q = pq[j];
-        const float sn = rs[j];
-        if (q >= c || sn == 0.0f) continue;
-        const float cs = rc[j];
-        for (int i = tx; i < c; i += 16) {
-          const float va = V[i * ld + p], vb = V[i * ld + q];
-          V[i * ld + p] = cs * va - sn * vb;
-          V[i * ld + q] = sn * va + cs * vb;
+      __syncthreads();
+      const float K = s_scal[0];
+      for (int i = ty; i < m; i += 16) {                     // A2 -= v w^T + w v^T
+        const float vi = v[i], wi = p[i] - K * vi;
+        float *row = A + (k + 1 + i) * ld + (k + 1);
+        for (int j = tx; j < m; j += 16) {
+          const float wj = p[j] - K * v[j];
+          row[j] -= vi * wj + wi * v[j];
         }
       }
       __syncthreads();
-      float *tmp = A; A = An; An = tmp;
     }
   }
-  // sort eigenvalues (diagonal) in decreasing order; ties by index
-  for (int i = tid; i < c; i += kJacThreads) {
-    const float li = A[i * ld + i];
-    int pos = 0;
-    for (int j = 0; j < c; ++j) {
-      const float lj = A[j * ld + j];
-      pos += (lj > li) || (lj == li && j < i);
+  if (tid == 0) {
+    if (c >= 2) {
+      d[c - 2] = A[(c - 2) * ld + (c - 2)];
+      e[c - 2] = A[(c - 1) * ld + (c - 2)];
     }
-    for (int r = 0; r < c; ++r) U[r * c + pos] = (double)V[r * ld + i];
+    d[c - 1] = A[(c - 1) * ld + (c - 1)];
+    e[c - 1] = 0.0f;
+    // Gerschgorin interval and the smallest pivot allowed in Sturm counts
+    float lo = 3.0e38f, hi = -3.0e38f, emax = 0.0f;
+    for (int i = 0; i < c; ++i) {
+      const float rad = (i > 0 ? fabsf(e[i - 1]) : 0.0f) + (i + 1 < c ? fabsf(e[i]) : 0.0f);
+      lo = fminf(lo, d[i] - rad);
+      hi = fmaxf(hi, d[i] + rad);
+      if (i + 1 < c) emax = fmaxf(emax, e[i] * e[i]);
+    }
+    s_scal[0] = lo;
+    s_scal[1] = hi;
+    s_scal[2] = 1e-35f * fmaxf(1.0f, emax);
+  }
+  __syncthreads();
+
+  // 2. bisection: thread i finds the i-th largest eigenvalue
+  const float glo = s_scal[0], ghi = s_scal[1], pivmin = s_scal[2];
+  const float span = fmaxf(fabsf(glo), fabsf(ghi));
+  for (int i = tid; i < c; i += kEigThreads) {
+    const int target = c - 1 - i;                           // count of smaller eigenvalues
+    float a = glo, b = ghi;
+    for (int it = 0; it < 80; ++it) {
+      const float mid = 0.5f * (a + b);
+      float q = d[0] - mid;
+      int cnt = q < 0.0f;
+      for (int j = 1; j < c; ++j) {
+        if (fabsf(q) < pivmin) q = -pivmin;
+        q = d[j] - mid - __fdividef(e[j - 1] * e[j - 1], q);
+        cnt += q < 0.0f;
+      }
+      if (cnt <= target) a = mid; else b = mid;
+      if (b - a <= 2.4e-7f * fmaxf(fmaxf(fabsf(a), fabsf(b)), 1e-7f * span)) break;
+    }
+    lam[i] = 0.5f * (a + b);
+  }
+  __syncthreads();
+
+  // 3. inverse iteration, one thread per eigenvector (column i of Z)
+  const float tiny = 1e-30f + 1e-13f * span;
+  for (int i = tid; i < c; i += kEigThreads) {
+    float a[kMaxSmall], du[kMaxSmall], du2[kMaxSmall], z[kMaxSmall];
+    for (int j = 0; j < c; ++j) z[j] = 1.0f + 0.25f * (float)((j * 7 + i * 13) % 17) / 17.0f;
+    for (int it = 0; it < 2; ++it) {
+      tridiag_shifted_solve(d, e, c, lam[i], tiny, a, du, du2, z);
+      float mx = 0.0f;                             // scale by max |z_j| first: z.z
+      for (int j = 0; j < c; ++j) mx = fmaxf(mx, fabsf(z[j]));   // may overflow
+      const float sc = mx > 0.0f ? 1.0f / mx : 0.0f;
+      float s = 0.0f;
+      for (int j = 0; j < c; ++j) {
+        z[j] *= sc;
+        s = fmaf(z[j], z[j], s);
+      }
+      const float inv = s > 0.0f ? rsqrtf(s) : 0.0f;
+      for (int j = 0; j < c; ++j) z[j] *= inv;
+    }
+    for (int j = 0; j < c; ++j) Z[j * ld + i] = z[j];
+  }
+  // cluster starts: lam decreasing, a new cluster where the gap exceeds the threshold
+  for (int i = tid; i < c; i += kEigThreads)
+    s_start[i] = (i == 0) || (lam[i - 1] - lam[i] > kClusterRel * span);
+  if (tid == 0) s_start[c] = 1;
+  __syncthreads();
+
+  // 4. modified Gram-Schmidt (twice) within clusters, a warp per cluster
+  for (int s0 = 0; s0 < c; ++s0) {
+    if (!s_start[s0] || (s0 % (kEigThreads / 32)) != warp) continue;
+    int t0 = s0 + 1;
+    while (!s_start[t0]) ++t0;
+    for (int a = s0 + 1; a < t0; ++a) {
+      for (int rep = 0; rep < 2; ++rep) {
+        for (int b = s0; b < a; ++b) {
+          float dot = 0.0f;
+          for (int r = lane; r < c; r += 32) dot = fmaf(Z[r * ld + b], Z[r * ld + a], dot);
+          dot = warp_sum_f(dot);
+          for (int r = lane; r < c; r += 32) Z[r * ld + a] = fmaf(-dot, Z[r * ld + b], Z[r * ld + a]);
+          __syncwarp();
+        }
+        float s = 0.0f;
+        for (int r = lane; r < c; r += 32) s = fmaf(Z[r * ld + a], Z[r * ld + a], s);
+        s = warp_sum_f(s);
+        const float inv = s > 0.0f ? rsqrtf(s) : 0.0f;
+        for (int r = lane; r < c; r += 32) Z[r * ld + a] *= inv;
+        __syncwarp();
+      }
+    }
+  }
+  __syncthreads();
+
+  // 5. back-transformation Z <- H_0 ... H_{c-3} Z
+  for (int k = c - 3; k >= 0; --k) {
+    const float beta = tau[k];
+    if (beta == 0.0f) continue;
+    const int m = c - k - 1;
+    const float *v = Vh + k * c;
+    for (int j = tid; j < c; j += kEigThreads) {
+      float s = 0.0f;
+      for (int r = 0; r < m; ++r) s = fmaf(v[r], Z[(k + 1 + r) * ld + j], s);
+      p[j] = beta * s;
+    }
+    __syncthreads();
+    for (int r = ty; r < m; r += 16) {
+      const float vr = v[r];
+      float *row = Z + (k + 1 + r) * ld;
+      for (int j = tx; j < c; j += 16) row[j] -= vr * p[j];
+    }
+    __syncthreads();
+  }
+  for (int e2 = tid; e2 < c * c; e2 += kEigThreads) {
+    const int r = e2 / c, i = e2 % c;
+    U[e2] = (double)Z[r * ld + i];
   }
 }
 
@@ -374,10 +521,7 @@ __global__ void set_ranks_kernel(RankTable t, long long *ranks) {
   for (int i = threadIdx.x; i < t.count; i += blockDim.x) ranks[i] = t.r[i];
 }
 
-size_t jac_smem(int c) {
-  const int P = c / 2 + 1;
-  return (size_t)3 * c * (c + 1) * sizeof(float) + 2 * P * sizeof(float) + 2 * P * sizeof(int);
-}
+size_t eig_smem(int c) { return ((size_t)2 * c * (c + 1) + (size_t)c * c + 5 * (size_t)c) * sizeof(float); }
 
 struct Layout {
   double *G, *U0, *U1, *UtU, *T, *S, *E, *B1, *e, *sigma, *K, *tmp, *gs;
@@ -459,14 +603,14 @@ cudaError_t trunc_step(double *Xk, int la, int n, int lb, double *Xkm1, int lm, 
   cudaError_t e;
 #define HATT_TRY(x) do { e = (x); if (e != cudaSuccess) return e; } while (0)
   HATT_TRY(gemm_f64(g_gram(Xk, la, N, L.G), L.gs, st));
-  HATT_TRY(cudaFuncSetAttribute(jacobi_eig32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)jac_smem(kMaxSmall)));
-  jacobi_eig32_kernel<<<1, kJacThreads, jac_smem(la), st>>>(L.G, la, L.U0);
+  HATT_TRY(cudaFuncSetAttribute(eig_tridiag32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)eig_smem(kMaxSmall)));
+  eig_tridiag32_kernel<<<1, kEigThreads, eig_smem(la), st>>>(L.G, la, L.U0);
   note_launch();
   HATT_TRY(cudaGetLastError());
   double *U = L.U0, *Un = L.U1;
-  for (int it = 0; it <= kRefineSteps; ++it) {
-    const int orth_only = (it == kRefineSteps);   // last step: orthonormalize only
+  for (int it = 0; it < kRefineSteps + kOrthSteps; ++it) {
+    const int orth_only = (it >= kRefineSteps);   // closing steps: orthonormalize only
     HATT_TRY(gemm_f64(g_tn(U, U, la, la, la, L.UtU, la), L.gs, st));
     if (!orth_only) {
       HATT_TRY(gemm_f64(g_nn(L.G, U, la, la, la, L.T), L.gs, st));
