@@ -140,7 +140,13 @@ chol_inv_kernel(const double *Gg, double *Ut_g, double *y_g, int c, int m, int *
     for (int j = 0; j < c; ++j) {
       if (tid == 0) {
         double piv = G[j * ld + j];
-        if (!(piv > floor_piv)) {
+        if (Gg[j * c + j] == 0.0) {
+          // an exactly zero column of S: its Gram row and column vanish, so
+          // R_jj = 1 leaves Q_j = 0 and couples nothing. Sending it to the
+          // shifted attempt instead would make every pass shifted and leave
+          // ||Q^T Q - I|| at the shift (~1e-11) on an otherwise benign S.
+          piv = 1.0;
+        } else if (!(piv > floor_piv)) {
           if (attempt == 0) s_fail = 1;
           piv = fmax(shift, 1e-300);          // shifted attempt: never divide by zero
         }
