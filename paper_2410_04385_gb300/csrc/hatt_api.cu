@@ -70,13 +70,13 @@ struct Runner {
     if (err == cudaSuccess) check(hatt::qr_inplace(S, m, c, ld, scratch, flags, st));
   }
   void trunc(double *Xk, int la, int n, int lb, double *Xkm1, int lm, int nm, int cap,
-             const double *delta2, ll *ranks, int k) {
+             const double *delta2, ll *ranks, int k, bool deep) {
     if (!exec) {
       scratch_need = std::max(scratch_need, hatt::trunc_scratch_doubles(la, n, lb, lm, nm));
       return;
     }
     if (err == cudaSuccess)
-      check(hatt::trunc_step(Xk, la, n, lb, Xkm1, lm, nm, cap, delta2, ranks, k, scratch, st));
+      check(hatt::trunc_step(Xk, la, n, lb, Xkm1, lm, nm, cap, delta2, ranks, k, deep, scratch, st));
   }
 };
 
@@ -322,7 +322,7 @@ void run_hatt(Runner &run, const HattArgs &a, const HattBufs &b) {
   }
   for (int k = d - 1; k >= 1; --k)
     run.trunc(Xk(k), (int)l[k], (int)n[k], (int)l[k + 1], Xk(k - 1), (int)l[k - 1], (int)n[k - 1],
-              a.cap, b.delta2, b.ranks, k);
+              a.cap, b.delta2, b.ranks, k, a.tol > 0.0);
   if (run.live())
     for (int k = 0; k < d; ++k)
       run.check(hatt::compact_core(Xk(k), a.Xout[k], (int)l[k], (int)n[k], (int)l[k + 1], b.ranks,
@@ -464,7 +464,7 @@ void run_round(Runner &run, const RoundArgs &a, const RoundBufs &u) {
   }
   for (int k = d - 1; k >= 1; --k)
     run.trunc(Xk(k), (int)bnd[k], (int)n[k], (int)bnd[k + 1], Xk(k - 1), (int)bnd[k - 1],
-              (int)n[k - 1], a.cap, u.delta2, u.ranks, k);
+              (int)n[k - 1], a.cap, u.delta2, u.ranks, k, a.tol > 0.0);
   if (run.live())
     for (int k = 0; k < d; ++k)
       run.check(hatt::compact_core(Xk(k), a.Bout[k], (int)bnd[k], (int)n[k], (int)bnd[k + 1],

@@ -96,8 +96,11 @@ size_t trunc_scratch_doubles(int la, int n, int lb, int lm, int nm);
 // Chooses rho = ranks_dev[k] <= min(la, cap) by the tolerance rule with
 // delta2_dev[0] = delta^2, replaces Xk by its rho orthonormal right factor and
 // multiplies the left factor into Xkm1; rows/cols beyond rho are zeroed.
+// deep (tolerance mode) adds the second eigen level and the cross step, which
+// resolve energies far below u ||B||^2; without it (rank cap only) the
+// low-energy directions may stay mixed, which does not change a rank cut.
 cudaError_t trunc_step(double *Xk, int la, int n, int lb, double *Xkm1, int lm, int nm,
-                       int cap, const double *delta2_dev, long long *ranks_dev, int k,
+                       int cap, const double *delta2_dev, long long *ranks_dev, int k, bool deep,
                        double *scratch, cudaStream_t st);
 // delta2_dev = (tol * ||x|| )^2 / (d-1) for a device vector x.
 cudaError_t trunc_delta2(const double *x, long long count, double tol, int d, double *delta2_dev,

@@ -138,7 +138,8 @@ __device__ void tridiag_shifted_solve(const float *d, const float *e, int c, flo
 }
 
 __global__ void __launch_bounds__(kEigThreads)
-eig_tridiag32_kernel(const double *G, int c, double *U) {
+eig_tridiag32_kernel(const double *G, int c, double *U, const int *skip) {
+  if (skip && *skip) return;
   extern __shared__ float fs[];
   const int ld = c + 1;
   float *A = fs;                 // c x ld
@@ -344,7 +345,9 @@ eig_tridiag32_kernel(const double *G, int c, double *U) {
 // sin(2x+2y) = sin 2x cos 2y + cos 2x sin 2y) are only orthogonalized, never
 // rotated by a quotient of two rounding errors.
 // With orth_only set, every pair is treated as clustered: E = (I - U^T U)/2,
-// one Newton-Schulz orthonormalization step (S and G are not read).
+// one Newton-Schulz orthonormalization step (S and G are not read). A
+// positive floor_norm replaces ||G||_F in the floor (the deflated matrix of
+// the second level has an exactly diagonal part that must not raise it).
 //
 // The quotient of a separated pair is formed in FP32 after scaling numerator
 // and denominator by 1/||G||_F (the denominator exceeds 64 c u ||G||, so it
@@ -357,7 +360,8 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 
 __global__ void __launch_bounds__(kOaThreads)
 oa_update_kernel(const double *UtU, const double *S, const double *G, int c, int orth_only,
-                 double *Eout) {
+                 double floor_norm, const int *skip, double *Eout) {
+  if (skip && *skip) return;
   __shared__ double wred[3][kOaThreads / 32];
   __shared__ double lam[kMaxSmall];
   __shared__ double s_delta, s_inv;
@@ -385,7 +389,7 @@ oa_update_kernel(const double *UtU, const double *S, const double *G, int c, int
       for (int w = 0; w < kOaThreads / 32; ++w) { a += wred[0][w]; b += wred[1][w]; s += wred[2][w]; }
       const double u = 1.1102230246251565e-16;
       const double gn = sqrt(a);
-      s_delta = fmax(2.0 * (sqrt(s) + gn * sqrt(b)), 64.0 * c * u * gn);
+      s_delta = fmax(2.0 * (sqrt(s) + gn * sqrt(b)), 64.0 * c * u * (floor_norm > 0.0 ? floor_norm : gn));
       s_inv = gn > 0.0 ? rcp_newton(gn) : 1.0;
     }
     __syncthreads();
@@ -406,6 +410,89 @@ oa_update_kernel(const double *UtU, const double *S, const double *G, int c, int
       }
       Eout[e] = E + (i == j ? 1.0 : 0.0);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Second level (tolerance mode only). The Gram matrix G = B B^T holds every
+// entry to an absolute u ||G||, so eigenvalues below ~64 c u ||G||_F stay
+// mixed after the refinement (their energies can be off by ~u^2 ||G||^2 /
+// lambda, far above delta^2 for small tolerances). G1 = B1 B1^T, formed from
+// the rotated rows B1 = U^T B, holds its entries to u times the row norms, so
+// the low-energy rows can be diagonalized again on their own scale:
+//   cluster C = {i : G1_ii < 1024 c u ||G1||_F},  s = sum_{i in C} G1_ii,
+//   H = G1[C, C] / s on the cluster, H_ii = 1.25 + i/(2c) (distinct, above
+//   the cluster's spectrum, no coupling) elsewhere,
+// and its eigenvectors V (same FP32 start + FP64 refinement, floor taken from
+// the cluster's norm, 1) rotate U <- U V. The step is skipped (V = I) when C
+// has fewer than two rows or when the whole cluster fits under delta^2, in
+// which case the cut cannot fall inside it.
+//   flags[0] = skip the second level
+//   flags[1] = skip the cross step (delta^2 > 1e-16 ||G1||_F: the level-one
+//              leakage, ~u^2 ||G1|| / 1e-12, is then irrelevant)
+//   flags[2] = both skipped: B1 needs no recomputation
+constexpr double kClusterFloor = 1024.0;
+
+__global__ void __launch_bounds__(kThreads)
+l2_prep_kernel(const double *G1, int c, const double *delta2, double *H, double *V, int *flags) {
+  __shared__ double red[kThreads];
+  __shared__ int inc[kMaxSmall];
+  const int tid = threadIdx.x;
+  double f2 = 0.0;
+  for (int e = tid; e < c * c; e += kThreads) f2 = fma(G1[e], G1[e], f2);
+  const double fn = sqrt(block_sum(f2, red));
+  const double thr = kClusterFloor * c * 1.1102230246251565e-16 * fn;
+  double s = 0.0, m = 0.0;
+  for (int i = tid; i < c; i += kThreads) {
+    const double ei = G1[i * c + i];
+    inc[i] = ei < thr;
+    if (inc[i]) { s += ei; m += 1.0; }
+  }
+  s = block_sum(s, red);
+  m = block_sum(m, red);
+  const double d2 = delta2[0];
+  const int skip_l2 = (m < 2.0) || !(s > d2);
+  const int skip_cross = d2 > 1e-16 * fn;
+  if (tid == 0) {
+    flags[0] = skip_l2;
+    flags[1] = skip_cross;
+    flags[2] = skip_l2 && skip_cross;
+  }
+  const double inv_s = skip_l2 ? 0.0 : 1.0 / s;
+  for (int e = tid; e < c * c; e += kThreads) {
+    const int i = e / c, j = e % c;
+    if (skip_l2) {
+      V[e] = (i == j) ? 1.0 : 0.0;
+    } else if (inc[i] && inc[j]) {
+      H[e] = G1[e] * inv_s;
+    } else {
+      H[e] = (i == j) ? 1.25 + 0.5 * (double)i / (double)c : 0.0;
+    }
+  }
+}
+
+// Cross step: one first-order Jacobi rotation for every pair whose energies
+// differ by more than half the larger, computed from G1 = B1 B1^T (entries
+// accurate relative to the row norms): E_ij = G1_ij / (G1_jj - G1_ii). It
+// removes the leakage of high-energy directions into low-energy ones that the
+// first level leaves at ~u ||G|| / gap. Rotations above 1e-2 are left out:
+// they belong to pairs the Gram matrices could not resolve, where a
+// first-order step would not converge. Eout = I + E (I when skipped).
+__global__ void __launch_bounds__(kOaThreads)
+cross_kernel(const double *G1, int c, const int *flags, double *Eout) {
+  const int skip = flags[1];
+  for (int e = threadIdx.x; e < c * c; e += kOaThreads) {
+    const int i = e / c, j = e % c;
+    double v = (i == j) ? 1.0 : 0.0;
+    if (!skip && i != j) {
+      const double ei = G1[i * c + i], ej = G1[j * c + j];
+      const double gap = ej - ei;
+      if (fabs(gap) > 0.5 * fmax(ei, ej)) {
+        const double q = G1[e] / gap;
+        if (fabs(q) <= 1e-2) v = q;
+      }
+    }
+    Eout[e] = v;
+  }
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -524,8 +611,8 @@ __global__ void set_ranks_kernel(RankTable t, long long *ranks) {
 size_t eig_smem(int c) { return ((size_t)2 * c * (c + 1) + (size_t)c * c + 5 * (size_t)c) * sizeof(float); }
 
 struct Layout {
-  double *G, *U0, *U1, *UtU, *T, *S, *E, *B1, *e, *sigma, *K, *tmp, *gs;
-  int *perm;
+  double *G, *U0, *U1, *UtU, *T, *S, *E, *H, *V0, *V1, *B1, *e, *sigma, *K, *tmp, *gs;
+  int *perm, *flags;
 };
 
 Layout carve(double *base, int la, long long N, long long mrows) {
@@ -540,6 +627,10 @@ Layout carve(double *base, int la, long long N, long long mrows) {
   L.S = p; p += c2;
   L.E = p; p += c2;
   L.K = p; p += c2;
+  L.H = p; p += c2;
+  L.V0 = p; p += c2;
+  L.V1 = p; p += c2;
+  L.flags = (int *)p; p += 2;
   L.e = p; p += la;
   L.sigma = p; p += la;
   L.perm = (int *)p; p += la;
@@ -550,7 +641,7 @@ Layout carve(double *base, int la, long long N, long long mrows) {
 }
 
 size_t carve_doubles(int la, long long N, long long mrows) {
-  return (size_t)8 * la * la + 3 * (size_t)la + (size_t)la * N + (size_t)mrows * la;
+  return (size_t)11 * la * la + 2 + 3 * (size_t)la + (size_t)la * N + (size_t)mrows * la;
 }
 
 Gemm g_gram(const double *B, int la, long long N, double *G) {
@@ -593,9 +684,49 @@ size_t trunc_scratch_doubles(int la, int n, int lb, int lm, int nm) {
   return carve_doubles(la, N, mrows) + gs;
 }
 
+// Eigenvectors of the symmetric c x c matrix A (row-major, device): FP32
+// start, kRefineSteps Ogita-Aishima steps and kOrthSteps Newton-Schulz steps
+// in FP64, ping-ponging between Ua and Ub; the result lands in Ua (an even
+// number of steps). Every launch is a no-op when *skip != 0.
+static cudaError_t eigvecs(const double *A, int c, double *Ua, double *Ub, double floor_norm,
+                    const int *skip, const Layout &L, cudaStream_t st) {
+  cudaError_t e;
+#define HATT_TRY(x) do { e = (x); if (e != cudaSuccess) return e; } while (0)
+  static_assert((kRefineSteps + kOrthSteps) % 2 == 0, "the result must land in Ua");
+  HATT_TRY(cudaFuncSetAttribute(eig_tridiag32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)eig_smem(kMaxSmall)));
+  eig_tridiag32_kernel<<<1, kEigThreads, eig_smem(c), st>>>(A, c, Ua, skip);
+  note_launch();
+  HATT_TRY(cudaGetLastError());
+  double *U = Ua, *Un = Ub;
+  for (int it = 0; it < kRefineSteps + kOrthSteps; ++it) {
+    const int orth_only = (it >= kRefineSteps);   // closing steps: orthonormalize only
+    Gemm g = g_tn(U, U, c, c, c, L.UtU, c);
+    g.skip_dev = skip;
+    HATT_TRY(gemm_f64(g, L.gs, st));
+    if (!orth_only) {
+      g = g_nn(A, U, c, c, c, L.T);
+      g.skip_dev = skip;
+      HATT_TRY(gemm_f64(g, L.gs, st));
+      g = g_tn(U, L.T, c, c, c, L.S, c);
+      g.skip_dev = skip;
+      HATT_TRY(gemm_f64(g, L.gs, st));
+    }
+    oa_update_kernel<<<1, kOaThreads, 0, st>>>(L.UtU, L.S, A, c, orth_only, floor_norm, skip, L.E);
+    note_launch();
+    HATT_TRY(cudaGetLastError());
+    g = g_nn(U, L.E, c, c, c, Un);
+    g.skip_dev = skip;
+    HATT_TRY(gemm_f64(g, L.gs, st));
+    std::swap(U, Un);
+  }
+#undef HATT_TRY
+  return cudaSuccess;
+}
+
 cudaError_t trunc_step(double *Xk, int la, int n, int lb, double *Xkm1, int lm, int nm, int cap,
-                       const double *delta2_dev, long long *ranks_dev, int k, double *scratch,
-                       cudaStream_t st) {
+                       const double *delta2_dev, long long *ranks_dev, int k, bool deep,
+                       double *scratch, cudaStream_t st) {
   if (la > kMaxSmall) return cudaErrorInvalidValue;
   const long long N = (long long)n * lb;
   const long long mrows = (long long)lm * nm;
@@ -603,26 +734,40 @@ cudaError_t trunc_step(double *Xk, int la, int n, int lb, double *Xkm1, int lm, 
   cudaError_t e;
 #define HATT_TRY(x) do { e = (x); if (e != cudaSuccess) return e; } while (0)
   HATT_TRY(gemm_f64(g_gram(Xk, la, N, L.G), L.gs, st));
-  HATT_TRY(cudaFuncSetAttribute(eig_tridiag32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)eig_smem(kMaxSmall)));
-  eig_tridiag32_kernel<<<1, kEigThreads, eig_smem(la), st>>>(L.G, la, L.U0);
-  note_launch();
-  HATT_TRY(cudaGetLastError());
-  double *U = L.U0, *Un = L.U1;
-  for (int it = 0; it < kRefineSteps + kOrthSteps; ++it) {
-    const int orth_only = (it >= kRefineSteps);   // closing steps: orthonormalize only
-    HATT_TRY(gemm_f64(g_tn(U, U, la, la, la, L.UtU, la), L.gs, st));
-    if (!orth_only) {
-      HATT_TRY(gemm_f64(g_nn(L.G, U, la, la, la, L.T), L.gs, st));
-      HATT_TRY(gemm_f64(g_tn(U, L.T, la, la, la, L.S, la), L.gs, st));
-    }
-    oa_update_kernel<<<1, kOaThreads, 0, st>>>(L.UtU, L.S, L.G, la, orth_only, L.E);
+  HATT_TRY(eigvecs(L.G, la, L.U0, L.U1, 0.0, nullptr, L, st));
+  double *U = L.U0;
+  HATT_TRY(gemm_f64(g_tn(U, Xk, la, N, N, L.B1, N), L.gs, st));
+  if (deep) {
+    // second level on the low-energy rows of B1, then the cross step
+    HATT_TRY(gemm_f64(g_gram(L.B1, la, N, L.G), L.gs, st));
+    l2_prep_kernel<<<1, kThreads, 0, st>>>(L.G, la, delta2_dev, L.H, L.V0, L.flags);
     note_launch();
     HATT_TRY(cudaGetLastError());
-    HATT_TRY(gemm_f64(g_nn(U, L.E, la, la, la, Un), L.gs, st));
-    std::swap(U, Un);
+    HATT_TRY(eigvecs(L.H, la, L.V0, L.V1, 1.0, L.flags, L, st));
+    HATT_TRY(gemm_f64(g_nn(L.U0, L.V0, la, la, la, L.U1), L.gs, st));          // U1 = U V
+    Gemm g = g_tn(L.U1, Xk, la, N, N, L.B1, N);                                 // B1 = U1^T B
+    g.skip_dev = L.flags + 2;
+    HATT_TRY(gemm_f64(g, L.gs, st));
+    g = g_gram(L.B1, la, N, L.G);                                               // G1 = B1 B1^T
+    g.skip_dev = L.flags + 1;
+    HATT_TRY(gemm_f64(g, L.gs, st));
+    cross_kernel<<<1, kOaThreads, 0, st>>>(L.G, la, L.flags, L.E);
+    note_launch();
+    HATT_TRY(cudaGetLastError());
+    HATT_TRY(gemm_f64(g_nn(L.U1, L.E, la, la, la, L.U0), L.gs, st));           // U0 = U1 (I + E)
+    for (int it = 0; it < 2; ++it) {                                            // U0 -> U1 -> U0
+      double *Ua = it == 0 ? L.U0 : L.U1, *Ub = it == 0 ? L.U1 : L.U0;
+      HATT_TRY(gemm_f64(g_tn(Ua, Ua, la, la, la, L.UtU, la), L.gs, st));
+      oa_update_kernel<<<1, kOaThreads, 0, st>>>(L.UtU, L.S, L.G, la, 1, 0.0, nullptr, L.E);
+      note_launch();
+      HATT_TRY(cudaGetLastError());
+      HATT_TRY(gemm_f64(g_nn(Ua, L.E, la, la, la, Ub), L.gs, st));
+    }
+    g = g_tn(L.U0, Xk, la, N, N, L.B1, N);                                      // B1 = U^T B
+    g.skip_dev = L.flags + 2;
+    HATT_TRY(gemm_f64(g, L.gs, st));
+    U = L.U0;
   }
-  HATT_TRY(gemm_f64(g_tn(U, Xk, la, N, N, L.B1, N), L.gs, st));
   rownorm_kernel<<<la, kThreads, 0, st>>>(L.B1, N, L.e);
   note_launch();
   HATT_TRY(cudaGetLastError());

@@ -243,3 +243,52 @@ def test_round_of_pkp_matches_hatt(B):
     A = ott.hadamard_pkp(Y, Z)
     Bg = to_np(B.tt_round(to_gpu(A), 0, 1e-14))
     assert rel_diff(Bg, A) <= 1e-12
+
+
+def hard_spectrum_tt(kind):
+    """A TT whose middle bond has a graded spectrum (twelve decades) or
+    clusters {1, 1e-3, 1e-6, 0} of six singular values each: the FP32 eigen
+    start of the truncation cannot resolve these, so the FP64 refinement and
+    its closing orthonormalization carry the accuracy."""
+    d, n, r = 5, 6, 24
+    A = wl.gaussian_tt([n] * d, [1, 6, r, r, 6, 1], 77)
+    if kind == "graded":
+        s = 10.0 ** (-np.linspace(0.0, 12.0, r))
+    else:
+        s = np.repeat([1.0, 1e-3, 1e-6, 0.0], r // 4)
+    A[1] = A[1] * s[None, None, :]
+    return A
+
+
+@pytest.mark.parametrize("kind,tol", [("graded", 1e-9), ("graded", 1e-5), ("clustered", 1e-12)])
+def test_round_hard_spectra(B, kind, tol):
+    A = hard_spectrum_tt(kind)
+    Bg = to_np(B.tt_round(to_gpu(A), 0, tol))
+    Bo, rk = oround.tt_round(A, 0, tol)
+    assert ott.ranks(Bg) == rk
+    assert rel_diff(Bg, A) <= tol * (1 + 1e-6) + 1e-13
+    assert rel_diff(Bg, Bo) <= tol + 1e-13
+    if kind == "clustered":
+        assert rk[2] == 18                      # the six zero singular values are dropped
+
+
+def test_round_cut_below_resolution_is_conservative(B):
+    """tol = 1e-11 puts the cut near sigma^2 ~ 1e-24 ||X||^2, below what two
+    Gram levels resolve in FP64: ranks may exceed the SVD's, never fall
+    below them, and the error bound holds."""
+    A = hard_spectrum_tt("graded")
+    tol = 1e-11
+    Bg = to_np(B.tt_round(to_gpu(A), 0, tol))
+    _, rk = oround.tt_round(A, 0, tol)
+    assert all(a >= b for a, b in zip(ott.ranks(Bg), rk))
+    assert rel_diff(Bg, A) <= tol
+
+
+def test_round_without_truncation_keeps_exact_zero_directions_exact(B):
+    """Six singular values of a bond are exactly zero, so the left-to-right
+    Cholesky QR meets exactly zero columns: they must be null columns of an
+    otherwise unshifted factorization, and a round that changes no rank must
+    reproduce the input to rounding."""
+    A = hard_spectrum_tt("clustered")
+    Bg = to_np(B.tt_round(to_gpu(A), 24, 0.0))
+    assert rel_diff(Bg, A) <= 1e-13
