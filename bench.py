@@ -15,6 +15,7 @@ pair (replicas, weak scaling); the time is the max over ranks.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -37,6 +38,28 @@ L2_FLUSH_BYTES = 256 << 20          # > 129 MB L2
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x FP64 FMA lanes/SM x 2 x max clock
 FP64_PEAK_NOTE = ("derived: 152 SMs x 2 FP64 FMA lanes/SM/clk x 2 flop x 2070 MHz = 1.259 TFLOP/s; "
                   "a DFMA throughput loop measured 1.196 TFLOP/s on this GB300 pool")
+
+
+GEMM_TIMING_STEPS = 3
+GEMM_PROFILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles",
+                            "gemm_f64_kernel_d20_traffic.json")
+GEMM_SOURCE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2410_04385_gb300",
+                           "csrc", "k_gemm.cu")
+
+
+def gemm_traffic_per_launch():
+    """DRAM bytes (read + write) per GEMM launch from the committed ncu
+    summary, or None when the kernel source has changed since the capture."""
+    try:
+        with open(GEMM_PROFILE) as f:
+            prof = json.load(f)
+        with open(GEMM_SOURCE, "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+    except (OSError, ValueError):
+        return None
+    if prof.get("source_sha256") != sha:
+        return None
+    return prof.get("dram_bytes_per_launch")
 
 
 def parse():
@@ -313,7 +336,30 @@ def main():
     torch.cuda.synchronize()
     e2e_ms = statistics.mean(s.elapsed_time(e) for s, e in zip(e_s, e_e))
 
-    # ---- roofline of the step (one graph launch = one recompression) ----
+    # ---- dominant kernel: the FP64 GEMM, timed live with CUDA events ----
+    # Eager steps under the library's kernel timer, each queued behind a
+    # bounded GPU sleep so that the host has enqueued the whole step before
+    # the GPU reaches it and no event pair brackets a host launch gap.
+    cap = 8192
+    sleep_cycles = int(2.1e9 * min(0.25, max(0.05, 3e-3 * eager_ms)))
+    t_s = [torch.cuda.Event(enable_timing=True) for _ in range(GEMM_TIMING_STEPS)]
+    t_e = [torch.cuda.Event(enable_timing=True) for _ in range(GEMM_TIMING_STEPS)]
+    binding.kernel_timer_start(cap)
+    for i in range(GEMM_TIMING_STEPS):
+        torch.cuda._sleep(sleep_cycles)
+        t_s[i].record(stream)
+        h.run()
+        t_e[i].record(stream)
+    torch.cuda.synchronize()
+    g_ms, g_fl, g_rec = binding.kernel_timer_stop(cap)
+    timed_steps_ms = sum(a.elapsed_time(b) for a, b in zip(t_s, t_e))
+    gemm_ms = sum(g_ms)
+    gemm_flops = sum(g_fl)
+    gemm_launches = len(g_ms)
+    gemm_tflops = gemm_flops / (gemm_ms * 1e-3) / 1e12
+    traffic = gemm_traffic_per_launch()
+
+    # ---- roofline of the whole step (one graph launch = one recompression) ----
     n = workloads.modes_of(Y)
     r = workloads.ranks_of(Y)
     s = workloads.ranks_of(Z)
@@ -335,10 +381,20 @@ def main():
         "wall_s_timed_region": wall,
         "e2e": {"value": world * 1000.0 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "roofline": {"bound": "alu", "kernel": "HaTT-1 step (graph of all libhatt kernels)",
-                     "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": None,
-                     "algorithmic_flops_per_step": alg_flops, "peak_source": FP64_PEAK_NOTE},
+        "roofline": {"bound": "alu", "kernel": "gemm_f64_kernel (FP64 GEMM, all shapes of one step)",
+                     "achieved": gemm_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": gemm_tflops / FP64_PEAK_TFLOPS, "traffic": traffic,
+                     "launches_timed": gemm_launches,
+                     "avg_launch_us": 1e3 * gemm_ms / max(gemm_launches, 1),
+                     "algorithmic_flops_per_launch": gemm_flops / max(gemm_launches, 1),
+                     "share_of_step": gemm_ms / timed_steps_ms,
+                     "timing": "CUDA events around every launch on its own stream (library kernel "
+                               "timer), eager steps queued behind a GPU sleep",
+                     "peak_source": FP64_PEAK_NOTE},
+        "roofline_step": {"bound": "alu", "kernel": "HaTT-1 step (graph of all libhatt kernels)",
+                          "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                          "frac": achieved_tflops / FP64_PEAK_TFLOPS,
+                          "algorithmic_flops_per_step": alg_flops},
         "clocks": clocks,
     }
 

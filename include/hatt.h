@@ -184,6 +184,25 @@ int tt_philox4x32_10(const uint32_t *ctr, uint32_t key0, uint32_t key1, uint32_t
  * launch count. Host only; never fails. */
 int64_t tt_launch_count(void);
 
+/* Kernel timer, a diagnostic with no counterpart in the paper: between
+ * tt_kernel_timer_start and tt_kernel_timer_stop, each launch of the FP64
+ * GEMM kernel that is not being captured into a CUDA graph is bracketed by a
+ * pair of CUDA events recorded on the stream it is launched on, and its
+ * algorithmic flop count 2*M*N*K*batch is kept, for the first `capacity`
+ * launches (later ones run untimed). This is how a caller measures the
+ * dominant kernel's average duration on its own stream.
+ * start: creates 2*capacity events on the current device (the library owns
+ *   them); capacity in [1, 1<<20], else TT_ERR_ARG; TT_ERR_CUDA if event
+ *   creation fails; a running timer is stopped and discarded first.
+ * stop: waits for the recorded events, writes ms[i] and flops[i] (host
+ *   arrays of `capacity` doubles, may be NULL when capacity is 0) for the
+ *   i < min(recorded, capacity) launches, *count = number recorded (may be
+ *   NULL), destroys the events. TT_ERR_ARG if no timer is running.
+ * Host only; one timer per process; not for use while another thread
+ * launches through this library. */
+int tt_kernel_timer_start(int32_t capacity);
+int tt_kernel_timer_stop(double *ms, double *flops, int32_t capacity, int64_t *count);
+
 /* Static description of a status code (never NULL). */
 const char *tt_status_string(int status);
 

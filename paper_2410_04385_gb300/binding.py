@@ -52,7 +52,8 @@ _lib = None
 
 EXPORTS = ("tt_hadamard_recompress_plan", "tt_hadamard_recompress", "tt_round_plan", "tt_round",
            "tt_dot_plan", "tt_dot", "tt_dot_noalloc", "tt_norm", "tt_sketch_tt",
-           "tt_philox4x32_10", "tt_launch_count", "tt_status_string")
+           "tt_philox4x32_10", "tt_launch_count", "tt_kernel_timer_start",
+           "tt_kernel_timer_stop", "tt_status_string")
 
 
 def load(path: Optional[str] = None):
@@ -86,6 +87,9 @@ def load(path: Optional[str] = None):
     lib.tt_philox4x32_10.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint32, vp, ctypes.c_int64, vp]
     lib.tt_launch_count.restype = ctypes.c_int64
     lib.tt_launch_count.argtypes = []
+    lib.tt_kernel_timer_start.argtypes = [ctypes.c_int32]
+    lib.tt_kernel_timer_stop.argtypes = [P(ctypes.c_double), P(ctypes.c_double), ctypes.c_int32,
+                                         P(ctypes.c_int64)]
     for name in EXPORTS:
         getattr(lib, name)
     if path is None:
@@ -96,6 +100,24 @@ def load(path: Optional[str] = None):
 def launch_count() -> int:
     """Kernels enqueued by libhatt in this process so far."""
     return int(load().tt_launch_count())
+
+
+def kernel_timer_start(capacity: int) -> None:
+    """Start timing the FP64 GEMM kernel launches (outside graph capture)
+    with CUDA events on their own stream; see tt_kernel_timer_start."""
+    _check("tt_kernel_timer_start", load().tt_kernel_timer_start(int(capacity)))
+
+
+def kernel_timer_stop(capacity: int):
+    """Stop the timer; returns (ms, flops, recorded): per-launch durations in
+    milliseconds and algorithmic flop counts of the first min(recorded,
+    capacity) timed launches."""
+    ms = (ctypes.c_double * max(capacity, 1))()
+    fl = (ctypes.c_double * max(capacity, 1))()
+    cnt = ctypes.c_int64(0)
+    _check("tt_kernel_timer_stop", load().tt_kernel_timer_stop(ms, fl, int(capacity), ctypes.byref(cnt)))
+    k = min(int(cnt.value), int(capacity))
+    return list(ms[:k]), list(fl[:k]), int(cnt.value)
 
 
 def status_string(status: int) -> str:

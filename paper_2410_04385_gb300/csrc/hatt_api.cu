@@ -24,6 +24,61 @@ std::atomic<long long> g_launches{0};
 }
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+// Kernel timer state (tt_kernel_timer_start / _stop). Guarded by a mutex;
+// `active` is read without it on the launch path so that the timer costs one
+// relaxed load when it is off.
+namespace {
+struct KernelTimer {
+  std::mutex mu;
+  std::atomic<bool> active{false};
+  std::vector<cudaEvent_t> ev;     // 2 per slot
+  std::vector<double> flops;
+  int used = 0;
+};
+KernelTimer g_timer;
+}  // namespace
+
+int timer_begin(cudaStream_t st) {
+  if (!g_timer.active.load(std::memory_order_relaxed)) return -1;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return -1;
+  }
+  std::lock_guard<std::mutex> lk(g_timer.mu);
+  const int cap = (int)g_timer.flops.size();
+  if (!g_timer.active.load() || g_timer.used >= cap) return -1;
+  const int slot = g_timer.used++;
+  if (cudaEventRecord(g_timer.ev[2 * slot], st) != cudaSuccess) {
+    cudaGetLastError();
+    g_timer.flops[slot] = -1.0;     // marks a slot without a valid start
+  }
+  return slot;
+}
+
+void timer_end(int slot, cudaStream_t st, double flops) {
+  if (slot < 0) return;
+  std::lock_guard<std::mutex> lk(g_timer.mu);
+  if (slot >= (int)g_timer.flops.size()) return;
+  if (g_timer.flops[slot] < 0.0) return;
+  if (cudaEventRecord(g_timer.ev[2 * slot + 1], st) != cudaSuccess) {
+    cudaGetLastError();
+    g_timer.flops[slot] = -1.0;
+    return;
+  }
+  g_timer.flops[slot] = flops;
+}
+
+namespace {
+void timer_release() {   // caller holds g_timer.mu
+  g_timer.active.store(false);
+  for (cudaEvent_t e : g_timer.ev) cudaEventDestroy(e);
+  g_timer.ev.clear();
+  g_timer.flops.clear();
+  g_timer.used = 0;
+}
+}  // namespace
 }  // namespace hatt
 
 namespace {
@@ -799,6 +854,57 @@ int tt_sketch_tt(int32_t d, const int64_t *n, const int64_t *ell, uint64_t seed,
 }
 
 int64_t tt_launch_count(void) { return (int64_t)hatt::launch_count(); }
+
+int tt_kernel_timer_start(int32_t capacity) {
+  if (capacity < 1 || capacity > (1 << 20)) return TT_ERR_ARG;
+  std::lock_guard<std::mutex> lk(hatt::g_timer.mu);
+  hatt::timer_release();
+  hatt::g_timer.ev.assign(2 * (size_t)capacity, nullptr);
+  for (auto &e : hatt::g_timer.ev) {
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      e = nullptr;
+      hatt::g_timer.ev.erase(std::remove(hatt::g_timer.ev.begin(), hatt::g_timer.ev.end(),
+                                         (cudaEvent_t) nullptr),
+                             hatt::g_timer.ev.end());
+      hatt::timer_release();
+      return TT_ERR_CUDA;
+    }
+  }
+  hatt::g_timer.flops.assign((size_t)capacity, 0.0);
+  hatt::g_timer.used = 0;
+  hatt::g_timer.active.store(true);
+  return TT_OK;
+}
+
+int tt_kernel_timer_stop(double *ms, double *flops, int32_t capacity, int64_t *count) {
+  if (capacity < 0 || (capacity > 0 && (ms == nullptr || flops == nullptr))) return TT_ERR_ARG;
+  std::lock_guard<std::mutex> lk(hatt::g_timer.mu);
+  if (!hatt::g_timer.active.load()) return TT_ERR_ARG;
+  hatt::g_timer.active.store(false);
+  const int used = hatt::g_timer.used;
+  int status = TT_OK;
+  for (int i = 0; i < used && i < capacity; ++i) {
+    float t = 0.0f;
+    const double f = hatt::g_timer.flops[i];
+    if (f < 0.0) {
+      ms[i] = -1.0;
+      flops[i] = 0.0;
+      continue;
+    }
+    if (cudaEventSynchronize(hatt::g_timer.ev[2 * i + 1]) != cudaSuccess ||
+        cudaEventElapsedTime(&t, hatt::g_timer.ev[2 * i], hatt::g_timer.ev[2 * i + 1]) != cudaSuccess) {
+      cudaGetLastError();
+      status = TT_ERR_CUDA;
+      t = -1.0f;
+    }
+    ms[i] = (double)t;
+    flops[i] = f;
+  }
+  if (count) *count = used;
+  hatt::timer_release();
+  return status;
+}
 
 int tt_philox4x32_10(const uint32_t *ctr, uint32_t key0, uint32_t key1, uint32_t *out,
                      int64_t count, void *stream) {

@@ -16,6 +16,11 @@ constexpr int kMaxSmall = 128;   // TT_MAX_SMALL_RANK
 // calls note_launch once).
 void note_launch();
 long long launch_count();
+// Kernel timer (see tt_kernel_timer_start): timer_begin returns a slot and
+// records its start event on st, or -1 when the timer is off, full, or st is
+// capturing; timer_end records the stop event and the launch's flops.
+int timer_begin(cudaStream_t st);
+void timer_end(int slot, cudaStream_t st, double flops);
 constexpr int kMaxOrder = 512;   // largest d handled by the parameter tables
 
 // ------------------------------------------------------------------ GEMM ---

@@ -258,6 +258,7 @@ cudaError_t gemm_f64(const Gemm &g, double *scratch, cudaStream_t st) {
   if (L.ksplit > 1 && scratch == nullptr) return cudaErrorInvalidValue;
   if ((long long)L.tiles_n * L.tiles_m * L.ksplit * g.batch >= (1LL << 31))
     return cudaErrorInvalidConfiguration;
+  const int slot = timer_begin(st);
   switch (L.out) {
     case 1: launch_tile<1>(g, L, scratch, st); break;
     case 2: launch_tile<2>(g, L, scratch, st); break;
@@ -266,6 +267,7 @@ cudaError_t gemm_f64(const Gemm &g, double *scratch, cudaStream_t st) {
     case 12: launch_tile<12>(g, L, scratch, st); break;
     default: launch_tile<16>(g, L, scratch, st); break;
   }
+  timer_end(slot, st, 2.0 * g.M * g.N * (double)g.K * g.batch);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || L.ksplit == 1) return e;
   const long long total = (long long)g.M * g.N * g.batch;

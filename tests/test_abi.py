@@ -173,3 +173,18 @@ def test_round_and_dot_plans(lib):
     assert B.load().tt_dot_plan(Ad.ref(), Bd.ref(), ctypes.byref(ws)) == 0
     Cd = B.TT(n=[5, 6, 8], r=[1, 2, 3, 1])
     assert B.load().tt_dot_plan(Ad.ref(), Cd.ref(), ctypes.byref(ws)) == 1
+
+
+def test_kernel_timer_argument_checks(lib):
+    """The timer's argument and state checks answer before any CUDA call
+    (status 3 = TT_ERR_ARG)."""
+    assert lib.tt_kernel_timer_start(0) == 3
+    assert lib.tt_kernel_timer_start(-5) == 3
+    assert lib.tt_kernel_timer_start((1 << 20) + 1) == 3
+    ms = (ctypes.c_double * 4)()
+    fl = (ctypes.c_double * 4)()
+    cnt = ctypes.c_int64(-1)
+    # no timer running
+    assert lib.tt_kernel_timer_stop(ms, fl, 4, ctypes.byref(cnt)) == 3
+    assert lib.tt_kernel_timer_stop(None, None, 4, None) == 3
+    assert lib.tt_kernel_timer_stop(ms, fl, -1, None) == 3

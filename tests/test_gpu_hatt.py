@@ -292,3 +292,30 @@ def test_round_without_truncation_keeps_exact_zero_directions_exact(B):
     A = hard_spectrum_tt("clustered")
     Bg = to_np(B.tt_round(to_gpu(A), 24, 0.0))
     assert rel_diff(Bg, A) <= 1e-13
+
+
+def test_kernel_timer_times_every_gemm_launch(B):
+    """One eager recompression under the kernel timer: every FP64 GEMM launch
+    gets a positive duration and the flop count of its shape; the launches
+    outside the capacity run untimed; a captured replay records nothing."""
+    Y, Z, o = wl.workload_small_sin_times_random()
+    Yg, Zg = to_gpu(Y), to_gpu(Z)
+    h = B.HadamardRecompressor(Yg, Zg, seed=0, **o)
+    B.kernel_timer_start(4096)
+    h.run()
+    torch.cuda.synchronize()
+    ms, fl, recorded = B.kernel_timer_stop(4096)
+    assert recorded == len(ms) > 10
+    assert all(0.0 < t < 100.0 for t in ms)
+    assert all(f > 0 and f == int(f) and int(f) % 2 == 0 for f in fl)
+    B.kernel_timer_start(3)
+    h.run()
+    torch.cuda.synchronize()
+    ms3, _, rec3 = B.kernel_timer_stop(3)
+    assert rec3 == 3 and len(ms3) == 3
+    h.capture()
+    B.kernel_timer_start(16)
+    h.replay()
+    torch.cuda.synchronize()
+    _, _, rec_graph = B.kernel_timer_stop(16)
+    assert rec_graph == 0
