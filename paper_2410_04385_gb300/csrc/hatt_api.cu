@@ -607,9 +607,16 @@ size_t measure(Carve carve, Run runf) {
   Runner run;
   auto bufs = carve(ws);
   runf(run, bufs);
+  ws.take<int>(hatt::kTileCounters);
   ws.take<double>(run.scratch_need);
   return ws.off + 256;
 }
+
+// Makes a tile-counter array current for the calling thread during one call.
+struct TileCounterScope {
+  explicit TileCounterScope(int *p) { hatt::set_tile_counters(p); }
+  ~TileCounterScope() { hatt::set_tile_counters(nullptr); }
+};
 
 template <class Carve, class Run>
 int execute(void *workspace, size_t wsb, cudaStream_t st, Carve carve, Run runf) {
@@ -626,8 +633,11 @@ int execute(void *workspace, size_t wsb, cudaStream_t st, Carve carve, Run runf)
   Runner run;
   run.exec = true;
   run.st = st;
+  int *counters = ws.take<int>(hatt::kTileCounters);
   run.scratch = ws.take<double>(plan.scratch_need);
   if (ws.off > wsb) return TT_ERR_WORKSPACE;
+  run.check(cudaMemsetAsync(counters, 0, hatt::kTileCounters * sizeof(int), st));
+  TileCounterScope scope(counters);
   runf(run, bufs);
   return from_cuda(run.err);
 }

@@ -16,6 +16,13 @@ constexpr int kMaxSmall = 128;   // TT_MAX_SMALL_RANK
 // calls note_launch once).
 void note_launch();
 long long launch_count();
+// Split-K GEMMs count finished blocks per output tile in an int array of
+// kTileCounters entries that is zero before every GEMM (each GEMM leaves it
+// zero). The entry points carve one per call, clear it once, and make it the
+// calling thread's current array for the duration of the call.
+constexpr int kTileCounters = 4096;
+void set_tile_counters(int *counters);
+int *tile_counters();
 // Kernel timer (see tt_kernel_timer_start): timer_begin returns a slot and
 // records its start event on st, or -1 when the timer is off, full, or st is
 // capturing; timer_end records the stop event and the launch's flops.

@@ -11,8 +11,10 @@
 //     chosen to divide M and N (e.g. 80 x 50 for a 1600 x 50 product), so
 //     almost no lane computes padding;
 //   * K is split until the grid has about four blocks per SM (wave
-//     quantization < 25%); split-K partial sums are reduced in a fixed order by
-//     a second kernel (no atomics), so results are bitwise reproducible.
+//     quantization < 25%); the block that finishes an output tile last (a
+//     per-tile counter) sums its split-K partials in split order 0..ksplit-1,
+//     whichever block that is, so results are bitwise reproducible and no
+//     second kernel is launched.
 #include <algorithm>
 #include <mutex>
 #include <vector>
@@ -34,10 +36,11 @@ struct Launch {
 template <int OUT>
 __global__ void __launch_bounds__(kThreads)
 gemm_f64_kernel(Gemm g, int bm, int bn, int tiles_n, int tiles_m, int ksplit, int kchunk,
-                double *partial) {
+                double *partial, int *counters) {
   if (g.skip_dev && *g.skip_dev) return;
   __shared__ double As[kBK][kMaxTile + 1];
   __shared__ double Bs[kBK][kMaxTile + 1];
+  __shared__ int s_last;
   const int tid = threadIdx.x;
   // 1-D grid: block -> (n tile, m tile, split, batch), n tile fastest
   long long blk = blockIdx.x;
@@ -99,18 +102,44 @@ gemm_f64_kernel(Gemm g, int bm, int bn, int tiles_n, int tiles_m, int ksplit, in
     __syncthreads();
   }
 
+  const double alpha = g.alpha * (g.alpha_dev ? *g.alpha_dev : 1.0);
+  double *C = g.C + b1 * g.sC1 + b2 * g.sC2;
   if (ksplit > 1) {
-    double *P = partial + ((long long)b * ksplit + ks) * g.M * (long long)g.N;
+    const long long mn = (long long)g.M * g.N;
+    const double *P0 = partial + (long long)b * ksplit * mn;
+    double *P = partial + ((long long)b * ksplit + ks) * mn;
 #pragma unroll
     for (int q = 0; q < OUT; ++q) {
       if (q >= nq) break;
       const int gm = m0 + om[q], gn = n0 + on[q];
       if (gm < g.M && gn < g.N) P[(long long)gm * g.N + gn] = acc[q];
     }
+    // publish this partial, then let the last of the tile's ksplit blocks sum
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+      const int t = (b * tiles_m + tm_i) * tiles_n + tn_i;
+      const int prev = atomicAdd(&counters[t], 1);
+      s_last = (prev == ksplit - 1);
+      if (s_last) counters[t] = 0;          // clean for the next GEMM on this array
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+#pragma unroll
+    for (int q = 0; q < OUT; ++q) {
+      if (q >= nq) break;
+      const int gm = m0 + om[q], gn = n0 + on[q];
+      if (gm >= g.M || gn >= g.N) continue;
+      const long long e = (long long)gm * g.N + gn;
+      double sum = 0.0;
+      for (int k = 0; k < ksplit; ++k) sum += (k == ks) ? acc[q] : __ldcg(P0 + k * mn + e);
+      double *c = C + gm * g.sCm + gn * g.sCn;
+      const double v = alpha * sum;
+      *c = (g.beta != 0.0) ? fma(g.beta, *c, v) : v;
+    }
     return;
   }
-  const double alpha = g.alpha * (g.alpha_dev ? *g.alpha_dev : 1.0);
-  double *C = g.C + b1 * g.sC1 + b2 * g.sC2;
 #pragma unroll
   for (int q = 0; q < OUT; ++q) {
     if (q >= nq) break;
@@ -118,27 +147,6 @@ gemm_f64_kernel(Gemm g, int bm, int bn, int tiles_n, int tiles_m, int ksplit, in
     if (gm >= g.M || gn >= g.N) continue;
     double *c = C + gm * g.sCm + gn * g.sCn;
     const double v = alpha * acc[q];
-    *c = (g.beta != 0.0) ? fma(g.beta, *c, v) : v;
-  }
-}
-
-__global__ void __launch_bounds__(kThreads)
-gemm_reduce_kernel(Gemm g, int ksplit, const double *partial) {
-  if (g.skip_dev && *g.skip_dev) return;
-  const long long mn = (long long)g.M * g.N;
-  const long long total = mn * g.batch;
-  const double alpha = g.alpha * (g.alpha_dev ? *g.alpha_dev : 1.0);
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int b = (int)(t / mn);
-    const long long e = t % mn;
-    const int gm = (int)(e / g.N), gn = (int)(e % g.N);
-    const double *P = partial + (long long)b * ksplit * mn + e;
-    double s = 0.0;
-    for (int k = 0; k < ksplit; ++k) s += P[k * mn];
-    const int b1 = b / g.bdiv, b2 = b % g.bdiv;
-    double *c = g.C + b1 * g.sC1 + b2 * g.sC2 + gm * g.sCm + gn * g.sCn;
-    const double v = alpha * s;
     *c = (g.beta != 0.0) ? fma(g.beta, *c, v) : v;
   }
 }
@@ -167,7 +175,9 @@ int tile_edge(int X, int cap) {
 //         blocks the busiest SM receives (wave quantization over 152 SMs);
 //   latency: ~450 clocks per 16-deep k-tile (staging + two barriers), hidden
 //         up to 4 blocks per SM;
-//   split-K: the reduce kernel (~2500 clocks plus its partial-sum traffic).
+//   split-K: the last block of each tile re-reads the tile's ksplit partial
+//         sums from L2 (~64 bytes per clock per SM) before it writes C; the
+//         busiest SM does ceil(tiles / 152) such reductions.
 double model_clocks(const Gemm &g, int bm, int bn, long long ksplit) {
   const long long tiles = ceil_div(g.M, bm) * ceil_div(g.N, bn) * (long long)g.batch;
   const long long kchunk = ceil_div(ceil_div(g.K, ksplit), kBK) * kBK;
@@ -176,7 +186,8 @@ double model_clocks(const Gemm &g, int bm, int bn, long long ksplit) {
   const double dfma = (double)bm * bn * std::min<long long>(kchunk, g.K);
   const double ktiles = (double)ceil_div(std::min<long long>(kchunk, g.K), kBK);
   double t = per_sm * (dfma / 2.0) + ceil_div(per_sm, 4) * ktiles * 450.0 + 1500.0;
-  if (ksplit > 1) t += 2500.0 + (double)ksplit * g.M * g.N * g.batch * 8.0 / 2500.0;
+  if (ksplit > 1)
+    t += (double)ceil_div(tiles, 152) * (600.0 + (double)ksplit * bm * bn * 8.0 / 64.0);
   return t;
 }
 
@@ -196,6 +207,7 @@ Launch plan_search(const Gemm &g) {
       cands[nc++] = std::min(kmax, std::max<long long>(1, ceil_div(kTargetBlocks, tiles)));
       cands[nc++] = std::min(kmax, std::max<long long>(1, ceil_div(152, tiles)));
       for (int i = 0; i < nc; ++i) {
+        if (cands[i] > 1 && tiles > kTileCounters) continue;   // one counter per tile
         const double t = model_clocks(g, bm, bn, cands[i]);
         if (t < best) {
           best = t;
@@ -233,11 +245,12 @@ Launch plan(const Gemm &g) {
 }
 
 template <int OUT>
-void launch_tile(const Gemm &g, const Launch &L, double *scratch, cudaStream_t st) {
+void launch_tile(const Gemm &g, const Launch &L, double *scratch, int *counters,
+                 cudaStream_t st) {
   const long long blocks = (long long)L.tiles_n * L.tiles_m * L.ksplit * g.batch;
   gemm_f64_kernel<OUT><<<(unsigned)blocks, kThreads, 0, st>>>(g, L.bm, L.bn, L.tiles_n,
                                                              L.tiles_m, L.ksplit, L.kchunk,
-                                                             scratch);
+                                                             scratch, counters);
   note_launch();
 }
 
@@ -255,26 +268,27 @@ cudaError_t gemm_f64(const Gemm &g, double *scratch, cudaStream_t st) {
     return cudaErrorInvalidValue;   // callers never issue empty contractions
   }
   const Launch L = plan(g);
-  if (L.ksplit > 1 && scratch == nullptr) return cudaErrorInvalidValue;
+  int *counters = tile_counters();
+  if (L.ksplit > 1 && (scratch == nullptr || counters == nullptr)) return cudaErrorInvalidValue;
   if ((long long)L.tiles_n * L.tiles_m * L.ksplit * g.batch >= (1LL << 31))
     return cudaErrorInvalidConfiguration;
   const int slot = timer_begin(st);
   switch (L.out) {
-    case 1: launch_tile<1>(g, L, scratch, st); break;
-    case 2: launch_tile<2>(g, L, scratch, st); break;
-    case 4: launch_tile<4>(g, L, scratch, st); break;
-    case 8: launch_tile<8>(g, L, scratch, st); break;
-    case 12: launch_tile<12>(g, L, scratch, st); break;
-    default: launch_tile<16>(g, L, scratch, st); break;
+    case 1: launch_tile<1>(g, L, scratch, counters, st); break;
+    case 2: launch_tile<2>(g, L, scratch, counters, st); break;
+    case 4: launch_tile<4>(g, L, scratch, counters, st); break;
+    case 8: launch_tile<8>(g, L, scratch, counters, st); break;
+    case 12: launch_tile<12>(g, L, scratch, counters, st); break;
+    default: launch_tile<16>(g, L, scratch, counters, st); break;
   }
   timer_end(slot, st, 2.0 * g.M * g.N * (double)g.K * g.batch);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || L.ksplit == 1) return e;
-  const long long total = (long long)g.M * g.N * g.batch;
-  const int blocks = (int)std::min<long long>((total + kThreads - 1) / kThreads, 4 * 152);
-  gemm_reduce_kernel<<<blocks, kThreads, 0, st>>>(g, L.ksplit, scratch);
-  note_launch();
   return cudaGetLastError();
 }
+
+namespace {
+thread_local int *t_tile_counters = nullptr;
+}
+void set_tile_counters(int *counters) { t_tile_counters = counters; }
+int *tile_counters() { return t_tile_counters; }
 
 }  // namespace hatt

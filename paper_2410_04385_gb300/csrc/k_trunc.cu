@@ -35,6 +35,8 @@ constexpr int kOaThreads = 1024;
 constexpr int kThreads = 256;
 constexpr int kRefineSteps = 3;   // Ogita-Aishima steps
 constexpr int kOrthSteps = 3;     // closing Newton-Schulz steps
+constexpr int kEigSteps = kRefineSteps + kOrthSteps;
+constexpr double kConverged = 1e-9;
 
 // 1/x for finite nonzero x: x = m 2^e with |m| in [0.5, 1), FP32 seed for 1/m,
 // two Newton-Raphson steps y <- y (2 - m y) in FP64 (relative error 2^-23 ->
@@ -360,8 +362,8 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 
 __global__ void __launch_bounds__(kOaThreads)
 oa_update_kernel(const double *UtU, const double *S, const double *G, int c, int orth_only,
-                 double floor_norm, const int *skip, double *Eout) {
-  if (skip && *skip) return;
+                 double floor_norm, int *state, int step, int nsteps, double *Eout) {
+  if (state && state[step]) return;
   __shared__ double wred[3][kOaThreads / 32];
   __shared__ double lam[kMaxSmall];
   __shared__ double s_delta, s_inv;
@@ -396,6 +398,7 @@ oa_update_kernel(const double *UtU, const double *S, const double *G, int c, int
   }
   const double delta = orth_only ? 0.0 : s_delta;
   const double inv = orth_only ? 1.0 : s_inv;
+  double emax = 0.0;
   for (int i = tid / 32; i < c; i += kOaThreads / 32)
     for (int j = tid % 32; j < c; j += 32) {
       const int e = i * c + j;
@@ -408,8 +411,35 @@ oa_update_kernel(const double *UtU, const double *S, const double *G, int c, int
       } else {
         E = 0.5 * r;
       }
+      emax = fmax(emax, fabs(E));
       Eout[e] = E + (i == j ? 1.0 : 0.0);
     }
+  // Converged: after this correction (|E| <= kConverged) the error is
+  // O(|E|^2 + 1e-7 |E|) ~ 1e-16, so every later step is skipped.
+  if (!state) return;
+  for (int o = 16; o > 0; o >>= 1) emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+  __shared__ double wmax[kOaThreads / 32];
+  if ((tid & 31) == 0) wmax[tid >> 5] = emax;
+  __syncthreads();
+  if (tid == 0) {
+    double m = 0.0;
+    for (int w = 0; w < kOaThreads / 32; ++w) m = fmax(m, wmax[w]);
+    if (m <= kConverged)
+      for (int j = step + 1; j < nsteps; ++j) state[j] = 1;
+  }
+}
+
+// After an eigvecs run whose steps may have stopped early: the number of
+// steps applied is the index of the first skipped step; if it is odd the
+// result sits in Ub and is copied to Ua.
+__global__ void select_result_kernel(const int *state, int nsteps, const double *Ub, double *Ua,
+                                     int count) {
+  int applied = nsteps;
+  for (int j = 0; j < nsteps; ++j)
+    if (state[j]) { applied = j; break; }
+  if ((applied & 1) == 0) return;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x)
+    Ua[e] = Ub[e];
 }
 
 // ---------------------------------------------------------------------------
@@ -433,7 +463,8 @@ oa_update_kernel(const double *UtU, const double *S, const double *G, int c, int
 constexpr double kClusterFloor = 1024.0;
 
 __global__ void __launch_bounds__(kThreads)
-l2_prep_kernel(const double *G1, int c, const double *delta2, double *H, double *V, int *flags) {
+l2_prep_kernel(const double *G1, int c, const double *delta2, double *H, double *V, int *flags,
+               int *eig_state) {
   __shared__ double red[kThreads];
   __shared__ int inc[kMaxSmall];
   const int tid = threadIdx.x;
@@ -457,6 +488,7 @@ l2_prep_kernel(const double *G1, int c, const double *delta2, double *H, double 
     flags[1] = skip_cross;
     flags[2] = skip_l2 && skip_cross;
   }
+  if (tid < kEigSteps) eig_state[tid] = skip_l2;
   const double inv_s = skip_l2 ? 0.0 : 1.0 / s;
   for (int e = tid; e < c * c; e += kThreads) {
     const int i = e / c, j = e % c;
@@ -630,7 +662,7 @@ Layout carve(double *base, int la, long long N, long long mrows) {
   L.H = p; p += c2;
   L.V0 = p; p += c2;
   L.V1 = p; p += c2;
-  L.flags = (int *)p; p += 2;
+  L.flags = (int *)p; p += 12;       // 24 ints: level-two flags, two eigvecs states
   L.e = p; p += la;
   L.sigma = p; p += la;
   L.perm = (int *)p; p += la;
@@ -641,7 +673,7 @@ Layout carve(double *base, int la, long long N, long long mrows) {
 }
 
 size_t carve_doubles(int la, long long N, long long mrows) {
-  return (size_t)11 * la * la + 2 + 3 * (size_t)la + (size_t)la * N + (size_t)mrows * la;
+  return (size_t)11 * la * la + 12 + 3 * (size_t)la + (size_t)la * N + (size_t)mrows * la;
 }
 
 Gemm g_gram(const double *B, int la, long long N, double *G) {
@@ -686,40 +718,46 @@ size_t trunc_scratch_doubles(int la, int n, int lb, int lm, int nm) {
 
 // Eigenvectors of the symmetric c x c matrix A (row-major, device): FP32
 // start, kRefineSteps Ogita-Aishima steps and kOrthSteps Newton-Schulz steps
-// in FP64, ping-ponging between Ua and Ub; the result lands in Ua (an even
-// number of steps). Every launch is a no-op when *skip != 0.
+// in FP64, ping-ponging between Ua and Ub; the result lands in Ua.
+// state[j] != 0 turns step j into no-ops (state[0] also the FP32 start): the
+// caller clears state[0..kEigSteps) or sets it to skip everything, and a step
+// whose correction is below kConverged sets the flags of all later steps.
 static cudaError_t eigvecs(const double *A, int c, double *Ua, double *Ub, double floor_norm,
-                    const int *skip, const Layout &L, cudaStream_t st) {
+                           int *state, const Layout &L, cudaStream_t st) {
   cudaError_t e;
 #define HATT_TRY(x) do { e = (x); if (e != cudaSuccess) return e; } while (0)
-  static_assert((kRefineSteps + kOrthSteps) % 2 == 0, "the result must land in Ua");
   HATT_TRY(cudaFuncSetAttribute(eig_tridiag32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)eig_smem(kMaxSmall)));
-  eig_tridiag32_kernel<<<1, kEigThreads, eig_smem(c), st>>>(A, c, Ua, skip);
+  eig_tridiag32_kernel<<<1, kEigThreads, eig_smem(c), st>>>(A, c, Ua, state);
   note_launch();
   HATT_TRY(cudaGetLastError());
   double *U = Ua, *Un = Ub;
-  for (int it = 0; it < kRefineSteps + kOrthSteps; ++it) {
+  for (int it = 0; it < kEigSteps; ++it) {
     const int orth_only = (it >= kRefineSteps);   // closing steps: orthonormalize only
     Gemm g = g_tn(U, U, c, c, c, L.UtU, c);
-    g.skip_dev = skip;
+    g.skip_dev = state + it;
     HATT_TRY(gemm_f64(g, L.gs, st));
     if (!orth_only) {
       g = g_nn(A, U, c, c, c, L.T);
-      g.skip_dev = skip;
+      g.skip_dev = state + it;
       HATT_TRY(gemm_f64(g, L.gs, st));
       g = g_tn(U, L.T, c, c, c, L.S, c);
-      g.skip_dev = skip;
+      g.skip_dev = state + it;
       HATT_TRY(gemm_f64(g, L.gs, st));
     }
-    oa_update_kernel<<<1, kOaThreads, 0, st>>>(L.UtU, L.S, A, c, orth_only, floor_norm, skip, L.E);
+    oa_update_kernel<<<1, kOaThreads, 0, st>>>(L.UtU, L.S, A, c, orth_only, floor_norm, state, it,
+                                                kEigSteps, L.E);
     note_launch();
     HATT_TRY(cudaGetLastError());
     g = g_nn(U, L.E, c, c, c, Un);
-    g.skip_dev = skip;
+    g.skip_dev = state + it;
     HATT_TRY(gemm_f64(g, L.gs, st));
     std::swap(U, Un);
   }
+  static_assert(kEigSteps % 2 == 0, "with every step applied the result is in Ua");
+  select_result_kernel<<<4, kThreads, 0, st>>>(state, kEigSteps, Ub, Ua, c * c);
+  note_launch();
+  HATT_TRY(cudaGetLastError());
 #undef HATT_TRY
   return cudaSuccess;
 }
@@ -733,17 +771,19 @@ cudaError_t trunc_step(double *Xk, int la, int n, int lb, double *Xkm1, int lm, 
   Layout L = carve(scratch, la, N, mrows);
   cudaError_t e;
 #define HATT_TRY(x) do { e = (x); if (e != cudaSuccess) return e; } while (0)
+  int *state1 = L.flags + 8, *state2 = L.flags + 16;
   HATT_TRY(gemm_f64(g_gram(Xk, la, N, L.G), L.gs, st));
-  HATT_TRY(eigvecs(L.G, la, L.U0, L.U1, 0.0, nullptr, L, st));
+  HATT_TRY(cudaMemsetAsync(state1, 0, kEigSteps * sizeof(int), st));
+  HATT_TRY(eigvecs(L.G, la, L.U0, L.U1, 0.0, state1, L, st));
   double *U = L.U0;
   HATT_TRY(gemm_f64(g_tn(U, Xk, la, N, N, L.B1, N), L.gs, st));
   if (deep) {
     // second level on the low-energy rows of B1, then the cross step
     HATT_TRY(gemm_f64(g_gram(L.B1, la, N, L.G), L.gs, st));
-    l2_prep_kernel<<<1, kThreads, 0, st>>>(L.G, la, delta2_dev, L.H, L.V0, L.flags);
+    l2_prep_kernel<<<1, kThreads, 0, st>>>(L.G, la, delta2_dev, L.H, L.V0, L.flags, state2);
     note_launch();
     HATT_TRY(cudaGetLastError());
-    HATT_TRY(eigvecs(L.H, la, L.V0, L.V1, 1.0, L.flags, L, st));
+    HATT_TRY(eigvecs(L.H, la, L.V0, L.V1, 1.0, state2, L, st));
     HATT_TRY(gemm_f64(g_nn(L.U0, L.V0, la, la, la, L.U1), L.gs, st));          // U1 = U V
     Gemm g = g_tn(L.U1, Xk, la, N, N, L.B1, N);                                 // B1 = U1^T B
     g.skip_dev = L.flags + 2;
@@ -758,7 +798,7 @@ cudaError_t trunc_step(double *Xk, int la, int n, int lb, double *Xkm1, int lm, 
     for (int it = 0; it < 2; ++it) {                                            // U0 -> U1 -> U0
       double *Ua = it == 0 ? L.U0 : L.U1, *Ub = it == 0 ? L.U1 : L.U0;
       HATT_TRY(gemm_f64(g_tn(Ua, Ua, la, la, la, L.UtU, la), L.gs, st));
-      oa_update_kernel<<<1, kOaThreads, 0, st>>>(L.UtU, L.S, L.G, la, 1, 0.0, nullptr, L.E);
+      oa_update_kernel<<<1, kOaThreads, 0, st>>>(L.UtU, L.S, L.G, la, 1, 0.0, nullptr, 0, 0, L.E);
       note_launch();
       HATT_TRY(cudaGetLastError());
       HATT_TRY(gemm_f64(g_nn(Ua, L.E, la, la, la, Ub), L.gs, st));
