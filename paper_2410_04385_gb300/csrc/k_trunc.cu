@@ -89,53 +89,83 @@ __device__ __forceinline__ float warp_sum_f(float v) {
   return v;
 }
 
-// Solve (T - lam I) z = b in place (b -> z), T with diagonal d, off-diagonal e.
+// Lanes per dot product when n dot products of one block share kEigThreads
+// threads: the largest power of two <= 32 with lanes * n <= kEigThreads.
+__device__ __forceinline__ int lanes_per_dot(int n) {
+  int t = 32;
+  while (t > 1 && t * n > kEigThreads) t >>= 1;
+  return t;
+}
+
+// Sum over aligned groups of `lanes` lanes (a power of two dividing 32); every
+// lane of the warp must call it.
+__device__ __forceinline__ float group_sum_f(float v, int lanes) {
+  for (int o = lanes >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Entry j of the start vector of eigenvector i: a hash of (i, j) mapped to
+// [-1, 1). Start vectors must have independent projections on a cluster's
+// eigenspace; a smooth pattern close to the all-ones vector does not (all of
+// them project onto nearly the same direction), and Gram-Schmidt then keeps
+// mostly the out-of-cluster error.
+__device__ __forceinline__ float start_entry(int i, int j) {
+  unsigned h = (unsigned)i * 0x9E3779B1u + (unsigned)j * 0x85EBCA77u + 0x165667B1u;
+  h ^= h >> 15;
+  h *= 0x2C1B3C6Du;
+  h ^= h >> 12;
+  h *= 0x297A2D39u;
+  h ^= h >> 15;
+  return -1.0f + 2.0f * (float)(h & 0xffffffu) * (1.0f / 16777216.0f);
+}
+
+// Solve (T - lam I) z = b in place (b -> z), T with diagonal d and
+// off-diagonal e, by Gaussian elimination with partial pivoting (Golub & Van
+// Loan 4.3). The row being eliminated is carried in registers, so the sweep
+// only stores the U factor (ua, udu, udu2) and the transformed right-hand side
+// (kept in b); the back substitution reads them in reverse order, with loads
+// that do not depend on its own recurrence.
 __device__ void tridiag_shifted_solve(const float *d, const float *e, int c, float lam,
-                                      float tiny, float *a, float *du, float *du2, float *b) {
-  for (int j = 0; j < c; ++j) {
-    a[j] = d[j] - lam;
-    du[j] = (j + 1 < c) ? e[j] : 0.0f;
-    du2[j] = 0.0f;
-  }
+                                      float tiny, float *ua, float *udu, float *udu2, float *b) {
+  float ac = d[0] - lam, duc = (c > 1) ? e[0] : 0.0f, bc = b[0];
   for (int j = 0; j + 1 < c; ++j) {
+    float an = d[j + 1] - lam, dun = (j + 2 < c) ? e[j + 1] : 0.0f, bn = b[j + 1];
     const float lo = e[j];                       // sub-diagonal entry of row j + 1
-    if (fabsf(a[j]) >= fabsf(lo)) {
-      if (a[j] == 0.0f) a[j] = tiny;
-      const float f = lo / a[j];
-      a[j + 1] -= f * du[j];
-      b[j + 1] -= f * b[j];
-    } else {                                     // swap rows j and j + 1
-      const float f = a[j] / lo;
-      a[j] = lo;
-      const float t = a[j + 1];
-      a[j + 1] = du[j] - f * t;
-      if (j + 2 < c) {
-        du2[j] = du[j + 1];
-        du[j + 1] = -f * du2[j];
-      }
-      du[j] = t;
-      const float tb = b[j];
-      b[j] = b[j + 1];
-      b[j + 1] = tb - f * b[j + 1];
+    if (fabsf(ac) >= fabsf(lo)) {
+      if (ac == 0.0f) ac = tiny;
+      const float f = __fdividef(lo, ac);
+      an = fmaf(-f, duc, an);
+      bn = fmaf(-f, bc, bn);
+      ua[j] = ac; udu[j] = duc; udu2[j] = 0.0f; b[j] = bc;
+    } else {                                     // rows j and j + 1 swap
+      const float f = __fdividef(ac, lo);
+      ua[j] = lo; udu[j] = an; udu2[j] = dun; b[j] = bn;
+      const float a2 = fmaf(-f, an, duc), du2n = -f * dun, b2 = fmaf(-f, bn, bc);
+      an = a2; dun = du2n; bn = b2;
     }
+    ac = an; duc = dun; bc = bn;
   }
+  ua[c - 1] = ac; udu[c - 1] = 0.0f; udu2[c - 1] = 0.0f; b[c - 1] = bc;
   // Back substitution. A shift equal to an eigenvalue leaves pivots near zero:
   // they are raised to +-tiny, and whenever a component exceeds 1e18 the whole
   // vector (solved and pending parts) is scaled by 1e-18 -- the system is
   // linear, so only the direction of z matters -- which keeps every
   // intermediate far from FP32 overflow.
+  float z1 = 0.0f, z2 = 0.0f;                    // z_{j+1}, z_{j+2}
   for (int j = c - 1; j >= 0; --j) {
-    float t = b[j];
-    if (j + 1 < c) t -= du[j] * b[j + 1];
-    if (j + 2 < c) t -= du2[j] * b[j + 2];
-    float piv = a[j];
+    float t = fmaf(-udu[j], z1, fmaf(-udu2[j], z2, b[j]));
+    float piv = ua[j];
     if (fabsf(piv) < tiny) piv = piv < 0.0f ? -tiny : tiny;
-    t = t / piv;
+    t = __fdividef(t, piv);
     if (fabsf(t) > 1e18f) {
       for (int q = 0; q < c; ++q) b[q] *= 1e-18f;
+      z1 *= 1e-18f;
+      z2 *= 1e-18f;
       t *= 1e-18f;
     }
     b[j] = t;
+    z2 = z1;
+    z1 = t;
   }
 }
 
@@ -195,11 +225,16 @@ eig_tridiag32_kernel(const double *G, int c, double *U, const int *skip) {
     __syncthreads();
     const float beta = tau[k];
     if (beta != 0.0f) {
-      for (int i = tid; i < m; i += kEigThreads) {          // p = beta A2 v
-        const float *row = A + (k + 1 + i) * ld + (k + 1);
+      {                                                     // p = beta A2 v
+        const int lanes = lanes_per_dot(m);
+        const int i = tid / lanes, sub = tid % lanes;
         float s = 0.0f;
-        for (int j = 0; j < m; ++j) s = fmaf(row[j], v[j], s);
-        p[i] = beta * s;
+        if (i < m) {
+          const float *row = A + (k + 1 + i) * ld + (k + 1);
+          for (int j = sub; j < m; j += lanes) s = fmaf(row[j], v[j], s);
+        }
+        s = group_sum_f(s, lanes);
+        if (i < m && sub == 0) p[i] = beta * s;
       }
       __syncthreads();
       if (warp == 0) {
@@ -263,12 +298,23 @@ eig_tridiag32_kernel(const double *G, int c, double *U, const int *skip) {
     lam[i] = 0.5f * (a + b);
   }
   __syncthreads();
+  // Shifts of equal (or nearly equal) eigenvalues are moved apart by 10 ulps
+  // of the larger magnitude, as in LAPACK's inverse iteration: identical
+  // shifts meet the same near-zero pivot and return the same vector, which
+  // Gram-Schmidt would then annihilate (exact ties occur, e.g. the two equal
+  // singular values of sin(a + b) = sin a cos b + cos a sin b).
+  if (tid == 0)
+    for (int i = 1; i < c; ++i) {
+      const float pert = 6e-7f * fabsf(lam[i - 1]);
+      if (lam[i - 1] - lam[i] < pert) lam[i] = lam[i - 1] - pert;
+    }
+  __syncthreads();
 
   // 3. inverse iteration, one thread per eigenvector (column i of Z)
   const float tiny = 1e-30f + 1e-13f * span;
   for (int i = tid; i < c; i += kEigThreads) {
     float a[kMaxSmall], du[kMaxSmall], du2[kMaxSmall], z[kMaxSmall];
-    for (int j = 0; j < c; ++j) z[j] = 1.0f + 0.25f * (float)((j * 7 + i * 13) % 17) / 17.0f;
+    for (int j = 0; j < c; ++j) z[j] = start_entry(i, j);
     for (int it = 0; it < 2; ++it) {
       tridiag_shifted_solve(d, e, c, lam[i], tiny, a, du, du2, z);
       float mx = 0.0f;                             // scale by max |z_j| first: z.z
@@ -321,10 +367,14 @@ eig_tridiag32_kernel(const double *G, int c, double *U, const int *skip) {
     if (beta == 0.0f) continue;
     const int m = c - k - 1;
     const float *v = Vh + k * c;
-    for (int j = tid; j < c; j += kEigThreads) {
+    {                                                       // p = beta Z2^T v
+      const int lanes = lanes_per_dot(c);
+      const int j = tid / lanes, sub = tid % lanes;
       float s = 0.0f;
-      for (int r = 0; r < m; ++r) s = fmaf(v[r], Z[(k + 1 + r) * ld + j], s);
-      p[j] = beta * s;
+      if (j < c)
+        for (int r = sub; r < m; r += lanes) s = fmaf(v[r], Z[(k + 1 + r) * ld + j], s);
+      s = group_sum_f(s, lanes);
+      if (j < c && sub == 0) p[j] = beta * s;
     }
     __syncthreads();
     for (int r = ty; r < m; r += 16) {
@@ -346,7 +396,8 @@ eig_tridiag32_kernel(const double *G, int c, double *U, const int *skip) {
 // accuracy (exact degeneracies, e.g. the equal singular values of
 // sin(2x+2y) = sin 2x cos 2y + cos 2x sin 2y) are only orthogonalized, never
 // rotated by a quotient of two rounding errors.
-// With orth_only set, every pair is treated as clustered: E = (I - U^T U)/2,
+// Rotations larger than 0.1 are not applied (the pair counts as clustered
+// for this step). With orth_only set, every pair is treated as clustered: E = (I - U^T U)/2,
 // one Newton-Schulz orthonormalization step (S and G are not read). A
 // positive floor_norm replaces ||G||_F in the floor (the deflated matrix of
 // the second level has an exactly diagonal part that must not raise it).
@@ -404,12 +455,15 @@ oa_update_kernel(const double *UtU, const double *S, const double *G, int c, int
       const int e = i * c + j;
       const double r = (i == j ? 1.0 : 0.0) - UtU[e];
       double E;
+      E = 0.5 * r;
       if (!orth_only && i != j && fabs(lam[i] - lam[j]) > delta) {
         const float num = (float)(fma(lam[j], r, S[e]) * inv);
         const float den = (float)((lam[j] - lam[i]) * inv);
-        E = (double)__fdividef(num, den);
-      } else {
-        E = 0.5 * r;
+        const float q = __fdividef(num, den);
+        // a first-order rotation above 0.1 belongs to a pair the current
+        // iterate does not resolve yet: applying it would wreck the
+        // orthogonality; the pair is treated as clustered for this step
+        if (fabsf(q) <= 0.1f) E = (double)q;
       }
       emax = fmax(emax, fabs(E));
       Eout[e] = E + (i == j ? 1.0 : 0.0);
