@@ -55,8 +55,24 @@ typedef struct {
   double **cores;
 } tt_t;
 
+/* Arithmetic of tt_hadamard_recompress. Only the right-to-left sketches
+ * W^{(k)} (HPCRL-1, Algorithm 3 / Eq. (3.6)) may run in low precision: each of
+ * their three products per core rounds its operands (W^{(k+1)} with its norm,
+ * the sketch core R_k, Z_k, Y_k and the intermediates) to the named type --
+ * FP64 -> FP32 round to nearest even, then for TF32 round to nearest with ties
+ * away at 10 mantissa bits, for BF16 round to nearest even at 7 -- and
+ * accumulates in FP32; the result is kept in FP64. A perturbed W is just
+ * another test matrix: range(C_k W) stays inside range(C_k), so the QR, the
+ * projection, the core update and the truncation (all FP64) keep the result
+ * exact whenever the sketch rank reaches the separation rank, and otherwise
+ * add an error of the order of the sketch's relative perturbation to the
+ * randomized range-finder error. The paper computes in FP64 throughout; the
+ * low-precision modes have no counterpart in it. */
 typedef enum {
-  TT_FP64 = 0            /* every step in IEEE binary64 */
+  TT_FP64 = 0,           /* every step in IEEE binary64 */
+  TT_MIXED_FP32 = 1,     /* HPCRL-1 products: FP32 operands, FP32 accumulation */
+  TT_MIXED_TF32 = 2,     /* HPCRL-1 products: TF32 operands, FP32 accumulation */
+  TT_MIXED_BF16 = 3      /* HPCRL-1 products: BF16 operands, FP32 accumulation */
 } tt_precision;
 
 /* Options of tt_hadamard_recompress (the problem statement of Algorithm 4:

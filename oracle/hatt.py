@@ -15,7 +15,11 @@ Readings of the paper taken here (the paper is silent or fixed-rank only):
   * QR uses the sign convention diag(R) >= 0;
   * an optional truncation sweep (right to left, SVD of each H(X_k) of the
     left-orthogonal result) enforces max_rank / tol with
-    delta = tol * ||X|| / sqrt(d-1).
+    delta = tol * ||X|| / sqrt(d-1);
+  * low-precision sketches (not in the paper, which is FP64 throughout) are
+    emulated by rounding every operand of the three HPCRL-1 products to the
+    named format and accumulating exactly in float64; everything after the
+    sketches stays float64.
 """
 from __future__ import annotations
 
@@ -94,11 +98,40 @@ def hpcrl1_wlwr(Y, Z, R, normalize=True):
     return W
 
 
-def hpcrl1_contract(Y, Z, R, normalize=True):
+FORMATS = ("fp64", "fp32", "tf32", "bf16")
+
+
+def round_operand(x, fmt="fp64"):
+    """The value a low-precision multiplier receives for the float64 x:
+    float64 -> binary32 (round to nearest even), then
+      tf32: 10 explicit mantissa bits, round to nearest, ties away from zero;
+      bf16: 7 explicit mantissa bits (the top half of binary32), round to
+            nearest, ties to even.
+    Both are written on the binary32 bit pattern: adding half of the dropped
+    part (plus the kept lsb for ties-to-even) and clearing the dropped bits."""
+    if fmt == "fp64":
+        return np.asarray(x, dtype=np.float64)
+    f = np.asarray(x, dtype=np.float64).astype(np.float32)
+    if fmt == "fp32":
+        return f.astype(np.float64)
+    u = f.view(np.uint32).astype(np.uint64)
+    if fmt == "tf32":
+        u = (u + 0x1000) & 0xFFFFE000
+    elif fmt == "bf16":
+        u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    else:
+        raise ValueError(fmt)
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def hpcrl1_contract(Y, Z, R, normalize=True, fmt="fp64"):
     """HPCRL-1 as a plain index contraction in three stages (Eq. (3.6)):
       T1[a', b', i, l] = sum_g  W[a' s + b', g] R_k(l, i, g)
       T2[a', b,  i, l] = sum_b' Z_k(b, i, b') T1[a', b', i, l]
-      W'[a s + b, l]   = sum_{a', i} Y_k(a, i, a') T2[a', b, i, l]."""
+      W'[a s + b, l]   = sum_{a', i} Y_k(a, i, a') T2[a', b, i, l].
+    With fmt != "fp64" every operand of the three products is rounded by
+    round_operand (exact float64 accumulation)."""
+    q = lambda x: round_operand(x, fmt)
     d = len(Y)
     W = [None] * (d + 1)
     W[d] = np.ones((1, 1))
@@ -108,9 +141,9 @@ def hpcrl1_contract(Y, Z, R, normalize=True):
         s0, _, s1 = zk.shape
         l0, _, l1 = rk.shape
         Wm = W[k + 1].reshape(r1, s1, l1)
-        T1 = np.einsum("abg,lig->abil", Wm, rk)
-        T2 = np.einsum("cib,abil->acil", zk, T1)
-        T3 = np.einsum("xia,acil->xcl", yk, T2)
+        T1 = np.einsum("abg,lig->abil", q(Wm), q(rk))
+        T2 = np.einsum("cib,abil->acil", q(zk), q(T1))
+        T3 = np.einsum("xia,acil->xcl", q(yk), q(T2))
         w = T3.reshape(r0 * s0, l0)
         if normalize:
             nw = np.linalg.norm(w)
@@ -194,7 +227,8 @@ def truncate_rl(X, max_rank=0, tol=0.0):
 # ------------------------------------------------------------ end to end ---
 
 def hadamard_recompress(Y, Z, max_rank=0, tol=0.0, sketch_rank=0, oversample=10,
-                        seed=0, normalize=True, coding="contract", return_info=False):
+                        seed=0, normalize=True, coding="contract", return_info=False,
+                        fmt="fp64"):
     """Recompress Y ⊙ Z with HaTT-1 (Algorithm 4) and the optional truncation.
 
     coding="contract" uses the three-stage contraction for HPCRL and the core
@@ -209,7 +243,7 @@ def hadamard_recompress(Y, Z, max_rank=0, tol=0.0, sketch_rank=0, oversample=10,
     if coding == "paper":
         W = hpcrl1_wlwr(Y, Z, R, normalize)
     else:
-        W = hpcrl1_contract(Y, Z, R, normalize)
+        W = hpcrl1_contract(Y, Z, R, normalize, fmt)
     X = hatt1_sweep(Y, Z, W, paper_form=(coding == "paper"))
     cap = int(max_rank) if max_rank > 0 else 0
     need_trunc = d > 1 and (tol > 0 or (cap > 0 and any(e > cap for e in ell)))

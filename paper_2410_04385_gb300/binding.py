@@ -18,6 +18,9 @@ LIB_PATH = os.path.join(_PKG, "_lib", "libhatt.so")
 
 TT_OK = 0
 TT_FP64 = 0
+TT_MIXED_FP32 = 1
+TT_MIXED_TF32 = 2
+TT_MIXED_BF16 = 3
 TT_MAX_SMALL_RANK = 128
 
 
@@ -249,10 +252,11 @@ class HadamardRecompressor:
 
 
 def tt_hadamard_recompress(Y, Z, max_rank=0, tol=0.0, sketch_rank=0, oversample=10, seed=0,
-                           stream=None) -> List[torch.Tensor]:
-    """HaTT-1 recompression of Y ⊙ Z; returns the output cores (synchronizes)."""
+                           precision=TT_FP64, stream=None) -> List[torch.Tensor]:
+    """HaTT-1 recompression of Y ⊙ Z; returns the output cores (synchronizes).
+    precision: TT_FP64, or TT_MIXED_FP32 / TF32 / BF16 for the sketches."""
     h = HadamardRecompressor(Y, Z, max_rank=max_rank, tol=tol, sketch_rank=sketch_rank,
-                             oversample=oversample, seed=seed)
+                             oversample=oversample, seed=seed, precision=precision)
     h.run(stream)
     (stream or torch.cuda.current_stream()).synchronize()
     return [c.clone() for c in h.result()]

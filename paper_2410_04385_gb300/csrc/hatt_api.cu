@@ -194,6 +194,7 @@ struct HattArgs {
   int cap;
   double tol;
   uint64_t seed;
+  int prec = hatt::kPrecFP64;   // arithmetic of the HPCRL-1 products (A2/A3)
 };
 
 struct HattBufs {
@@ -295,6 +296,7 @@ void run_hatt(Runner &run, const HattArgs &a, const HattBufs &b) {
       g.B = Rk; g.sB1 = l1; g.sBk = 1; g.sBn = (ll)nk * l1;
       g.C = b.T1; g.sC1 = (ll)r1 * s1 * l0; g.sCm = l0; g.sCn = 1;
       g.alpha_dev = b.winv ? b.winv + (k + 1) : nullptr;
+      g.prec = a.prec;
       run.gemm(g);
     }
     {   // S2: T2[i][a'][b][lam] = sum_b' Z_k[b][i][b'] T1[i][a'][b'][lam]
@@ -304,6 +306,7 @@ void run_hatt(Runner &run, const HattArgs &a, const HattBufs &b) {
       g.A = a.Y ? a.Z[k] : nullptr; g.sA1 = s1; g.sA2 = 0; g.sAm = (ll)nk * s1; g.sAk = 1;
       g.B = b.T1; g.sB1 = (ll)r1 * s1 * l0; g.sB2 = (ll)s1 * l0; g.sBk = l0; g.sBn = 1;
       g.C = b.T2; g.sC1 = (ll)r1 * s0 * l0; g.sC2 = (ll)s0 * l0; g.sCm = l0; g.sCn = 1;
+      g.prec = a.prec;
       run.gemm(g);
     }
     {   // S3: W[a][b][lam] = sum_{i,a'} Y_k[a][i][a'] T2[i][a'][b][lam]
@@ -312,6 +315,7 @@ void run_hatt(Runner &run, const HattArgs &a, const HattBufs &b) {
       g.A = a.Y ? a.Y[k] : nullptr; g.sAm = (ll)nk * r1; g.sAk = 1;
       g.B = b.T2; g.sBk = (ll)s0 * l0; g.sBn = 1;
       g.C = Wk(k); g.sCm = (ll)s0 * l0; g.sCn = 1;
+      g.prec = a.prec;
       run.gemm(g);
     }
     if (run.live())
@@ -397,8 +401,9 @@ int prepare_hatt(const tt_t *Y, const tt_t *Z, const tt_opts *o, bool need_cores
   if (o->max_rank < 0 || o->sketch_rank < 0 || o->oversample < 0 || !(o->tol >= 0.0) ||
       !std::isfinite(o->tol))
     return TT_ERR_ARG;
-  if (o->precision != TT_FP64) return TT_ERR_ARG;
+  if (o->precision < TT_FP64 || o->precision > TT_MIXED_BF16) return TT_ERR_ARG;
   if (o->variant != 1) return TT_ERR_ARG;
+  a.prec = o->precision;
   const int d = Y->d;
   a.d = d;
   a.n = Y->n;

@@ -40,6 +40,10 @@ constexpr int kMaxOrder = 512;   // largest d handled by the parameter tables
 // beta == 0 never reads C. When the planner splits K, partial sums go to a
 // workspace buffer and a second kernel reduces them in a fixed order, so the
 // result is bitwise reproducible.
+// Arithmetic of a GEMM: FP64 throughout, or operands rounded to FP32 / TF32 /
+// BF16 with FP32 accumulation (the values match tt_precision).
+constexpr int kPrecFP64 = 0, kPrecFP32 = 1, kPrecTF32 = 2, kPrecBF16 = 3;
+
 struct Gemm {
   int M = 0, N = 0, K = 0;
   int batch = 1, bdiv = 1;
@@ -51,6 +55,7 @@ struct Gemm {
   double alpha = 1.0, beta = 0.0;
   const double *alpha_dev = nullptr;
   const int *skip_dev = nullptr;   // if set and *skip_dev != 0 the launch does nothing
+  int prec = 0;                    // kPrecFP64, or the operand type of a low-precision product
 };
 
 // Doubles of split-K scratch this GEMM needs (0 if it runs unsplit).

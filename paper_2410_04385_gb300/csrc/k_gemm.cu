@@ -17,6 +17,7 @@
 //     second kernel is launched.
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 #include "hatt_internal.cuh"
 
@@ -33,14 +34,31 @@ struct Launch {
   int bm, bn, tiles_m, tiles_n, ksplit, kchunk, out;
 };
 
-template <int OUT>
+// Operand of a low-precision product: FP64 -> FP32 (round to nearest even),
+// then, for TF32, round to nearest with ties away from zero at 10 mantissa
+// bits, and for BF16 round to nearest even at 7 mantissa bits: the values a
+// tensor core multiplies (exactly) and accumulates in FP32.
+__device__ __forceinline__ float round_operand(double x, int prec) {
+  const float f = (float)x;
+  unsigned u = __float_as_uint(f);
+  if (prec == kPrecTF32) u = (u + 0x1000u) & 0xFFFFE000u;
+  else if (prec == kPrecBF16) u = (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
+  return __uint_as_float(u);
+}
+
+// LOWP = false: FP64 operands and accumulators. LOWP = true: operands rounded
+// to g.prec as they are staged (above) and FP32 accumulators; the result is
+// written in FP64 (scaled by alpha in FP64).
+template <int OUT, bool LOWP>
 __global__ void __launch_bounds__(kThreads)
 gemm_f64_kernel(Gemm g, int bm, int bn, int tiles_n, int tiles_m, int ksplit, int kchunk,
                 double *partial, int *counters) {
+  using T = typename std::conditional<LOWP, float, double>::type;
   if (g.skip_dev && *g.skip_dev) return;
-  __shared__ double As[kBK][kMaxTile + 1];
-  __shared__ double Bs[kBK][kMaxTile + 1];
+  __shared__ T As[kBK][kMaxTile + 1];
+  __shared__ T Bs[kBK][kMaxTile + 1];
   __shared__ int s_last;
+  const int prec = g.prec;
   const int tid = threadIdx.x;
   // 1-D grid: block -> (n tile, m tile, split, batch), n tile fastest
   long long blk = blockIdx.x;
@@ -57,7 +75,7 @@ gemm_f64_kernel(Gemm g, int bm, int bn, int tiles_n, int tiles_m, int ksplit, in
   const int outs = bm * bn;
 
   int om[OUT], on[OUT];
-  double acc[OUT];
+  T acc[OUT];
 #pragma unroll
   for (int q = 0; q < OUT; ++q) {
     const int o = tid + kThreads * q;
@@ -74,13 +92,15 @@ gemm_f64_kernel(Gemm g, int bm, int bn, int tiles_n, int tiles_m, int ksplit, in
       int mm, kk;
       if (a_kfast) { mm = e / kBK; kk = e % kBK; } else { kk = e / bm; mm = e % bm; }
       const int gm = m0 + mm, gk = kt + kk;
-      As[kk][mm] = (gm < g.M && gk < kend) ? A[gm * g.sAm + gk * g.sAk] : 0.0;
+      const double v = (gm < g.M && gk < kend) ? A[gm * g.sAm + gk * g.sAk] : 0.0;
+      if (LOWP) As[kk][mm] = round_operand(v, prec); else As[kk][mm] = v;
     }
     for (int e = tid; e < bn * kBK; e += kThreads) {
       int nn, kk;
       if (b_nfast) { kk = e / bn; nn = e % bn; } else { nn = e / kBK; kk = e % kBK; }
       const int gn = n0 + nn, gk = kt + kk;
-      Bs[kk][nn] = (gn < g.N && gk < kend) ? B[gk * g.sBk + gn * g.sBn] : 0.0;
+      const double v = (gn < g.N && gk < kend) ? B[gk * g.sBk + gn * g.sBn] : 0.0;
+      if (LOWP) Bs[kk][nn] = round_operand(v, prec); else Bs[kk][nn] = v;
     }
     __syncthreads();
     // exact depth: a ragged last k-tile issues no DFMAs on zero padding
@@ -112,7 +132,7 @@ gemm_f64_kernel(Gemm g, int bm, int bn, int tiles_n, int tiles_m, int ksplit, in
     for (int q = 0; q < OUT; ++q) {
       if (q >= nq) break;
       const int gm = m0 + om[q], gn = n0 + on[q];
-      if (gm < g.M && gn < g.N) P[(long long)gm * g.N + gn] = acc[q];
+      if (gm < g.M && gn < g.N) P[(long long)gm * g.N + gn] = (double)acc[q];
     }
     // publish this partial, then let the last of the tile's ksplit blocks sum
     __threadfence();
@@ -133,7 +153,7 @@ gemm_f64_kernel(Gemm g, int bm, int bn, int tiles_n, int tiles_m, int ksplit, in
       if (gm >= g.M || gn >= g.N) continue;
       const long long e = (long long)gm * g.N + gn;
       double sum = 0.0;
-      for (int k = 0; k < ksplit; ++k) sum += (k == ks) ? acc[q] : __ldcg(P0 + k * mn + e);
+      for (int k = 0; k < ksplit; ++k) sum += (k == ks) ? (double)acc[q] : __ldcg(P0 + k * mn + e);
       double *c = C + gm * g.sCm + gn * g.sCn;
       const double v = alpha * sum;
       *c = (g.beta != 0.0) ? fma(g.beta, *c, v) : v;
@@ -146,7 +166,7 @@ gemm_f64_kernel(Gemm g, int bm, int bn, int tiles_n, int tiles_m, int ksplit, in
     const int gm = m0 + om[q], gn = n0 + on[q];
     if (gm >= g.M || gn >= g.N) continue;
     double *c = C + gm * g.sCm + gn * g.sCn;
-    const double v = alpha * acc[q];
+    const double v = alpha * (double)acc[q];
     *c = (g.beta != 0.0) ? fma(g.beta, *c, v) : v;
   }
 }
@@ -248,9 +268,12 @@ template <int OUT>
 void launch_tile(const Gemm &g, const Launch &L, double *scratch, int *counters,
                  cudaStream_t st) {
   const long long blocks = (long long)L.tiles_n * L.tiles_m * L.ksplit * g.batch;
-  gemm_f64_kernel<OUT><<<(unsigned)blocks, kThreads, 0, st>>>(g, L.bm, L.bn, L.tiles_n,
-                                                             L.tiles_m, L.ksplit, L.kchunk,
-                                                             scratch, counters);
+  if (g.prec == kPrecFP64)
+    gemm_f64_kernel<OUT, false><<<(unsigned)blocks, kThreads, 0, st>>>(
+        g, L.bm, L.bn, L.tiles_n, L.tiles_m, L.ksplit, L.kchunk, scratch, counters);
+  else
+    gemm_f64_kernel<OUT, true><<<(unsigned)blocks, kThreads, 0, st>>>(
+        g, L.bm, L.bn, L.tiles_n, L.tiles_m, L.ksplit, L.kchunk, scratch, counters);
   note_launch();
 }
 

@@ -188,3 +188,16 @@ def test_kernel_timer_argument_checks(lib):
     assert lib.tt_kernel_timer_stop(ms, fl, 4, ctypes.byref(cnt)) == 3
     assert lib.tt_kernel_timer_stop(None, None, 4, None) == 3
     assert lib.tt_kernel_timer_stop(ms, fl, -1, None) == 3
+
+
+def test_binding_entry_points_accept_every_option():
+    """The Python wrappers pass every tt_opts field through (marshalling only)."""
+    import inspect
+    fields = {name for name, _ in B.OptsStruct._fields_} - {"variant"}
+    assert fields <= set(inspect.signature(B.make_opts).parameters)
+    assert fields <= set(inspect.signature(B.tt_hadamard_recompress).parameters)
+    assert (B.TT_FP64, B.TT_MIXED_FP32, B.TT_MIXED_TF32, B.TT_MIXED_BF16) == (0, 1, 2, 3)
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                            "include", "hatt.h")).read()
+    for name, v in (("TT_FP64", 0), ("TT_MIXED_FP32", 1), ("TT_MIXED_TF32", 2), ("TT_MIXED_BF16", 3)):
+        assert re.search(rf"{name}\s*=\s*{v}\b", hdr)
