@@ -219,6 +219,14 @@ int64_t tt_launch_count(void);
 int tt_kernel_timer_start(int32_t capacity);
 int tt_kernel_timer_stop(double *ms, double *flops, int32_t capacity, int64_t *count);
 
+/* Device error word, a diagnostic with no counterpart in the paper: set when
+ * a bounded wait inside a kernel runs out (the tensor-core products wait on
+ * an mbarrier for their own MMAs); that kernel writes NaN to its outputs,
+ * frees its tensor memory and returns, so nothing hangs or traps. Writes the
+ * word to *value (host) and clears it; synchronizes the current device.
+ * TT_ERR_ARG if value is NULL, TT_ERR_CUDA if the device cannot be read. */
+int tt_device_error(int32_t *value);
+
 /* Static description of a status code (never NULL). */
 const char *tt_status_string(int status);
 

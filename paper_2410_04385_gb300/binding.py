@@ -56,7 +56,7 @@ _lib = None
 EXPORTS = ("tt_hadamard_recompress_plan", "tt_hadamard_recompress", "tt_round_plan", "tt_round",
            "tt_dot_plan", "tt_dot", "tt_dot_noalloc", "tt_norm", "tt_sketch_tt",
            "tt_philox4x32_10", "tt_launch_count", "tt_kernel_timer_start",
-           "tt_kernel_timer_stop", "tt_status_string")
+           "tt_kernel_timer_stop", "tt_device_error", "tt_status_string")
 
 
 def load(path: Optional[str] = None):
@@ -91,6 +91,7 @@ def load(path: Optional[str] = None):
     lib.tt_launch_count.restype = ctypes.c_int64
     lib.tt_launch_count.argtypes = []
     lib.tt_kernel_timer_start.argtypes = [ctypes.c_int32]
+    lib.tt_device_error.argtypes = [P(ctypes.c_int32)]
     lib.tt_kernel_timer_stop.argtypes = [P(ctypes.c_double), P(ctypes.c_double), ctypes.c_int32,
                                          P(ctypes.c_int64)]
     for name in EXPORTS:
@@ -103,6 +104,14 @@ def load(path: Optional[str] = None):
 def launch_count() -> int:
     """Kernels enqueued by libhatt in this process so far."""
     return int(load().tt_launch_count())
+
+
+def device_error() -> int:
+    """Read and clear the device error word (synchronizes): nonzero when a
+    bounded wait inside a kernel ran out since the last read."""
+    v = ctypes.c_int32(0)
+    _check("tt_device_error", load().tt_device_error(ctypes.byref(v)))
+    return int(v.value)
 
 
 def kernel_timer_start(capacity: int) -> None:

@@ -870,6 +870,17 @@ int tt_sketch_tt(int32_t d, const int64_t *n, const int64_t *ell, uint64_t seed,
 
 int64_t tt_launch_count(void) { return (int64_t)hatt::launch_count(); }
 
+int tt_device_error(int32_t *value) {
+  if (!value) return TT_ERR_ARG;
+  int v = 0;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = hatt::read_device_error(&v);
+  if (e == cudaSuccess && v != 0) e = hatt::clear_device_error();
+  if (e != cudaSuccess) return from_cuda(e);
+  *value = v;
+  return TT_OK;
+}
+
 int tt_kernel_timer_start(int32_t capacity) {
   if (capacity < 1 || capacity > (1 << 20)) return TT_ERR_ARG;
   std::lock_guard<std::mutex> lk(hatt::g_timer.mu);

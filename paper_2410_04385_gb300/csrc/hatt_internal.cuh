@@ -60,6 +60,16 @@ struct Gemm {
 
 // Doubles of split-K scratch this GEMM needs (0 if it runs unsplit).
 size_t gemm_scratch_doubles(const Gemm &g);
+// TF32 / BF16 products on the tensor cores (tcgen05, FP32 accumulator in
+// tensor memory); gemm_f64 dispatches to them by g.prec.
+bool gemm_tc_supported(const Gemm &g);
+size_t gemm_tc_scratch_doubles(const Gemm &g);
+cudaError_t gemm_tc(const Gemm &g, double *scratch, int *counters, cudaStream_t st);
+// Error word set by a device wait that ran out (the kernel wrote NaN to its
+// outputs, freed its tensor memory and returned): read (synchronizing the
+// device) and clear it.
+cudaError_t read_device_error(int *value);
+cudaError_t clear_device_error();
 // Enqueue; `scratch` must hold gemm_scratch_doubles(g) doubles.
 cudaError_t gemm_f64(const Gemm &g, double *scratch, cudaStream_t st);
 

@@ -281,6 +281,7 @@ void launch_tile(const Gemm &g, const Launch &L, double *scratch, int *counters,
 
 size_t gemm_scratch_doubles(const Gemm &g) {
   if (g.M <= 0 || g.N <= 0 || g.K <= 0) return 0;
+  if (gemm_tc_supported(g)) return gemm_tc_scratch_doubles(g);
   const Launch L = plan(g);
   return L.ksplit > 1 ? (size_t)L.ksplit * g.batch * (size_t)g.M * g.N : 0;
 }
@@ -289,6 +290,12 @@ cudaError_t gemm_f64(const Gemm &g, double *scratch, cudaStream_t st) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
   if (g.K <= 0) {
     return cudaErrorInvalidValue;   // callers never issue empty contractions
+  }
+  if (gemm_tc_supported(g)) {                     // TF32 / BF16 operands: tensor cores
+    const int slot = timer_begin(st);
+    const cudaError_t e = gemm_tc(g, scratch, tile_counters(), st);
+    timer_end(slot, st, 2.0 * g.M * g.N * (double)g.K * g.batch);
+    return e;
   }
   const Launch L = plan(g);
   int *counters = tile_counters();

@@ -86,6 +86,30 @@ def test_rank_deficient_sketch_meets_the_per_config_bound(B, prec):
     assert eg <= 10 * max(e64, eem)
 
 
+def test_no_device_wait_ran_out(B):
+    """The tensor-core products wait on an mbarrier with a bounded loop; none
+    of the runs above may have hit the bound."""
+    assert B.device_error() == 0
+
+
+def test_tensor_core_products_match_simt_rounding_model(B):
+    """The TF32 / BF16 products run on tcgen05; their result equals the
+    exact product of the rounded operands up to FP32 accumulation, checked
+    through a one-core-deep chain against the emulation on a shape that
+    spans several 128-row tiles, a ragged N and split K."""
+    n = [40, 40, 40]
+    Y = wl.gaussian_tt(n, [1, 37, 29, 1], 41)
+    Z = wl.gaussian_tt(n, [1, 23, 31, 1], 42)
+    for prec in (2, 3):
+        Xg = run_gpu(B, Y, Z, sketch_rank=40, seed=9, precision=prec)
+        Xo = ohatt.hadamard_recompress(Y, Z, sketch_rank=40, seed=9, fmt=FMT[prec])
+        A = ott.tt_full(Y) * ott.tt_full(Z)
+        eg = np.linalg.norm(ott.tt_full(Xg) - A) / np.linalg.norm(A)
+        eo = np.linalg.norm(ott.tt_full(Xo) - A) / np.linalg.norm(A)
+        assert eg <= 10 * max(eo, 1e-14) and eo <= 10 * max(eg, 1e-14)
+    assert B.device_error() == 0
+
+
 def test_rejects_unknown_precision(B):
     Y, Z, _ = wl.workload_small_sin_times_random()
     with pytest.raises(B.HattError):
