@@ -62,6 +62,52 @@ def gemm_traffic_per_launch():
     return prof.get("dram_bytes_per_launch")
 
 
+def sampled_entries(cores, idx):
+    """Entries of a TT at the multi-indices idx (samples x d), float64."""
+    import numpy as np
+    M = np.ones((idx.shape[0], 1))
+    for k, c in enumerate(cores):
+        M = np.einsum("sa,sab->sb", M, c[:, idx[:, k], :].transpose(1, 0, 2))
+    return M[:, 0]
+
+
+def run_mixed_cfg3(binding, workloads, dev, samples=2000, steps=2):
+    """Smooth TT pair d=50, n=64, ranks 40 (sketch 90, target 80, tol 1e-8) in
+    every precision: device time per recompression (graph replay, CUDA events)
+    and the relative error on sampled entries against the exact product."""
+    import numpy as np
+    import torch
+    Y, Z, opts = workloads.workload_smooth_d50()
+    idx = np.random.default_rng(0).integers(0, 64, size=(samples, len(Y)))
+    exact = sampled_entries(Y, idx) * sampled_entries(Z, idx)
+    Yg = [torch.from_numpy(c).to(dev) for c in Y]
+    Zg = [torch.from_numpy(c).to(dev) for c in Z]
+    out = {"workload": "smooth TT pair d=50, n=64, ranks 40, sketch 90, max rank 80, tol 1e-8",
+           "error": f"relative, on {samples} sampled entries, against Y*Z", "per_precision": {}}
+    for prec, name in ((0, "fp64"), (1, "fp32"), (2, "tf32"), (3, "bf16")):
+        h = binding.HadamardRecompressor(Yg, Zg, seed=SKETCH_SEED, precision=prec, **opts)
+        h.run()
+        h.capture()
+        h.replay()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            h.replay()
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        X = [c.cpu().numpy() for c in h.result()]
+        x = sampled_entries(X, idx)
+        err = float(np.sqrt(np.sum((x - exact) ** 2) / np.sum(exact ** 2)))
+        out["per_precision"][name] = {"ms_per_recompression": min(ms), "rel_error_sampled": err,
+                                      "max_rank": int(max(h.Xd.r))}
+        del h
+    out["device_error"] = binding.device_error()
+    return out
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -70,6 +116,8 @@ def parse():
     p.add_argument("--impl", choices=["hatt", "reference"], default="hatt")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-pkp", action="store_true")
+    p.add_argument("--no-mixed", action="store_true",
+                   help="skip the per-precision run of the smooth d=50 workload")
     p.add_argument("--cpu-leg", default=None, help=argparse.SUPPRESS)
     p.add_argument("--gpu-result", default=None, help=argparse.SUPPRESS)
     p.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -414,6 +462,10 @@ def main():
                                      "with torch.linalg (cuSOLVER) FP64 QR/SVD on the same GPU"}
         line["speedup_vs_pkp_round"] = (1000.0 / ms) * pkp_s
         del B
+
+    # ---- mixed-precision sketches on the smooth d=50 workload ----
+    if not args.no_mixed and rank == 0:
+        line["mixed_cfg3"] = run_mixed_cfg3(binding, workloads, dev)
 
     # ---- CPU oracle baseline and the error gate ----
     if not args.no_cpu_baseline and rank == 0:
