@@ -72,7 +72,14 @@ typedef enum {
   TT_FP64 = 0,           /* every step in IEEE binary64 */
   TT_MIXED_FP32 = 1,     /* HPCRL-1 products: FP32 operands, FP32 accumulation */
   TT_MIXED_TF32 = 2,     /* HPCRL-1 products: TF32 operands, FP32 accumulation */
-  TT_MIXED_BF16 = 3      /* HPCRL-1 products: BF16 operands, FP32 accumulation */
+  TT_MIXED_BF16 = 3,     /* HPCRL-1 products: BF16 operands, FP32 accumulation */
+  TT_FP64_TC = 4         /* FP64 accuracy throughout; large products (max(M, N) >= 128,
+                            K >= 128, >= 2e7 flops) on the BF16 tensor cores: each row /
+                            column scaled by a power of two and cut into 9 slices of 6
+                            bits, slice products accumulated exactly in FP32 (<= 9 pairs
+                            per level, <= 448 terms of K per accumulation), levels
+                            combined in FP64; the error is that of an FP64 product
+                            (within 2^-54 of each row's and column's largest entry) */
 } tt_precision;
 
 /* Options of tt_hadamard_recompress (the problem statement of Algorithm 4:

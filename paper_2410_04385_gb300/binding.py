@@ -21,6 +21,7 @@ TT_FP64 = 0
 TT_MIXED_FP32 = 1
 TT_MIXED_TF32 = 2
 TT_MIXED_BF16 = 3
+TT_FP64_TC = 4
 TT_MAX_SMALL_RANK = 128
 
 

@@ -401,9 +401,9 @@ int prepare_hatt(const tt_t *Y, const tt_t *Z, const tt_opts *o, bool need_cores
   if (o->max_rank < 0 || o->sketch_rank < 0 || o->oversample < 0 || !(o->tol >= 0.0) ||
       !std::isfinite(o->tol))
     return TT_ERR_ARG;
-  if (o->precision < TT_FP64 || o->precision > TT_MIXED_BF16) return TT_ERR_ARG;
+  if (o->precision < TT_FP64 || o->precision > TT_FP64_TC) return TT_ERR_ARG;
   if (o->variant != 1) return TT_ERR_ARG;
-  a.prec = o->precision;
+  a.prec = o->precision == TT_FP64_TC ? hatt::kPrecFP64 : o->precision;
   const int d = Y->d;
   a.d = d;
   a.n = Y->n;
@@ -617,6 +617,12 @@ size_t measure(Carve carve, Run runf) {
   return ws.off + 256;
 }
 
+// Switches the FP64-accurate tensor-core products on for one call.
+struct Fp64TcScope {
+  explicit Fp64TcScope(bool on) { hatt::set_fp64_tensor_cores(on); }
+  ~Fp64TcScope() { hatt::set_fp64_tensor_cores(false); }
+};
+
 // Makes a tile-counter array current for the calling thread during one call.
 struct TileCounterScope {
   explicit TileCounterScope(int *p) { hatt::set_tile_counters(p); }
@@ -725,6 +731,7 @@ int tt_hadamard_recompress_plan(const tt_t *Y, const tt_t *Z, const tt_opts *opt
   a.Y = nullptr;
   a.Z = nullptr;
   a.Xout = nullptr;
+  Fp64TcScope tc(opts->precision == TT_FP64_TC);
   *workspace_bytes = measure([&](Ws &ws) { return carve_hatt(ws, a); },
                              [&](Runner &run, const HattBufs &b) { run_hatt(run, a, b); });
   return TT_OK;
@@ -756,6 +763,7 @@ int tt_hadamard_recompress(const tt_t *Y, const tt_t *Z, const tt_opts *opts, tt
   a.Z = Z->cores;
   a.Xout = X->cores;
   cudaStream_t strm = (cudaStream_t)stream;
+  Fp64TcScope tc(opts->precision == TT_FP64_TC);
   HattBufs bufs_for_ranks;
   st = execute(workspace, workspace_bytes, strm,
                [&](Ws &ws) {

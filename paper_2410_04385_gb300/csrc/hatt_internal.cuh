@@ -65,6 +65,14 @@ size_t gemm_scratch_doubles(const Gemm &g);
 bool gemm_tc_supported(const Gemm &g);
 size_t gemm_tc_scratch_doubles(const Gemm &g);
 cudaError_t gemm_tc(const Gemm &g, double *scratch, int *counters, cudaStream_t st);
+// FP64-accurate products on the BF16 tensor cores (slices of 6 bits, exact
+// FP32 accumulation per level): gemm_f64 uses them for large FP64 products
+// while the calling thread has switched them on.
+void set_fp64_tensor_cores(bool on);
+bool gemm_oz_applicable(const Gemm &g);
+size_t gemm_oz_scratch_doubles(const Gemm &g);
+cudaError_t gemm_oz(const Gemm &g, double *scratch, cudaStream_t st);
+cudaError_t oz_error_word(int *value, bool clear);
 // Error word set by a device wait that ran out (the kernel wrote NaN to its
 // outputs, freed its tensor memory and returned): read (synchronizing the
 // device) and clear it.

@@ -282,6 +282,7 @@ void launch_tile(const Gemm &g, const Launch &L, double *scratch, int *counters,
 size_t gemm_scratch_doubles(const Gemm &g) {
   if (g.M <= 0 || g.N <= 0 || g.K <= 0) return 0;
   if (gemm_tc_supported(g)) return gemm_tc_scratch_doubles(g);
+  if (gemm_oz_applicable(g)) return gemm_oz_scratch_doubles(g);
   const Launch L = plan(g);
   return L.ksplit > 1 ? (size_t)L.ksplit * g.batch * (size_t)g.M * g.N : 0;
 }
@@ -294,6 +295,12 @@ cudaError_t gemm_f64(const Gemm &g, double *scratch, cudaStream_t st) {
   if (gemm_tc_supported(g)) {                     // TF32 / BF16 operands: tensor cores
     const int slot = timer_begin(st);
     const cudaError_t e = gemm_tc(g, scratch, tile_counters(), st);
+    timer_end(slot, st, 2.0 * g.M * g.N * (double)g.K * g.batch);
+    return e;
+  }
+  if (gemm_oz_applicable(g)) {                    // FP64 accuracy on BF16 tensor cores
+    const int slot = timer_begin(st);
+    const cudaError_t e = gemm_oz(g, scratch, st);
     timer_end(slot, st, 2.0 * g.M * g.N * (double)g.K * g.batch);
     return e;
   }

@@ -275,12 +275,19 @@ TcLaunch tc_plan(const Gemm &g) {
 }  // namespace
 
 cudaError_t read_device_error(int *value) {
-  return cudaMemcpyFromSymbol(value, g_device_error, sizeof(int));
+  int oz = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(value, g_device_error, sizeof(int));
+  if (e == cudaSuccess) e = oz_error_word(&oz, false);
+  if (e == cudaSuccess) *value |= oz;
+  return e;
 }
 
 cudaError_t clear_device_error() {
   const int zero = 0;
-  return cudaMemcpyToSymbol(g_device_error, &zero, sizeof(int));
+  int oz = 0;
+  cudaError_t e = cudaMemcpyToSymbol(g_device_error, &zero, sizeof(int));
+  if (e == cudaSuccess) e = oz_error_word(&oz, true);
+  return e;
 }
 
 bool gemm_tc_supported(const Gemm &g) {
