@@ -62,6 +62,24 @@ def gemm_traffic_per_launch():
     return prof.get("dram_bytes_per_launch")
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest per-rank value (the job's step time is its slowest rank's);
+    identity on one rank. Uses the default process group (NCCL on GPUs)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(ms_per_step: float, world: int) -> float:
+    """Whole-job recompressions per second: every rank recompresses its own
+    pair per step (replicas), so N pairs per max-over-ranks step time."""
+    return world * 1000.0 / ms_per_step
+
+
 def sampled_entries(cores, idx):
     """Entries of a TT at the multi-indices idx (samples x d), float64."""
     import numpy as np
@@ -353,12 +371,8 @@ def main():
     wall = time.perf_counter() - wall0
     clocks = sampler.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    ms = statistics.mean(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * 1000.0 / ms
+    ms = max_over_ranks(statistics.mean(step_ms), world, dev)
+    value = job_throughput(ms, world)
 
     # ---- end to end through the C ABI with host buffers (pinned) ----
     Yh = [c.cpu().pin_memory() for c in Yg]
