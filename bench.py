@@ -89,6 +89,40 @@ def sampled_entries(cores, idx):
     return M[:, 0]
 
 
+def run_batch_cfg4(binding, workloads, dev, lanes=16):
+    """256 independent pairs (d in [10, 40], n in {16, 32, 64}, inner ranks in
+    [8, 48], target 2 max(r_Y, r_Z), FP32 sketches, FP64 QR / projection /
+    truncation) recompressed by one batched call over `lanes` library streams,
+    against the same call with one lane (the pairs one after another on one
+    stream). Device time of one whole batch each (CUDA events)."""
+    import torch
+    pairs = workloads.workload_batch_uneven()
+    gpu = [([torch.from_numpy(c).to(dev) for c in Y], [torch.from_numpy(c).to(dev) for c in Z],
+            dict(o, precision=binding.TT_MIXED_FP32, seed=j)) for j, (Y, Z, o) in enumerate(pairs)]
+    out = {"workload": "256 TT pairs, d 10-40, n 16/32/64, ranks 8-48, target 2 max(r), "
+                       "FP32 sketch, FP64 QR / projection / truncation",
+           "unit": "recompressions/s"}
+    for name, nl in (("one_lane", 1), (f"{lanes}_lanes", lanes)):
+        b = binding.BatchRecompressor(gpu, lanes=nl)
+        b.run()
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record()
+        b.run()
+        s1.record()
+        torch.cuda.synchronize()
+        ms = s0.elapsed_time(s1)
+        out[name] = {"ms_per_batch": ms, "value": 1000.0 * len(gpu) / ms,
+                     "workspace_gb": b.workspace_bytes / 1e9}
+        del b
+        torch.cuda.empty_cache()
+    out["speedup_batched"] = out["one_lane"]["ms_per_batch"] / out[f"{lanes}_lanes"]["ms_per_batch"]
+    out["device_error"] = binding.device_error()
+    del gpu
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_mixed_cfg3(binding, workloads, dev, samples=2000, steps=2):
     """Smooth TT pair d=50, n=64, ranks 40 (sketch 90, target 80, tol 1e-8) in
     every precision: device time per recompression (graph replay, CUDA events)
@@ -134,6 +168,8 @@ def parse():
     p.add_argument("--impl", choices=["hatt", "reference"], default="hatt")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-pkp", action="store_true")
+    p.add_argument("--no-batch", action="store_true",
+                   help="skip the 256-pair batched run (about a minute)")
     p.add_argument("--no-mixed", action="store_true",
                    help="skip the per-precision run of the smooth d=50 workload")
     p.add_argument("--cpu-leg", default=None, help=argparse.SUPPRESS)
@@ -480,6 +516,10 @@ def main():
     # ---- mixed-precision sketches on the smooth d=50 workload ----
     if not args.no_mixed and rank == 0:
         line["mixed_cfg3"] = run_mixed_cfg3(binding, workloads, dev)
+
+    # ---- many uneven pairs: batched over library streams vs one after another ----
+    if not args.no_batch and rank == 0:
+        line["batch_cfg4"] = run_batch_cfg4(binding, workloads, dev)
 
     # ---- CPU oracle baseline and the error gate ----
     if not args.no_cpu_baseline and rank == 0:

@@ -143,6 +143,29 @@ int tt_hadamard_recompress_plan(const tt_t *Y, const tt_t *Z, const tt_opts *opt
 int tt_hadamard_recompress(const tt_t *Y, const tt_t *Z, const tt_opts *opts, tt_t *X,
                            void *workspace, size_t workspace_bytes, void *stream);
 
+/* Many independent recompressions in one call (pairs of uneven order, mode
+ * sizes and ranks; no counterpart in the paper, whose experiments run one
+ * pair at a time). A single small pair leaves most of the GPU idle, so the
+ * pairs are spread over `lanes` library-owned CUDA streams (pair j on lane
+ * j % lanes, in order within a lane): the caller's `stream` forks into the
+ * lanes through an event and waits for all of them at the end, so the call
+ * stays stream-ordered (and capturable into a CUDA graph, after a first call
+ * outside capture has created the library's streams and events on this
+ * device). Each lane reuses one region of the workspace for its pairs.
+ *   count            number of pairs (>= 0)
+ *   Y, Z, opts, X    host arrays of `count` (as for tt_hadamard_recompress;
+ *                    X[j] sized from that pair's tt_hadamard_recompress_plan)
+ *   lanes            1..32
+ *   workspace        device, 256-byte aligned, at least the batch plan's size
+ * Every pair is validated before anything is enqueued; the first pair's
+ * error code is returned. */
+int tt_hadamard_recompress_batch_plan(int32_t count, const tt_t *Y, const tt_t *Z,
+                                      const tt_opts *opts, int32_t lanes,
+                                      size_t *workspace_bytes);
+int tt_hadamard_recompress_batch(int32_t count, const tt_t *Y, const tt_t *Z,
+                                 const tt_opts *opts, tt_t *X, int32_t lanes, void *workspace,
+                                 size_t workspace_bytes, void *stream);
+
 /* Workspace size of tt_round and its output rank bound (min(r_k, max_rank)
  * clamped by the mode-size products), both host outputs. */
 int tt_round_plan(const tt_t *A, int64_t max_rank, double tol, int64_t *out_rank_bound,

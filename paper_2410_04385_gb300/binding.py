@@ -57,7 +57,8 @@ _lib = None
 EXPORTS = ("tt_hadamard_recompress_plan", "tt_hadamard_recompress", "tt_round_plan", "tt_round",
            "tt_dot_plan", "tt_dot", "tt_dot_noalloc", "tt_norm", "tt_sketch_tt",
            "tt_philox4x32_10", "tt_launch_count", "tt_kernel_timer_start",
-           "tt_kernel_timer_stop", "tt_device_error", "tt_status_string")
+           "tt_kernel_timer_stop", "tt_device_error", "tt_hadamard_recompress_batch_plan",
+           "tt_hadamard_recompress_batch", "tt_status_string")
 
 
 def load(path: Optional[str] = None):
@@ -93,6 +94,12 @@ def load(path: Optional[str] = None):
     lib.tt_launch_count.argtypes = []
     lib.tt_kernel_timer_start.argtypes = [ctypes.c_int32]
     lib.tt_device_error.argtypes = [P(ctypes.c_int32)]
+    lib.tt_hadamard_recompress_batch_plan.argtypes = [ctypes.c_int32, P(TTStruct), P(TTStruct),
+                                                      P(OptsStruct), ctypes.c_int32,
+                                                      P(ctypes.c_size_t)]
+    lib.tt_hadamard_recompress_batch.argtypes = [ctypes.c_int32, P(TTStruct), P(TTStruct),
+                                                 P(OptsStruct), P(TTStruct), ctypes.c_int32, vp,
+                                                 ctypes.c_size_t, vp]
     lib.tt_kernel_timer_stop.argtypes = [P(ctypes.c_double), P(ctypes.c_double), ctypes.c_int32,
                                          P(ctypes.c_int64)]
     for name in EXPORTS:
@@ -365,3 +372,70 @@ def tt_philox4x32_10(ctr: torch.Tensor, key0: int, key1: int, stream=None) -> to
         ctypes.c_void_p(out.data_ptr()), int(ctr.shape[0]), _stream_ptr(stream)))
     (stream or torch.cuda.current_stream()).synchronize()
     return out
+
+
+class BatchRecompressor:
+    """Many independent pairs (uneven orders, modes, ranks) recompressed by one
+    tt_hadamard_recompress_batch call over `lanes` library streams. Plans once
+    and owns every output buffer and the lane workspace."""
+
+    def __init__(self, pairs, lanes: int = 8):
+        """pairs: list of (Y cores, Z cores, options dict) with CUDA float64 cores."""
+        lib = load()
+        self.count = len(pairs)
+        self.lanes = int(lanes)
+        self.Yd = [TT(Y) for Y, _, _ in pairs]
+        self.Zd = [TT(Z) for _, Z, _ in pairs]
+        self.opts = [make_opts(**o) for _, _, o in pairs]
+        self.Xd, self.out_bufs = [], []
+        for (Y, _, _), yd, zd, op in zip(pairs, self.Yd, self.Zd, self.opts):
+            bound = (ctypes.c_int64 * (yd.d + 1))()
+            ws = ctypes.c_size_t()
+            _check("tt_hadamard_recompress_plan",
+                   lib.tt_hadamard_recompress_plan(yd.ref(), zd.ref(), ctypes.byref(op), bound,
+                                                   ctypes.byref(ws)))
+            n, b = yd.n, [int(v) for v in bound]
+            bufs = [torch.empty(b[k] * n[k] * b[k + 1], dtype=torch.float64, device=Y[0].device)
+                    for k in range(yd.d)]
+            xd = TT(n=n, r=b, pinned_ranks=True)
+            xd.set_core_ptrs([t.data_ptr() for t in bufs])
+            self.Xd.append(xd)
+            self.out_bufs.append(bufs)
+        self.Ya = (TTStruct * max(self.count, 1))(*[t.s for t in self.Yd])
+        self.Za = (TTStruct * max(self.count, 1))(*[t.s for t in self.Zd])
+        self.Xa = (TTStruct * max(self.count, 1))(*[t.s for t in self.Xd])
+        self.Oa = (OptsStruct * max(self.count, 1))(*self.opts)
+        ws = ctypes.c_size_t()
+        _check("tt_hadamard_recompress_batch_plan",
+               lib.tt_hadamard_recompress_batch_plan(self.count, self.Ya, self.Za, self.Oa,
+                                                     self.lanes, ctypes.byref(ws)))
+        self.workspace_bytes = int(ws.value)
+        dev = pairs[0][0][0].device if pairs else torch.device("cuda")
+        self.workspace = torch.empty(max(self.workspace_bytes, 1), dtype=torch.uint8, device=dev)
+        self.graph = None
+
+    def run(self, stream=None):
+        _check("tt_hadamard_recompress_batch",
+               load().tt_hadamard_recompress_batch(self.count, self.Ya, self.Za, self.Oa, self.Xa,
+                                                   self.lanes,
+                                                   ctypes.c_void_p(self.workspace.data_ptr()),
+                                                   self.workspace_bytes, _stream_ptr(stream)))
+
+    def capture(self):
+        """One batch call in a CUDA graph (the lanes fork from and join into the
+        capturing stream); replay with `replay()`."""
+        self.run()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.run()
+        self.graph = g
+        return g
+
+    def replay(self):
+        self.graph.replay()
+
+    def result(self, j: int) -> List[torch.Tensor]:
+        r, n = self.Xd[j].r, self.Xd[j].n
+        return [self.out_bufs[j][k][: r[k] * n[k] * r[k + 1]].view(r[k], n[k], r[k + 1])
+                for k in range(self.Xd[j].d)]

@@ -783,6 +783,121 @@ int tt_hadamard_recompress(const tt_t *Y, const tt_t *Z, const tt_opts *opts, tt
   return TT_OK;
 }
 
+// ------------------------------------------------------------- batches ---
+// Library-owned streams and events of the batched entry point, created once
+// per device (cached until the process exits).
+namespace {
+constexpr int kMaxLanes = 32;
+struct LaneSet {
+  bool ready = false;
+  cudaStream_t s[kMaxLanes] = {};
+  cudaEvent_t join[kMaxLanes] = {};
+  cudaEvent_t fork = nullptr;
+};
+std::mutex g_lanes_mu;
+LaneSet g_lanes[kNoAllocMaxDevices];
+
+cudaError_t lanes_for_device(LaneSet **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_lanes_mu);
+  LaneSet &L = g_lanes[dev];
+  if (!L.ready) {
+    e = cudaEventCreateWithFlags(&L.fork, cudaEventDisableTiming);
+    for (int i = 0; i < kMaxLanes && e == cudaSuccess; ++i) {
+      e = cudaStreamCreateWithFlags(&L.s[i], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L.join[i], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return e;
+    L.ready = true;
+  }
+  *out = &L;
+  return cudaSuccess;
+}
+
+// Per-lane workspace sizes (pair j runs on lane j % lanes) and the total.
+int batch_layout(int count, const tt_t *Y, const tt_t *Z, const tt_opts *opts, int lanes,
+                 std::vector<size_t> &lane_bytes, size_t &total) {
+  if (count < 0 || lanes < 1 || lanes > kMaxLanes) return TT_ERR_ARG;
+  if (count > 0 && (!Y || !Z || !opts)) return TT_ERR_ARG;
+  lane_bytes.assign(lanes, 0);
+  for (int j = 0; j < count; ++j) {
+    std::vector<int64_t> bound((size_t)std::max(Y[j].d, 0) + 1);
+    size_t b = 0;
+    const int st = tt_hadamard_recompress_plan(&Y[j], &Z[j], &opts[j], bound.data(), &b);
+    if (st != TT_OK) return st;
+    size_t &lb = lane_bytes[j % lanes];
+    lb = std::max(lb, (b + 255) & ~(size_t)255);
+  }
+  total = 0;
+  for (size_t b : lane_bytes) total += b;
+  total += 256;
+  return TT_OK;
+}
+}  // namespace
+
+int tt_hadamard_recompress_batch_plan(int32_t count, const tt_t *Y, const tt_t *Z,
+                                      const tt_opts *opts, int32_t lanes,
+                                      size_t *workspace_bytes) {
+  if (!workspace_bytes) return TT_ERR_ARG;
+  std::vector<size_t> lane_bytes;
+  size_t total = 0;
+  const int st = batch_layout(count, Y, Z, opts, lanes, lane_bytes, total);
+  if (st != TT_OK) return st;
+  *workspace_bytes = total;
+  return TT_OK;
+}
+
+int tt_hadamard_recompress_batch(int32_t count, const tt_t *Y, const tt_t *Z,
+                                 const tt_opts *opts, tt_t *X, int32_t lanes, void *workspace,
+                                 size_t workspace_bytes, void *stream) {
+  std::vector<size_t> lane_bytes;
+  size_t total = 0;
+  int st = batch_layout(count, Y, Z, opts, lanes, lane_bytes, total);
+  if (st != TT_OK) return st;
+  if (count == 0) return TT_OK;
+  if (!X) return TT_ERR_ARG;
+  if (!workspace || !aligned(workspace)) return TT_ERR_WORKSPACE;
+  if (workspace_bytes < total) return TT_ERR_WORKSPACE;
+  // validate every pair before anything is enqueued (shapes, outputs, aliasing)
+  for (int j = 0; j < count; ++j) {
+    HattArgs a;
+    st = prepare_hatt(&Y[j], &Z[j], &opts[j], true, a);
+    if (st != TT_OK) return st;
+    if (!X[j].cores || !X[j].r || !X[j].n || X[j].d != Y[j].d) return TT_ERR_ARG;
+  }
+  LaneSet *L = nullptr;
+  cudaError_t e = lanes_for_device(&L);
+  if (e != cudaSuccess) return from_cuda(e);
+  const cudaStream_t caller = (cudaStream_t)stream;
+  const int used = std::min<int>(lanes, count);
+  e = cudaEventRecord(L->fork, caller);
+  for (int l = 0; l < used && e == cudaSuccess; ++l) e = cudaStreamWaitEvent(L->s[l], L->fork, 0);
+  if (e != cudaSuccess) return from_cuda(e);
+  std::vector<char *> base(lanes);
+  char *p = (char *)workspace;
+  for (int l = 0; l < lanes; ++l) {
+    base[l] = p;
+    p += lane_bytes[l];
+  }
+  int first_error = TT_OK;
+  for (int j = 0; j < count && first_error == TT_OK; ++j) {
+    const int l = j % lanes;
+    first_error = tt_hadamard_recompress(&Y[j], &Z[j], &opts[j], &X[j], base[l], lane_bytes[l],
+                                         L->s[l]);
+  }
+  // join every lane that was forked, also after an error, so the caller's
+  // stream never runs ahead of work already enqueued on a lane
+  for (int l = 0; l < used; ++l) {
+    cudaError_t e2 = cudaEventRecord(L->join[l], L->s[l]);
+    if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(caller, L->join[l], 0);
+    if (e2 != cudaSuccess && first_error == TT_OK) first_error = from_cuda(e2);
+  }
+  return first_error;
+}
+
 int tt_round_plan(const tt_t *A, int64_t max_rank, double tol, int64_t *out_rank_bound,
                   size_t *workspace_bytes) {
   if (!out_rank_bound || !workspace_bytes) return TT_ERR_ARG;

@@ -204,3 +204,24 @@ def workload_smooth_d50(seed_y: int = 3, seed_z: int = 4):
     d, n, r = 50, 64, 40
     return (smooth_tt(d, n, r, seed_y), smooth_tt(d, n, r, seed_z),
             dict(max_rank=80, tol=1e-8, sketch_rank=90))
+
+
+def workload_batch_uneven(count: int = 256, seed: int = 7, d_range=(10, 40), n_choices=(16, 32, 64),
+                          r_range=(8, 48)):
+    """Many independent pairs of uneven order, mode size and rank: per pair
+    d uniform in d_range, one mode size from n_choices, every inner rank of
+    Y and of Z uniform in r_range, Gaussian cores; target rank
+    2 max(r_Y, r_Z) (capped at 118 so that the oversampled sketch stays within
+    the 128 of the small factorizations). Returns a list of (Y, Z, opts)."""
+    rng = np.random.default_rng(seed)
+    pairs = []
+    for j in range(count):
+        d = int(rng.integers(d_range[0], d_range[1] + 1))
+        n = int(rng.choice(n_choices))
+        ry = [1] + [int(v) for v in rng.integers(r_range[0], r_range[1] + 1, size=d - 1)] + [1]
+        rz = [1] + [int(v) for v in rng.integers(r_range[0], r_range[1] + 1, size=d - 1)] + [1]
+        Y = gaussian_tt([n] * d, ry, int(rng.integers(1 << 30)))
+        Z = gaussian_tt([n] * d, rz, int(rng.integers(1 << 30)))
+        target = min(2 * max(max(ry), max(rz)), 118)
+        pairs.append((Y, Z, dict(max_rank=target, oversample=10)))
+    return pairs

@@ -201,3 +201,35 @@ def test_binding_entry_points_accept_every_option():
                             "include", "hatt.h")).read()
     for name, v in (("TT_FP64", 0), ("TT_MIXED_FP32", 1), ("TT_MIXED_TF32", 2), ("TT_MIXED_BF16", 3)):
         assert re.search(rf"{name}\s*=\s*{v}\b", hdr)
+
+
+def test_batch_plan_sums_per_lane_maxima(lib):
+    """Host-only: the batch workspace is one region per lane, each the largest
+    single-pair workspace of the pairs on that lane (pair j on lane j % lanes)."""
+    pairs = []
+    for j, (n, r) in enumerate([(8, 3), (16, 5), (4, 2), (8, 6), (32, 4)]):
+        Y = B.TT(n=[n] * 4, r=[1, r, r, r, 1])
+        Z = B.TT(n=[n] * 4, r=[1, r + 1, r + 1, r + 1, 1])
+        pairs.append((Y, Z, B.make_opts(sketch_rank=2 * r)))
+    single = []
+    for Y, Z, o in pairs:
+        bound = (ctypes.c_int64 * 5)()
+        ws = ctypes.c_size_t()
+        assert lib.tt_hadamard_recompress_plan(Y.ref(), Z.ref(), ctypes.byref(o), bound, ctypes.byref(ws)) == 0
+        single.append((ws.value + 255) // 256 * 256)
+    Ya = (B.TTStruct * 5)(*[p[0].s for p in pairs])
+    Za = (B.TTStruct * 5)(*[p[1].s for p in pairs])
+    Oa = (B.OptsStruct * 5)(*[p[2] for p in pairs])
+    for lanes in (1, 2, 3, 5, 8):
+        ws = ctypes.c_size_t()
+        assert lib.tt_hadamard_recompress_batch_plan(5, Ya, Za, Oa, lanes, ctypes.byref(ws)) == 0
+        expect = sum(max([single[j] for j in range(5) if j % lanes == l] or [0]) for l in range(lanes))
+        assert ws.value == expect + 256
+    ws = ctypes.c_size_t()
+    assert lib.tt_hadamard_recompress_batch_plan(5, Ya, Za, Oa, 0, ctypes.byref(ws)) == 3
+    assert lib.tt_hadamard_recompress_batch_plan(5, Ya, Za, Oa, 33, ctypes.byref(ws)) == 3
+    assert lib.tt_hadamard_recompress_batch_plan(0, None, None, None, 4, ctypes.byref(ws)) == 0
+    assert ws.value == 256
+    bad = (B.OptsStruct * 5)(*[p[2] for p in pairs])
+    bad[3].precision = 9
+    assert lib.tt_hadamard_recompress_batch_plan(5, Ya, Za, bad, 2, ctypes.byref(ws)) == 3
