@@ -89,6 +89,30 @@ def sampled_entries(cores, idx):
     return M[:, 0]
 
 
+def run_power_iteration(workloads, dev, d=50, iters=100):
+    """Example 3: largest entry of the Qing and Alpine TTs (d = 50, n = 10,
+    ranks d) by 100 power iterations with HaTT-1 at sketch rank 5; wall time
+    of the whole iteration (one synchronizing library call sequence per step)
+    and the relative error of the last estimate against the exact maximum."""
+    import numpy as np
+    import torch
+    from paper_2410_04385_gb300 import power_iteration as pi
+    out = {"workload": f"Qing / Alpine TT, d={d}, n=10, ranks {d}, sketch rank 5, {iters} iterations"}
+    for name, gfun in (("qing", workloads.qing_grid), ("alpine", workloads.alpine_grid)):
+        g = gfun(d)
+        Y = [torch.from_numpy(c).to(dev) for c in workloads.separable_sum_tt(g)]
+        pi.largest_entry(Y, iters=2, rank=5)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lams, _ = pi.largest_entry(Y, iters=iters, rank=5)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        true = float(sum(np.max(v) for v in g))    # separable sum: sum of per-coordinate maxima
+        out[name] = {"s_per_run": wall, "iterations_per_s": iters / wall,
+                     "rel_error_of_max": abs(float(lams[-1].item()) - true) / true}
+    return out
+
+
 def run_batch_cfg4(binding, workloads, dev, lanes=16):
     """256 independent pairs (d in [10, 40], n in {16, 32, 64}, inner ranks in
     [8, 48], target 2 max(r_Y, r_Z), FP32 sketches, FP64 QR / projection /
@@ -168,6 +192,7 @@ def parse():
     p.add_argument("--impl", choices=["hatt", "reference"], default="hatt")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-pkp", action="store_true")
+    p.add_argument("--no-power", action="store_true", help="skip the power iteration run")
     p.add_argument("--no-batch", action="store_true",
                    help="skip the 256-pair batched run (about a minute)")
     p.add_argument("--no-mixed", action="store_true",
@@ -520,6 +545,10 @@ def main():
     # ---- many uneven pairs: batched over library streams vs one after another ----
     if not args.no_batch and rank == 0:
         line["batch_cfg4"] = run_batch_cfg4(binding, workloads, dev)
+
+    # ---- power iteration for the largest entry (Example 3) ----
+    if not args.no_power and rank == 0:
+        line["power_iteration"] = run_power_iteration(workloads, dev)
 
     # ---- CPU oracle baseline and the error gate ----
     if not args.no_cpu_baseline and rank == 0:

@@ -249,6 +249,12 @@ int64_t tt_launch_count(void);
 int tt_kernel_timer_start(int32_t capacity);
 int tt_kernel_timer_stop(double *ms, double *flops, int32_t capacity, int64_t *count);
 
+/* x[i] /= *divisor for i < count (x, divisor: device; stream ordered, so the
+ * divisor may be a norm that an earlier call on the stream computes, e.g. the
+ * normalization X / ||X|| of the power iteration of Section 5, Example 3).
+ * TT_ERR_ARG for a negative count or NULL pointers (count > 0). */
+int tt_scale(double *x, int64_t count, const double *divisor, void *stream);
+
 /* Device error word, a diagnostic with no counterpart in the paper: set when
  * a bounded wait inside a kernel runs out (the tensor-core products wait on
  * an mbarrier for their own MMAs); that kernel writes NaN to its outputs,

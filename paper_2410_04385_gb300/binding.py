@@ -58,7 +58,7 @@ EXPORTS = ("tt_hadamard_recompress_plan", "tt_hadamard_recompress", "tt_round_pl
            "tt_dot_plan", "tt_dot", "tt_dot_noalloc", "tt_norm", "tt_sketch_tt",
            "tt_philox4x32_10", "tt_launch_count", "tt_kernel_timer_start",
            "tt_kernel_timer_stop", "tt_device_error", "tt_hadamard_recompress_batch_plan",
-           "tt_hadamard_recompress_batch", "tt_status_string")
+           "tt_hadamard_recompress_batch", "tt_scale", "tt_status_string")
 
 
 def load(path: Optional[str] = None):
@@ -94,6 +94,7 @@ def load(path: Optional[str] = None):
     lib.tt_launch_count.argtypes = []
     lib.tt_kernel_timer_start.argtypes = [ctypes.c_int32]
     lib.tt_device_error.argtypes = [P(ctypes.c_int32)]
+    lib.tt_scale.argtypes = [vp, ctypes.c_int64, vp, vp]
     lib.tt_hadamard_recompress_batch_plan.argtypes = [ctypes.c_int32, P(TTStruct), P(TTStruct),
                                                       P(OptsStruct), ctypes.c_int32,
                                                       P(ctypes.c_size_t)]
@@ -112,6 +113,14 @@ def load(path: Optional[str] = None):
 def launch_count() -> int:
     """Kernels enqueued by libhatt in this process so far."""
     return int(load().tt_launch_count())
+
+
+def tt_scale(x: torch.Tensor, divisor: torch.Tensor, stream=None) -> None:
+    """x /= divisor[0] in place on the device (both CUDA float64)."""
+    if x.dtype != torch.float64 or divisor.dtype != torch.float64 or not x.is_contiguous():
+        raise ValueError("x and divisor must be contiguous CUDA float64 tensors")
+    _check("tt_scale", load().tt_scale(ctypes.c_void_p(x.data_ptr()), x.numel(),
+                                       ctypes.c_void_p(divisor.data_ptr()), _stream_ptr(stream)))
 
 
 def device_error() -> int:

@@ -993,6 +993,13 @@ int tt_sketch_tt(int32_t d, const int64_t *n, const int64_t *ell, uint64_t seed,
 
 int64_t tt_launch_count(void) { return (int64_t)hatt::launch_count(); }
 
+int tt_scale(double *x, int64_t count, const double *divisor, void *stream) {
+  if (count < 0) return TT_ERR_ARG;
+  if (count == 0) return TT_OK;
+  if (!x || !divisor) return TT_ERR_ARG;
+  return from_cuda(hatt::div_by_scalar(x, count, divisor, (cudaStream_t)stream));
+}
+
 int tt_device_error(int32_t *value) {
   if (!value) return TT_ERR_ARG;
   int v = 0;

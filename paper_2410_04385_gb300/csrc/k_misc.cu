@@ -149,6 +149,14 @@ __global__ void eye_kernel(double *X, int m) {
     X[e] = (e / m == e % m) ? 1.0 : 0.0;
 }
 
+// x[i] /= *divisor (a device scalar, e.g. a norm just computed on the stream).
+__global__ void div_kernel(double *x, long long count, const double *divisor) {
+  const double q = *divisor;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] = x[i] / q;
+}
+
 __global__ void copy_kernel(const double *src, double *dst, long long count) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
        e += (long long)gridDim.x * blockDim.x)
@@ -234,6 +242,13 @@ cudaError_t set_identity(double *X, int m, cudaStream_t st) {
   const long long total = (long long)m * m;
   if (total <= 0) return cudaSuccess;
   eye_kernel<<<grid_for(total), kThreads, 0, st>>>(X, m);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t div_by_scalar(double *x, long long count, const double *divisor, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  div_kernel<<<grid_for(count), kThreads, 0, st>>>(x, count, divisor);
   note_launch();
   return cudaGetLastError();
 }

@@ -225,3 +225,41 @@ def workload_batch_uneven(count: int = 256, seed: int = 7, d_range=(10, 40), n_c
         target = min(2 * max(max(ry), max(rz)), 118)
         pairs.append((Y, Z, dict(max_rank=target, oversample=10)))
     return pairs
+
+
+def separable_sum_tt(g):
+    """TT of f(x_1..x_d) = sum_k g[k](x_k) (g: list of d vectors of length n)
+    in the rank-d form of a d-term canonical decomposition: bond ranks
+    {1, d, ..., d, 1}; term j is the product over k of g[k] if k == j and of
+    ones otherwise, carried on bond index j (diagonal inner cores)."""
+    d = len(g)
+    n = len(g[0])
+    cores = []
+    for k in range(d):
+        a = 1 if k == 0 else d
+        b = 1 if k == d - 1 else d
+        c = np.zeros((a, n, b))
+        for j in range(d):
+            vec = np.asarray(g[k], dtype=np.float64) if j == k else np.ones(n)
+            c[0 if k == 0 else j, :, 0 if k == d - 1 else j] = vec
+        cores.append(c)
+    return cores
+
+
+def qing_grid(d: int, n: int = 10):
+    """Per-coordinate terms of the Qing function (x_i - i)^2, i = 1..d, on a
+    uniform grid of n points over [-500, 500] (endpoints included)."""
+    x = np.linspace(-500.0, 500.0, n)
+    return [(x - (k + 1)) ** 2 for k in range(d)]
+
+
+def alpine_grid(d: int, n: int = 10):
+    """Per-coordinate terms |x sin x + 0.1 x| of the Alpine function on a
+    uniform grid of n points over [-2.5 pi, 2.5 pi]."""
+    x = np.linspace(-2.5 * np.pi, 2.5 * np.pi, n)
+    return [np.abs(x * np.sin(x) + 0.1 * x) for _ in range(d)]
+
+
+def ones_tt_list(d: int, n: int = 10):
+    """The all-ones TT (rank 1), the power iteration's start."""
+    return [np.ones((1, n, 1)) for _ in range(d)]
