@@ -89,6 +89,48 @@ def sampled_entries(cores, idx):
     return M[:, 0]
 
 
+def allen_cahn_initial(d, n, terms=4, seed=0):
+    """sum_{j<terms} prod_i sin(k_ij x_i), k_ij in {1, 2, 3} (seeded), x_i =
+    2 pi m / n, as a TT of ranks {1, terms, ..., terms, 1}."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    K = rng.integers(1, 4, size=(terms, d))
+    x = 2.0 * np.pi * np.arange(n) / n
+    cores = []
+    for i in range(d):
+        c = np.zeros((1 if i == 0 else terms, n, 1 if i == d - 1 else terms))
+        for j in range(terms):
+            c[0 if i == 0 else j, :, 0 if i == d - 1 else j] = np.sin(K[j, i] * x)
+        cores.append(c)
+    return cores
+
+
+def run_allen_cahn(dev, d=8, n=64, steps=100, eps=0.1, dt=1e-3):
+    """Example 4 on [0, 2 pi)^8, n = 64, eps = 0.1, dt = 1e-3: explicit Euler
+    with u^2, u^3 by HaTT-1 (rank cap 48, tol 1e-10) and tt_round (cap 24, tol
+    1e-8) each step; wall time per step and the discrete energy."""
+    import math
+    import torch
+    from paper_2410_04385_gb300 import allen_cahn as ac
+    h = 2.0 * math.pi / n
+    u = [torch.from_numpy(c).to(dev) for c in allen_cahn_initial(d, n)]
+    energies = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for w in range(steps):
+        u, u2 = ac.step(u, h, eps, dt, max_rank=24, tol=1e-8, hatt_tol=1e-10, seed=10 * w)
+        if w % 10 == 9:
+            energies.append(ac.energy(u, u2, h, eps))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    return {"workload": f"u_t = eps^2 Lap u + u - u^3 on [0,2pi)^{d}, n={n}, eps={eps}, dt={dt}, "
+                        f"explicit Euler, u^3 by two HaTT-1 calls, tt_round tol 1e-8",
+            "steps": steps, "ms_per_step": 1000.0 * wall / steps,
+            "max_rank": int(max(c.shape[2] for c in u)),
+            "energy_every_10_steps": energies,
+            "energy_non_increasing": bool(all(b <= a * (1 + 1e-9) for a, b in zip(energies, energies[1:])))}
+
+
 def run_power_iteration(workloads, dev, d=50, iters=100):
     """Example 3: largest entry of the Qing and Alpine TTs (d = 50, n = 10,
     ranks d) by 100 power iterations with HaTT-1 at sketch rank 5; wall time
@@ -193,6 +235,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-pkp", action="store_true")
     p.add_argument("--no-power", action="store_true", help="skip the power iteration run")
+    p.add_argument("--no-allen-cahn", action="store_true", help="skip the Allen-Cahn run")
     p.add_argument("--no-batch", action="store_true",
                    help="skip the 256-pair batched run (about a minute)")
     p.add_argument("--no-mixed", action="store_true",
@@ -549,6 +592,10 @@ def main():
     # ---- power iteration for the largest entry (Example 3) ----
     if not args.no_power and rank == 0:
         line["power_iteration"] = run_power_iteration(workloads, dev)
+
+    # ---- Allen-Cahn time stepping (Example 4) ----
+    if not args.no_allen_cahn and rank == 0:
+        line["allen_cahn"] = run_allen_cahn(dev)
 
     # ---- CPU oracle baseline and the error gate ----
     if not args.no_cpu_baseline and rank == 0:

@@ -249,6 +249,22 @@ int64_t tt_launch_count(void);
 int tt_kernel_timer_start(int32_t capacity);
 int tt_kernel_timer_stop(double *ms, double *flops, int32_t capacity, int64_t *count);
 
+/* Periodic central-difference Laplacian of a TT (Section 5, Example 4):
+ * L = sum_k I x .. x D_k x .. x I applied to A, D the n_k x n_k second
+ * difference (u_{i+1} - 2 u_i + u_{i-1}) * inv_h2 with wrap-around. L has
+ * ranks {1, 2 r_1, ..., 2 r_{d-1}, 1} and cores [A_1 | D A_1],
+ * [[A_k, D A_k], [0, A_k]], [[D A_d], [A_d]] (for d = 1 the single core
+ * D A_1). L: caller-allocated cores of those shapes and L->r set to them
+ * (TT_ERR_SHAPE otherwise); stream ordered. */
+int tt_laplacian(const tt_t *A, double inv_h2, tt_t *L, void *stream);
+
+/* S = sum_j coef[j] T[j] (count >= 1 TTs of equal order and mode sizes,
+ * coef host) with block-diagonal cores: ranks r_k(S) = sum_j r_k(T_j) for
+ * the inner bonds, the coefficients multiply the first cores (for d = 1 the
+ * single core is the plain sum). S: caller-allocated, S->r set to those
+ * ranks (TT_ERR_SHAPE otherwise); stream ordered. */
+int tt_lincomb(int32_t count, const tt_t *T, const double *coef, tt_t *S, void *stream);
+
 /* x[i] /= *divisor for i < count (x, divisor: device; stream ordered, so the
  * divisor may be a norm that an earlier call on the stream computes, e.g. the
  * normalization X / ||X|| of the power iteration of Section 5, Example 3).

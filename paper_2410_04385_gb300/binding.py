@@ -58,7 +58,8 @@ EXPORTS = ("tt_hadamard_recompress_plan", "tt_hadamard_recompress", "tt_round_pl
            "tt_dot_plan", "tt_dot", "tt_dot_noalloc", "tt_norm", "tt_sketch_tt",
            "tt_philox4x32_10", "tt_launch_count", "tt_kernel_timer_start",
            "tt_kernel_timer_stop", "tt_device_error", "tt_hadamard_recompress_batch_plan",
-           "tt_hadamard_recompress_batch", "tt_scale", "tt_status_string")
+           "tt_hadamard_recompress_batch", "tt_scale", "tt_laplacian", "tt_lincomb",
+           "tt_status_string")
 
 
 def load(path: Optional[str] = None):
@@ -95,6 +96,8 @@ def load(path: Optional[str] = None):
     lib.tt_kernel_timer_start.argtypes = [ctypes.c_int32]
     lib.tt_device_error.argtypes = [P(ctypes.c_int32)]
     lib.tt_scale.argtypes = [vp, ctypes.c_int64, vp, vp]
+    lib.tt_laplacian.argtypes = [P(TTStruct), ctypes.c_double, P(TTStruct), vp]
+    lib.tt_lincomb.argtypes = [ctypes.c_int32, P(TTStruct), P(ctypes.c_double), P(TTStruct), vp]
     lib.tt_hadamard_recompress_batch_plan.argtypes = [ctypes.c_int32, P(TTStruct), P(TTStruct),
                                                       P(OptsStruct), ctypes.c_int32,
                                                       P(ctypes.c_size_t)]
@@ -121,6 +124,34 @@ def tt_scale(x: torch.Tensor, divisor: torch.Tensor, stream=None) -> None:
         raise ValueError("x and divisor must be contiguous CUDA float64 tensors")
     _check("tt_scale", load().tt_scale(ctypes.c_void_p(x.data_ptr()), x.numel(),
                                        ctypes.c_void_p(divisor.data_ptr()), _stream_ptr(stream)))
+
+
+def tt_laplacian(A: Sequence[torch.Tensor], inv_h2: float, stream=None) -> List[torch.Tensor]:
+    """Periodic central-difference Laplacian of the TT A (ranks doubled)."""
+    Ad = TT(A)
+    d, n, r = Ad.d, Ad.n, Ad.r
+    rl = [1] + [2 * v for v in r[1:-1]] + [1] if d > 1 else [1, 1]
+    out = [torch.empty((rl[k], n[k], rl[k + 1]), dtype=torch.float64, device=A[0].device)
+           for k in range(d)]
+    Ld = TT(out)
+    _check("tt_laplacian", load().tt_laplacian(Ad.ref(), float(inv_h2), Ld.ref(), _stream_ptr(stream)))
+    return out
+
+
+def tt_lincomb(terms: Sequence[Sequence[torch.Tensor]], coef: Sequence[float],
+               stream=None) -> List[torch.Tensor]:
+    """sum_j coef[j] terms[j] as one TT (block-diagonal cores)."""
+    Td = [TT(t) for t in terms]
+    d, n = Td[0].d, Td[0].n
+    rs = [sum(t.r[k] for t in Td) for k in range(d + 1)]
+    rs[0] = rs[d] = 1
+    out = [torch.empty((rs[k], n[k], rs[k + 1]), dtype=torch.float64, device=terms[0][0].device)
+           for k in range(d)]
+    Sd = TT(out)
+    Ta = (TTStruct * len(Td))(*[t.s for t in Td])
+    ca = (ctypes.c_double * len(coef))(*[float(c) for c in coef])
+    _check("tt_lincomb", load().tt_lincomb(len(Td), Ta, ca, Sd.ref(), _stream_ptr(stream)))
+    return out
 
 
 def device_error() -> int:

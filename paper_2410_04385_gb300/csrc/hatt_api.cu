@@ -993,6 +993,77 @@ int tt_sketch_tt(int32_t d, const int64_t *n, const int64_t *ell, uint64_t seed,
 
 int64_t tt_launch_count(void) { return (int64_t)hatt::launch_count(); }
 
+int tt_laplacian(const tt_t *A, double inv_h2, tt_t *L, void *stream) {
+  int st = check_tt(A, true);
+  if (st != TT_OK) return st;
+  if (!L || !L->n || !L->r || !L->cores || !std::isfinite(inv_h2)) return TT_ERR_ARG;
+  const int d = A->d;
+  if (L->d != d) return TT_ERR_SHAPE;
+  for (int k = 0; k < d; ++k) {
+    if (L->n[k] != A->n[k] || !L->cores[k]) return TT_ERR_SHAPE;
+    if (A->n[k] > kIntMax / 2 || 2 * A->r[k] > kIntMax) return TT_ERR_RANK;
+  }
+  for (int k = 0; k <= d; ++k) {
+    const int64_t want = (k == 0 || k == d) ? 1 : 2 * A->r[k];
+    if (L->r[k] != want) return TT_ERR_SHAPE;
+  }
+  cudaStream_t strm = (cudaStream_t)stream;
+  for (int k = 0; k < d; ++k) {
+    const int pos = d == 1 ? 0 : (k == 0 ? 1 : (k == d - 1 ? 3 : 2));
+    cudaError_t e = hatt::laplacian_core(A->cores[k], (int)A->r[k], (int)A->n[k], (int)A->r[k + 1],
+                                         pos, inv_h2, L->cores[k], strm);
+    if (e != cudaSuccess) return from_cuda(e);
+  }
+  return TT_OK;
+}
+
+int tt_lincomb(int32_t count, const tt_t *T, const double *coef, tt_t *S, void *stream) {
+  if (count < 1 || !T || !coef || !S || !S->n || !S->r || !S->cores) return TT_ERR_ARG;
+  for (int j = 0; j < count; ++j) {
+    const int st = check_tt(&T[j], true);
+    if (st != TT_OK) return st;
+    if (!std::isfinite(coef[j])) return TT_ERR_ARG;
+  }
+  const int d = T[0].d;
+  if (S->d != d) return TT_ERR_SHAPE;
+  for (int j = 0; j < count; ++j) {
+    if (T[j].d != d) return TT_ERR_SHAPE;
+    for (int k = 0; k < d; ++k)
+      if (T[j].n[k] != T[0].n[k]) return TT_ERR_SHAPE;
+  }
+  for (int k = 0; k < d; ++k)
+    if (S->n[k] != T[0].n[k] || !S->cores[k]) return TT_ERR_SHAPE;
+  for (int k = 0; k <= d; ++k) {
+    ll want = 0;
+    for (int j = 0; j < count; ++j) want += T[j].r[k];
+    if (k == 0 || k == d) want = 1;
+    if (S->r[k] != want) return TT_ERR_SHAPE;
+    if (want > kIntMax) return TT_ERR_RANK;
+  }
+  cudaStream_t strm = (cudaStream_t)stream;
+  for (int k = 0; k < d; ++k) {
+    const int n = (int)T[0].n[k];
+    const int A = (int)S->r[k], Bw = (int)S->r[k + 1];
+    cudaError_t e = cudaSuccess;
+    if (d > 1 && k > 0 && k < d - 1)
+      e = cudaMemsetAsync(S->cores[k], 0, (size_t)A * n * Bw * sizeof(double), strm);
+    int ra = 0, rb = 0;
+    for (int j = 0; j < count && e == cudaSuccess; ++j) {
+      const int a = (int)T[j].r[k], b = (int)T[j].r[k + 1];
+      const double c = (k == 0) ? coef[j] : 1.0;          // coefficients on the first cores
+      if (d == 1) {
+        e = hatt::put_block(T[j].cores[0], 1, n, 1, coef[j], S->cores[0], 1, 1, 0, 0, j > 0, strm);
+        continue;
+      }
+      e = hatt::put_block(T[j].cores[k], a, n, b, c, S->cores[k], A, Bw, ra, rb, false, strm);
+      if (k > 0) ra += a;
+      if (k < d - 1) rb += b;
+    }
+    if (e != cudaSuccess) return from_cuda(e);
+  }
+  return TT_OK;
+}
+
 int tt_scale(double *x, int64_t count, const double *divisor, void *stream) {
   if (count < 0) return TT_ERR_ARG;
   if (count == 0) return TT_OK;

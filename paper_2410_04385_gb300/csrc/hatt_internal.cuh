@@ -110,6 +110,11 @@ cudaError_t set_value(double *x, long long count, double v, cudaStream_t st);
 cudaError_t set_identity(double *X, int m, cudaStream_t st);
 cudaError_t copy_f64(const double *src, double *dst, long long count, cudaStream_t st);
 cudaError_t div_by_scalar(double *x, long long count, const double *divisor, cudaStream_t st);
+// TT operations of the Allen-Cahn application (k_ops.cu).
+cudaError_t laplacian_core(const double *u, int a, int n, int b, int pos, double inv_h2,
+                           double *out, cudaStream_t st);
+cudaError_t put_block(const double *src, int a, int n, int b, double coef, double *dst, int A,
+                      int B, int ra, int rb, bool accumulate, cudaStream_t st);
 // dst[(a*n + i)*rb + b] = src[(a*n + i)*lb + b] for a < ra, b < rb, with ra, rb
 // read from ranks_dev[k], ranks_dev[k+1] (device int64) and bounds la x n x lb.
 cudaError_t compact_core(const double *src, double *dst, int la, int n, int lb,

@@ -1,0 +1,89 @@
+// TT operations of the Allen-Cahn application (Section 5, Example 4):
+// the periodic second-difference Laplacian applied to a TT, and linear
+// combinations of TTs. Both only assemble block cores (elementwise work).
+#include <algorithm>
+#include "hatt_internal.cuh"
+
+namespace hatt {
+namespace {
+
+constexpr int kOpThreads = 256;
+
+int op_grid(long long count) {
+  return (int)std::max<long long>(1, std::min<long long>((count + kOpThreads - 1) / kOpThreads, 8 * 152));
+}
+
+// (D u)(alpha, i, beta) = (u(alpha, i+1, beta) - 2 u(alpha, i, beta) + u(alpha, i-1, beta)) / h^2,
+// indices modulo n (periodic).
+__device__ __forceinline__ double stencil(const double *u, int n, int b, int alpha, int i,
+                                          int beta, double inv_h2) {
+  const int ip = (i + 1 == n) ? 0 : i + 1, im = (i == 0) ? n - 1 : i - 1;
+  const long long row = (long long)alpha * n;
+  return (u[(row + ip) * b + beta] - 2.0 * u[(row + i) * b + beta] + u[(row + im) * b + beta]) * inv_h2;
+}
+
+// Core k of Lap u. pos: 0 = only core (D u), 1 = first [u | D u],
+// 2 = middle [[u, D u], [0, u]], 3 = last [[D u], [u]]. u is a x n x b.
+__global__ void laplacian_core_kernel(const double *u, int a, int n, int b, int pos,
+                                      double inv_h2, double *out) {
+  const int oa = (pos == 2 || pos == 3) ? 2 * a : a;
+  const int ob = (pos == 1 || pos == 2) ? 2 * b : b;
+  const long long total = (long long)oa * n * ob;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int beta = (int)(t % ob);
+    const long long r = t / ob;
+    const int i = (int)(r % n), alpha = (int)(r / n);
+    double v = 0.0;
+    if (pos == 0) {
+      v = stencil(u, n, b, alpha, i, beta, inv_h2);
+    } else if (pos == 1) {
+      v = beta < b ? u[((long long)alpha * n + i) * b + beta] : stencil(u, n, b, alpha, i, beta - b, inv_h2);
+    } else if (pos == 3) {
+      v = alpha < a ? stencil(u, n, b, alpha, i, beta, inv_h2) : u[((long long)(alpha - a) * n + i) * b + beta];
+    } else {
+      const bool top = alpha < a, left = beta < b;
+      if (top && left) v = u[((long long)alpha * n + i) * b + beta];
+      else if (top) v = stencil(u, n, b, alpha, i, beta - b, inv_h2);
+      else if (!left) v = u[((long long)(alpha - a) * n + i) * b + (beta - b)];
+    }
+    out[t] = v;
+  }
+}
+
+// Writes coef * src (a x n x b) into the block of dst (A x n x B) whose top
+// left corner is (ra, rb), or adds it there when accumulate is set.
+__global__ void put_block_kernel(const double *src, int a, int n, int b, double coef, double *dst,
+                                 int A, int B, int ra, int rb, int accumulate) {
+  const long long total = (long long)a * n * b;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int beta = (int)(t % b);
+    const long long r = t / b;
+    const int i = (int)(r % n), alpha = (int)(r / n);
+    double *d = dst + ((long long)(ra + alpha) * n + i) * B + rb + beta;
+    *d = accumulate ? fma(coef, src[t], *d) : coef * src[t];
+  }
+}
+
+}  // namespace
+
+cudaError_t laplacian_core(const double *u, int a, int n, int b, int pos, double inv_h2,
+                           double *out, cudaStream_t st) {
+  const int oa = (pos == 2 || pos == 3) ? 2 * a : a;
+  const int ob = (pos == 1 || pos == 2) ? 2 * b : b;
+  laplacian_core_kernel<<<op_grid((long long)oa * n * ob), kOpThreads, 0, st>>>(u, a, n, b, pos,
+                                                                               inv_h2, out);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t put_block(const double *src, int a, int n, int b, double coef, double *dst, int A,
+                      int B, int ra, int rb, bool accumulate, cudaStream_t st) {
+  put_block_kernel<<<op_grid((long long)a * n * b), kOpThreads, 0, st>>>(src, a, n, b, coef, dst,
+                                                                        A, B, ra, rb, accumulate);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace hatt
