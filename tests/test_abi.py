@@ -233,3 +233,14 @@ def test_batch_plan_sums_per_lane_maxima(lib):
     bad = (B.OptsStruct * 5)(*[p[2] for p in pairs])
     bad[3].precision = 9
     assert lib.tt_hadamard_recompress_batch_plan(5, Ya, Za, bad, 2, ctypes.byref(ws)) == 3
+
+
+def test_precision_range_is_checked_on_the_host(lib):
+    """tt_opts.precision: 0..4 plan, anything else is TT_ERR_ARG (status 3)."""
+    Y = B.TT(n=[4, 4, 4], r=[1, 2, 2, 1])
+    Z = B.TT(n=[4, 4, 4], r=[1, 2, 2, 1])
+    bound = (ctypes.c_int64 * 4)()
+    ws = ctypes.c_size_t()
+    for prec, expect in [(-1, 3), (0, 0), (1, 0), (2, 0), (3, 0), (4, 0), (5, 3)]:
+        o = B.make_opts(sketch_rank=4, precision=prec)
+        assert lib.tt_hadamard_recompress_plan(Y.ref(), Z.ref(), ctypes.byref(o), bound, ctypes.byref(ws)) == expect

@@ -113,4 +113,4 @@ def test_tensor_core_products_match_simt_rounding_model(B):
 def test_rejects_unknown_precision(B):
     Y, Z, _ = wl.workload_small_sin_times_random()
     with pytest.raises(B.HattError):
-        run_gpu(B, Y, Z, sketch_rank=12, precision=4)
+        run_gpu(B, Y, Z, sketch_rank=12, precision=5)     # past TT_FP64_TC = 4
