@@ -94,7 +94,18 @@ typedef enum {
  *   oversample   used when sketch_rank = 0 (>= 0)
  *   seed         Philox4x32-10 key of the Gaussian sketch TT
  *   precision    a tt_precision
- *   variant      1 = HaTT-1 (HPCRL-1 sketches, Eq. (3.6)) */
+ *   variant      1 = HaTT-1 (HPCRL-1 sketches, Eq. (3.6));
+ *                2 = HaTT-2 (HPCRL-2, Eq. (3.7)): before each contraction
+ *                W^{(k+1)} is replaced by its leading singular terms, the
+ *                R_k with sigma > ep * sigma_max (at least one), and the
+ *                contraction runs on R_k <= l_{k+1} columns. The singular
+ *                values come from the Gram matrix W^T W (FP64), so directions
+ *                below ~1e-8 sigma_max are not resolved and ep < 1e-8 keeps
+ *                them (the result is then HaTT-1's up to rounding). R_k is read
+ *                on the host: the call synchronizes `stream` once per core and
+ *                returns TT_ERR_ARG while the stream is being captured; the
+ *                batched entry point rejects it.
+ *   ep           HaTT-2 truncation threshold, 0 <= ep < 1 (ignored by variant 1) */
 typedef struct {
   int64_t max_rank;
   double tol;
@@ -103,6 +114,7 @@ typedef struct {
   uint64_t seed;
   int32_t precision;
   int32_t variant;
+  double ep;
 } tt_opts;
 
 /* Rank plan and workspace size of tt_hadamard_recompress.

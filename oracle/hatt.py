@@ -153,6 +153,45 @@ def hpcrl1_contract(Y, Z, R, normalize=True, fmt="fp64"):
     return W
 
 
+def hpcrl2(Y, Z, R, ep, normalize=True):
+    """HPCRL-2 (Eq. (3.7), Algorithm 3 with the truncated SVD): at each step
+    W^{(k)} = U S V^T is cut to the R singular values above ep * ||W^{(k)}||_2
+    and the recursion runs on the R rank-one terms,
+      W_L(:, (i, g)) = vec(Z_k(i) U_g Y_k(i)^T),  W_R(:, (i, g)) = R_k(i) V(:, g) s_g,
+      W^{(k-1)} = W_L W_R^T.
+    Reading: the returned sketches are the matrices the recursion computes
+    (l columns each); the truncation only shortens the next contraction.
+    Returns (W, Rk) with Rk[k] the rank kept when forming W^{(k-1)}."""
+    d = len(Y)
+    W = [None] * (d + 1)
+    W[d] = np.ones((1, 1))
+    kept = [0] * (d + 1)
+    for k in range(d - 1, 0, -1):
+        yk, zk, rk = Y[k], Z[k], R[k]
+        r0, n, r1 = yk.shape
+        s0, _, s1 = zk.shape
+        l0, _, l1 = rk.shape
+        Wn = W[k + 1]
+        u, sv, vt = np.linalg.svd(Wn, full_matrices=False)
+        Rn = max(1, int(np.sum(sv > ep * sv[0]))) if sv[0] > 0 else 1
+        kept[k + 1] = Rn
+        WL = np.empty((r0 * s0, n * Rn))
+        WR = np.empty((l0, n * Rn))
+        for i in range(n):
+            for g in range(Rn):
+                Ug = u[:, g].reshape(r1, s1).T                  # s1 x r1
+                P = zk[:, i, :] @ Ug @ yk[:, i, :].T            # s0 x r0
+                WL[:, i * Rn + g] = P.reshape(-1, order="F")    # index alpha * s0 + beta
+                WR[:, i * Rn + g] = rk[:, i, :] @ vt[g] * sv[g]
+        w = WL @ WR.T
+        if normalize:
+            nw = np.linalg.norm(w)
+            if nw > 0:
+                w = w / nw
+        W[k] = w
+    return W, kept
+
+
 # ----------------------------------------------------- left-to-right pass ---
 
 def core_update_paper(M, yk, zk):
@@ -228,7 +267,7 @@ def truncate_rl(X, max_rank=0, tol=0.0):
 
 def hadamard_recompress(Y, Z, max_rank=0, tol=0.0, sketch_rank=0, oversample=10,
                         seed=0, normalize=True, coding="contract", return_info=False,
-                        fmt="fp64"):
+                        fmt="fp64", variant=1, ep=0.0):
     """Recompress Y ⊙ Z with HaTT-1 (Algorithm 4) and the optional truncation.
 
     coding="contract" uses the three-stage contraction for HPCRL and the core
@@ -240,7 +279,9 @@ def hadamard_recompress(Y, Z, max_rank=0, tol=0.0, sketch_rank=0, oversample=10,
     lreq = requested_sketch_rank(r, s, max_rank, sketch_rank, oversample)
     ell = plan_ranks(n, r, s, lreq)
     R = philox.sketch_tt(seed, n, ell)
-    if coding == "paper":
+    if variant == 2:
+        W, _ = hpcrl2(Y, Z, R, ep, normalize)
+    elif coding == "paper":
         W = hpcrl1_wlwr(Y, Z, R, normalize)
     else:
         W = hpcrl1_contract(Y, Z, R, normalize, fmt)

@@ -43,6 +43,7 @@ class OptsStruct(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("precision", ctypes.c_int32),
         ("variant", ctypes.c_int32),
+        ("ep", ctypes.c_double),
     ]
 
 
@@ -240,9 +241,9 @@ class TT:
 
 
 def make_opts(max_rank=0, tol=0.0, sketch_rank=0, oversample=10, seed=0, precision=TT_FP64,
-              variant=1):
+              variant=1, ep=0.0):
     return OptsStruct(int(max_rank), float(tol), int(sketch_rank), int(oversample),
-                      int(seed) & 0xFFFFFFFFFFFFFFFF, int(precision), int(variant))
+                      int(seed) & 0xFFFFFFFFFFFFFFFF, int(precision), int(variant), float(ep))
 
 
 class HadamardRecompressor:
@@ -309,11 +310,14 @@ class HadamardRecompressor:
 
 
 def tt_hadamard_recompress(Y, Z, max_rank=0, tol=0.0, sketch_rank=0, oversample=10, seed=0,
-                           precision=TT_FP64, stream=None) -> List[torch.Tensor]:
-    """HaTT-1 recompression of Y ⊙ Z; returns the output cores (synchronizes).
-    precision: TT_FP64, or TT_MIXED_FP32 / TF32 / BF16 for the sketches."""
+                           precision=TT_FP64, variant=1, ep=0.0,
+                           stream=None) -> List[torch.Tensor]:
+    """HaTT recompression of Y ⊙ Z; returns the output cores (synchronizes).
+    precision: TT_FP64, TT_MIXED_FP32 / TF32 / BF16 or TT_FP64_TC;
+    variant 1 = HaTT-1, 2 = HaTT-2 with threshold ep."""
     h = HadamardRecompressor(Y, Z, max_rank=max_rank, tol=tol, sketch_rank=sketch_rank,
-                             oversample=oversample, seed=seed, precision=precision)
+                             oversample=oversample, seed=seed, precision=precision,
+                             variant=variant, ep=ep)
     h.run(stream)
     (stream or torch.cuda.current_stream()).synchronize()
     return [c.clone() for c in h.result()]

@@ -124,6 +124,13 @@ struct Runner {
     }
     if (err == cudaSuccess) check(hatt::qr_inplace(S, m, c, ld, scratch, flags, st));
   }
+  void eig(const double *G, int c, double *U) {
+    if (!exec) {
+      scratch_need = std::max(scratch_need, hatt::sym_eig_scratch_doubles(c));
+      return;
+    }
+    if (err == cudaSuccess) check(hatt::sym_eig(G, c, U, scratch, st));
+  }
   void trunc(double *Xk, int la, int n, int lb, double *Xkm1, int lm, int nm, int cap,
              const double *delta2, ll *ranks, int k, bool deep) {
     if (!exec) {
@@ -195,6 +202,8 @@ struct HattArgs {
   double tol;
   uint64_t seed;
   int prec = hatt::kPrecFP64;   // arithmetic of the HPCRL-1 products (A2/A3)
+  int variant = 1;              // 1 = HPCRL-1 (Eq. (3.6)), 2 = HPCRL-2 (Eq. (3.7))
+  double ep = 0.0;              // HPCRL-2: keep sigma > ep * ||W^{(k)}||_2
 };
 
 struct HattBufs {
@@ -203,6 +212,11 @@ struct HattBufs {
   int *flags;
   unsigned int *ticket;
   std::vector<ll> Roff, Woff, Xoff;
+  // HPCRL-2 only: Gram and eigenvectors of W^{(k+1)}, W V, its kept columns
+  // U_R S_R, V_R, R_k V_R, and the two partial contractions (sized for R = l)
+  double *G2 = nullptr, *V2 = nullptr, *Uf = nullptr, *UR = nullptr, *VR = nullptr,
+         *Rv = nullptr, *P2 = nullptr, *P3 = nullptr;
+  int *Rdev = nullptr;
 };
 
 HattBufs carve_hatt(Ws &ws, const HattArgs &a) {
@@ -245,7 +259,127 @@ HattBufs carve_hatt(Ws &ws, const HattArgs &a) {
   b.ranks = ws.take<ll>(d + 1);
   b.flags = ws.take<int>(8);
   b.ticket = ws.take<unsigned int>(1);
+  if (a.variant == 2) {
+    ll c2 = 1, xc = 1, rv = 1, p2 = 1, p3 = 1;
+    for (int k = 1; k < d; ++k) {
+      const ll x = (ll)r[k + 1] * s[k + 1], c = l[k + 1];
+      c2 = std::max(c2, c * c);
+      xc = std::max(xc, x * c);
+      rv = std::max(rv, l[k] * n[k] * c);
+      p2 = std::max(p2, (ll)n[k] * r[k + 1] * s[k] * c);
+      p3 = std::max(p3, (ll)r[k] * s[k] * n[k] * c);
+    }
+    b.G2 = ws.take<double>(c2);
+    b.V2 = ws.take<double>(c2);
+    b.Uf = ws.take<double>(xc);
+    b.UR = ws.take<double>(xc);
+    b.VR = ws.take<double>(c2);
+    b.Rv = ws.take<double>(rv);
+    b.P2 = ws.take<double>(p2);
+    b.P3 = ws.take<double>(p3);
+    b.Rdev = ws.take<int>(1);
+  }
   return b;
+}
+
+// HPCRL-2 step (Eq. (3.7)): W^{(k)} from the leading singular directions of
+// W^{(k+1)} = U S V^T (x = r_{k+1} s_{k+1} rows, c = l_{k+1} columns).
+//   G = W^T W, V = eig(G), U S = W V / ||W||  (right singular vectors from the
+//   Gram matrix; column norms of W V are the singular values),
+//   keep the R columns with sigma > ep * sigma_max, then with R terms
+//   Rv[l][i][g]       = sum_c R_k[l][i][c] V_R[c][g]
+//   P2[i][a'][b][g]   = sum_b' Z_k[b][i][b'] (U S)_R[a' s1 + b'][g]
+//   P3[a][b][i][g]    = sum_a' Y_k[a][i][a'] P2[i][a'][b][g]
+//   W^{(k)}[a s0 + b][l] = sum_{i,g} P3[a][b][i][g] Rv[l][i][g]
+// (the W_L W_R^T form: W_L = P3, W_R = Rv). R is read on the host, so this
+// variant synchronizes the stream once per core.
+void hpcrl2_step(Runner &run, const HattArgs &a, const HattBufs &b, int k, double *Wnext,
+                 double *Wout) {
+  const auto &n = a.n;
+  const auto &r = a.r;
+  const auto &s = a.s;
+  const auto &l = a.ell;
+  const int r0 = (int)r[k], r1 = (int)r[k + 1], s0 = (int)s[k], s1 = (int)s[k + 1];
+  const int l0 = (int)l[k], c = (int)l[k + 1], nk = (int)n[k];
+  const int x = r1 * s1;
+  const double *Rk = run.exec ? b.R + b.Roff[k] : nullptr;
+  {   // G = W^T W
+    Gemm g;
+    g.M = c; g.N = c; g.K = x;
+    g.A = Wnext; g.sAm = 1; g.sAk = c;
+    g.B = Wnext; g.sBk = c; g.sBn = 1;
+    g.C = b.G2; g.sCm = c; g.sCn = 1;
+    if (c > 1) run.gemm(g);
+  }
+  if (c > 1) {
+    run.eig(b.G2, c, b.V2);
+  } else if (run.live()) {
+    run.check(hatt::set_value(b.V2, 1, 1.0, run.st));
+  }
+  {   // Uf = W V / ||W||
+    Gemm g;
+    g.M = x; g.N = c; g.K = c;
+    g.A = Wnext; g.sAm = c; g.sAk = 1;
+    g.B = b.V2; g.sBk = c; g.sBn = 1;
+    g.C = b.Uf; g.sCm = c; g.sCn = 1;
+    g.alpha_dev = run.exec ? b.winv + (k + 1) : nullptr;
+    run.gemm(g);
+  }
+  auto contract = [&](int R) {
+    {   // Rv = R_k V_R
+      Gemm g;
+      g.M = l0 * nk; g.N = R; g.K = c;
+      g.A = Rk; g.sAm = c; g.sAk = 1;
+      g.B = b.VR; g.sBk = R; g.sBn = 1;
+      g.C = b.Rv; g.sCm = R; g.sCn = 1;
+      g.prec = a.prec;
+      run.gemm(g);
+    }
+    {   // P2, batched over (i, a')
+      Gemm g;
+      g.M = s0; g.N = R; g.K = s1;
+      g.batch = nk * r1; g.bdiv = r1;
+      g.A = a.Z ? a.Z[k] : nullptr; g.sA1 = s1; g.sA2 = 0; g.sAm = (ll)nk * s1; g.sAk = 1;
+      g.B = b.UR; g.sB1 = 0; g.sB2 = (ll)s1 * R; g.sBk = R; g.sBn = 1;
+      g.C = b.P2; g.sC1 = (ll)r1 * s0 * R; g.sC2 = (ll)s0 * R; g.sCm = R; g.sCn = 1;
+      g.prec = a.prec;
+      run.gemm(g);
+    }
+    {   // P3, batched over (i, b)
+      Gemm g;
+      g.M = r0; g.N = R; g.K = r1;
+      g.batch = nk * s0; g.bdiv = s0;
+      g.A = a.Y ? a.Y[k] : nullptr; g.sA1 = r1; g.sA2 = 0; g.sAm = (ll)nk * r1; g.sAk = 1;
+      g.B = b.P2; g.sB1 = (ll)r1 * s0 * R; g.sB2 = R; g.sBk = (ll)s0 * R; g.sBn = 1;
+      g.C = b.P3; g.sC1 = R; g.sC2 = (ll)nk * R; g.sCm = (ll)s0 * nk * R; g.sCn = 1;
+      g.prec = a.prec;
+      run.gemm(g);
+    }
+    {   // W^{(k)} = W_L W_R^T
+      Gemm g;
+      g.M = r0 * s0; g.N = l0; g.K = nk * R;
+      g.A = b.P3; g.sAm = (ll)nk * R; g.sAk = 1;
+      g.B = b.Rv; g.sBk = 1; g.sBn = (ll)nk * R;
+      g.C = Wout; g.sCm = l0; g.sCn = 1;
+      g.prec = a.prec;
+      run.gemm(g);
+    }
+  };
+  if (!run.exec) {   // planning: every R the selection can return
+    for (int R = 1; R <= c; ++R) contract(R);
+    return;
+  }
+  if (!run.live()) return;
+  run.check(hatt::select_directions(b.Uf, b.V2, x, c, a.ep, b.UR, b.VR, b.Rdev, run.st));
+  int R = 0;
+  run.check(cudaMemcpyAsync(&R, b.Rdev, sizeof(int), cudaMemcpyDeviceToHost, run.st));
+  run.check(cudaStreamSynchronize(run.st));
+  if (!run.live()) return;
+  if (R < 1 || R > c) {
+    run.check(cudaErrorUnknown);
+    return;
+  }
+  contract(R);
 }
 
 void run_hatt(Runner &run, const HattArgs &a, const HattBufs &b) {
@@ -288,6 +422,12 @@ void run_hatt(Runner &run, const HattArgs &a, const HattBufs &b) {
     const int r0 = (int)r[k], r1 = (int)r[k + 1], s0 = (int)s[k], s1 = (int)s[k + 1];
     const int l0 = (int)l[k], l1 = (int)l[k + 1], nk = (int)n[k];
     const double *Rk = b.R + b.Roff[k];
+    if (a.variant == 2) {
+      hpcrl2_step(run, a, b, k, Wk(k + 1), Wk(k));
+      if (run.live())
+        run.check(hatt::inv_norm(Wk(k), (ll)r0 * s0 * l0, b.winv + k, b.partials, b.ticket, run.st));
+      continue;
+    }
     {   // S1: T1[i][x][lam] = sum_g W[x][g] R_k[lam][i][g] / ||W||
       Gemm g;
       g.M = r1 * s1; g.N = l0; g.K = l1;
@@ -402,7 +542,10 @@ int prepare_hatt(const tt_t *Y, const tt_t *Z, const tt_opts *o, bool need_cores
       !std::isfinite(o->tol))
     return TT_ERR_ARG;
   if (o->precision < TT_FP64 || o->precision > TT_FP64_TC) return TT_ERR_ARG;
-  if (o->variant != 1) return TT_ERR_ARG;
+  if (o->variant != 1 && o->variant != 2) return TT_ERR_ARG;
+  if (o->variant == 2 && (!(o->ep >= 0.0) || !(o->ep < 1.0))) return TT_ERR_ARG;
+  a.variant = o->variant;
+  a.ep = o->ep;
   a.prec = o->precision == TT_FP64_TC ? hatt::kPrecFP64 : o->precision;
   const int d = Y->d;
   a.d = d;
@@ -763,6 +906,11 @@ int tt_hadamard_recompress(const tt_t *Y, const tt_t *Z, const tt_opts *opts, tt
   a.Z = Z->cores;
   a.Xout = X->cores;
   cudaStream_t strm = (cudaStream_t)stream;
+  if (a.variant == 2) {   // the kept ranks are read on the host: no stream capture
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(strm, &cs) != cudaSuccess) return from_cuda(cudaGetLastError());
+    if (cs != cudaStreamCaptureStatusNone) return TT_ERR_ARG;
+  }
   Fp64TcScope tc(opts->precision == TT_FP64_TC);
   HattBufs bufs_for_ranks;
   st = execute(workspace, workspace_bytes, strm,
@@ -824,6 +972,7 @@ int batch_layout(int count, const tt_t *Y, const tt_t *Z, const tt_opts *opts, i
   if (count > 0 && (!Y || !Z || !opts)) return TT_ERR_ARG;
   lane_bytes.assign(lanes, 0);
   for (int j = 0; j < count; ++j) {
+    if (opts[j].variant == 2) return TT_ERR_ARG;   // reads ranks on the host: one pair per call
     std::vector<int64_t> bound((size_t)std::max(Y[j].d, 0) + 1);
     size_t b = 0;
     const int st = tt_hadamard_recompress_plan(&Y[j], &Z[j], &opts[j], bound.data(), &b);

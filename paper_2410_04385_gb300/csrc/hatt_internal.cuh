@@ -143,6 +143,14 @@ size_t trunc_scratch_doubles(int la, int n, int lb, int lm, int nm);
 cudaError_t trunc_step(double *Xk, int la, int n, int lb, double *Xkm1, int lm, int nm,
                        int cap, const double *delta2_dev, long long *ranks_dev, int k, bool deep,
                        double *scratch, cudaStream_t st);
+// Eigenvectors (columns of U, c x c row-major) of the symmetric c x c matrix G.
+size_t sym_eig_scratch_doubles(int c);
+cudaError_t sym_eig(const double *G, int c, double *U, double *scratch, cudaStream_t st);
+// HPCRL-2: keeps the columns of Uf = W V (x x c) whose norms exceed ep times the
+// largest, packed (leading dimension R) into UR and, with the same columns of
+// V, into VR; writes R (>= 1) to device memory.
+cudaError_t select_directions(const double *Uf, const double *V, long long x, int c, double ep,
+                              double *UR, double *VR, int *R, cudaStream_t st);
 // delta2_dev = (tol * ||x|| )^2 / (d-1) for a device vector x.
 cudaError_t trunc_delta2(const double *x, long long count, double tol, int d, double *delta2_dev,
                          double *partials, unsigned int *ticket, cudaStream_t st);

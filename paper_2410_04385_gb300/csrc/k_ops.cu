@@ -1,6 +1,7 @@
 // TT operations of the Allen-Cahn application (Section 5, Example 4):
 // the periodic second-difference Laplacian applied to a TT, and linear
 // combinations of TTs. Both only assemble block cores (elementwise work).
+// Also the selection of the leading singular directions of HPCRL-2 (Eq. (3.7)).
 #include <algorithm>
 #include "hatt_internal.cuh"
 
@@ -66,6 +67,69 @@ __global__ void put_block_kernel(const double *src, int a, int n, int b, double 
   }
 }
 
+// HPCRL-2 selection. Uf = W V (x rows, c columns) holds W's right singular
+// directions scaled by their singular values: column j has squared norm
+// e_j = sigma_j^2. Keeps the columns with sigma_j > ep * sigma_max (at least
+// one), in descending order of e_j (ties by index), and writes them packed
+// with leading dimension R: UR (x x R) = U_R S_R and VR (c x R) = V_R.
+// One block: warp w sums the columns w, w + 32, ... in a fixed order, so the
+// decision is the same on every run.
+constexpr int kSelThreads = 1024;
+
+__global__ void __launch_bounds__(kSelThreads)
+select_directions_kernel(const double *Uf, const double *V, long long x, int c, double ep,
+                         double *UR, double *VR, int *Rout) {
+  __shared__ double e[kMaxSmall];
+  __shared__ int pos[kMaxSmall];
+  __shared__ int s_R;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int j = warp; j < c; j += kSelThreads / 32) {
+    double acc = 0.0;
+    for (long long r = lane; r < x; r += 32) {
+      const double v = Uf[r * c + j];
+      acc = fma(v, v, acc);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) e[j] = acc;
+  }
+  __syncthreads();
+  double emax = 0.0;
+  for (int j = 0; j < c; ++j) emax = fmax(emax, e[j]);
+  const double thr = ep * ep * emax;
+  int top = 0;   // index of the largest column (kept when nothing passes)
+  for (int j = 1; j < c; ++j)
+    if (e[j] > e[top]) top = j;
+  for (int j = tid; j < c; j += kSelThreads) {
+    const bool keep = e[j] > thr || j == top;
+    int p = -1;
+    if (keep) {
+      p = 0;
+      for (int i = 0; i < c; ++i) {
+        const bool ki = e[i] > thr || i == top;
+        if (ki && (e[i] > e[j] || (e[i] == e[j] && i < j))) ++p;
+      }
+    }
+    pos[j] = p;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int R = 0;
+    for (int j = 0; j < c; ++j) R += pos[j] >= 0;
+    s_R = R;
+    *Rout = R;
+  }
+  __syncthreads();
+  const int R = s_R;
+  for (long long t = tid; t < x * c; t += kSelThreads) {
+    const int j = (int)(t % c);
+    if (pos[j] >= 0) UR[(t / c) * R + pos[j]] = Uf[t];
+  }
+  for (int t = tid; t < c * c; t += kSelThreads) {
+    const int j = t % c;
+    if (pos[j] >= 0) VR[(t / c) * R + pos[j]] = V[t];
+  }
+}
+
 }  // namespace
 
 cudaError_t laplacian_core(const double *u, int a, int n, int b, int pos, double inv_h2,
@@ -82,6 +146,14 @@ cudaError_t put_block(const double *src, int a, int n, int b, double coef, doubl
                       int B, int ra, int rb, bool accumulate, cudaStream_t st) {
   put_block_kernel<<<op_grid((long long)a * n * b), kOpThreads, 0, st>>>(src, a, n, b, coef, dst,
                                                                         A, B, ra, rb, accumulate);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t select_directions(const double *Uf, const double *V, long long x, int c, double ep,
+                              double *UR, double *VR, int *R, cudaStream_t st) {
+  if (c < 1 || c > kMaxSmall) return cudaErrorInvalidValue;
+  select_directions_kernel<<<1, kSelThreads, 0, st>>>(Uf, V, x, c, ep, UR, VR, R);
   note_launch();
   return cudaGetLastError();
 }

@@ -883,6 +883,26 @@ cudaError_t trunc_step(double *Xk, int la, int n, int lb, double *Xkm1, int lm, 
   return cudaSuccess;
 }
 
+// Eigenvectors of a symmetric c x c matrix G (columns of U), the same FP32
+// start and FP64 refinement as the truncation sweep uses.
+size_t sym_eig_scratch_doubles(int c) {
+  size_t gs = 0;
+  gs = std::max(gs, gemm_scratch_doubles(g_tn(nullptr, nullptr, c, c, c, nullptr, c)));
+  gs = std::max(gs, gemm_scratch_doubles(g_nn(nullptr, nullptr, c, c, c, nullptr)));
+  return carve_doubles(c, 1, 1) + gs;
+}
+
+cudaError_t sym_eig(const double *G, int c, double *U, double *scratch, cudaStream_t st) {
+  if (c < 1 || c > kMaxSmall) return cudaErrorInvalidValue;
+  Layout L = carve(scratch, c, 1, 1);
+  int *state = L.flags + 8;
+  cudaError_t e = cudaMemsetAsync(state, 0, kEigSteps * sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  e = eigvecs(G, c, L.U0, L.U1, 0.0, state, L, st);
+  if (e != cudaSuccess) return e;
+  return copy_f64(L.U0, U, (long long)c * c, st);
+}
+
 cudaError_t trunc_delta2(const double *x, long long count, double tol, int d, double *delta2_dev,
                          double *partials, unsigned int *ticket, cudaStream_t st) {
   const int blocks = (int)std::max<long long>(1, std::min<long long>((count + kThreads - 1) / kThreads, 2 * 152));

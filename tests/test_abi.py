@@ -103,6 +103,7 @@ def test_plan_workspace_grows_with_size(lib):
 @pytest.mark.parametrize("case,expect", [
     ("order_mismatch", 1), ("mode_mismatch", 1), ("boundary_rank", 1), ("zero_mode", 1),
     ("negative_opt", 3), ("bad_precision", 3), ("bad_variant", 3), ("rank_too_big", 2),
+    ("negative_ep", 3), ("ep_one", 3), ("ep_nan", 3),
 ])
 def test_plan_rejects_bad_arguments(lib, case, expect):
     n = [4, 4, 4]
@@ -128,6 +129,12 @@ def test_plan_rejects_bad_arguments(lib, case, expect):
             opts = dict(precision=7)
         elif case == "bad_variant":
             opts = dict(variant=5)
+        elif case == "negative_ep":
+            opts = dict(variant=2, ep=-1e-3)
+        elif case == "ep_one":
+            opts = dict(variant=2, ep=1.0)
+        elif case == "ep_nan":
+            opts = dict(variant=2, ep=float("nan"))
     o = B.make_opts(**opts)
     bound = (ctypes.c_int64 * 8)()
     ws = ctypes.c_size_t()
@@ -193,7 +200,7 @@ def test_kernel_timer_argument_checks(lib):
 def test_binding_entry_points_accept_every_option():
     """The Python wrappers pass every tt_opts field through (marshalling only)."""
     import inspect
-    fields = {name for name, _ in B.OptsStruct._fields_} - {"variant"}
+    fields = {name for name, _ in B.OptsStruct._fields_}
     assert fields <= set(inspect.signature(B.make_opts).parameters)
     assert fields <= set(inspect.signature(B.tt_hadamard_recompress).parameters)
     assert (B.TT_FP64, B.TT_MIXED_FP32, B.TT_MIXED_TF32, B.TT_MIXED_BF16) == (0, 1, 2, 3)
@@ -244,3 +251,20 @@ def test_precision_range_is_checked_on_the_host(lib):
     for prec, expect in [(-1, 3), (0, 0), (1, 0), (2, 0), (3, 0), (4, 0), (5, 3)]:
         o = B.make_opts(sketch_rank=4, precision=prec)
         assert lib.tt_hadamard_recompress_plan(Y.ref(), Z.ref(), ctypes.byref(o), bound, ctypes.byref(ws)) == expect
+
+
+def test_hatt2_plan_and_batch_rejection(lib):
+    """HaTT-2 plans the same output bound as HaTT-1 and a workspace that also
+    holds its own buffers; the batched entry point rejects it (it reads the
+    kept ranks on the host)."""
+    n = [6] * 5
+    Yr, Zr = [1, 4, 5, 5, 3, 1], [1, 3, 4, 2, 3, 1]
+    st1, b1, w1 = _plan(Yr, Zr, n, sketch_rank=9)
+    st2, b2, w2 = _plan(Yr, Zr, n, sketch_rank=9, variant=2, ep=1e-3)
+    assert st1 == st2 == 0 and b1 == b2 and w2 > w1
+    Yd, Zd = B.TT(n=n, r=Yr), B.TT(n=n, r=Zr)
+    Ys = (B.TTStruct * 1)(Yd.s)
+    Zs = (B.TTStruct * 1)(Zd.s)
+    o = (B.OptsStruct * 1)(B.make_opts(sketch_rank=9, variant=2, ep=1e-3))
+    bound = ctypes.c_size_t()
+    assert B.load().tt_hadamard_recompress_batch_plan(1, Ys, Zs, o, 1, ctypes.byref(bound)) == 3

@@ -1,0 +1,126 @@
+"""GPU parity of HaTT-2 (HPCRL-2, Eq. (3.7)) through the C ABI against the
+FP64 oracle, which takes a full SVD of every W^{(k)}.
+
+The GPU path reads the singular values off the Gram matrix W^T W, so a cut
+decision can only differ from the oracle's when a ratio sigma_j / sigma_1
+lies within rounding of ep: every case checks, with the oracle's singular
+values, that each ratio is at least 1e-3 away from ep (relatively), so both
+sides keep the same terms. Tensors are compared (gauges are not unique),
+relative Frobenius difference <= 1e-10: the kept directions agree to
+~1e-15 / gap, and the result is that of the same rank-R sketches.
+"""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import hatt as ohatt
+from oracle import philox as ophilox
+from oracle import tt as ott
+from paper_2410_04385_gb300 import workloads as wl
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+REL_TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2410_04385_gb300 import binding, build
+    if not os.path.exists(binding.LIB_PATH):
+        build.build()
+    binding.load()
+    return binding
+
+
+def to_gpu(cores):
+    return [torch.from_numpy(np.ascontiguousarray(c)).cuda() for c in cores]
+
+
+def run_gpu(B, Y, Z, **opts):
+    return [c.cpu().numpy() for c in B.tt_hadamard_recompress(to_gpu(Y), to_gpu(Z), **opts)]
+
+
+def rel_diff(X, A):
+    return ott.tt_diff_norm(X, A) / max(ott.tt_norm(A), 1e-300)
+
+
+def cut_margin(Y, Z, sketch_rank, seed, ep):
+    """Smallest |sigma_j / sigma_1 / ep - 1| over the matrices HPCRL-2 cuts."""
+    n = [c.shape[1] for c in Y]
+    ell = ohatt.plan_ranks(n, ott.ranks(Y), ott.ranks(Z), sketch_rank)
+    W, kept = ohatt.hpcrl2(Y, Z, ophilox.sketch_tt(seed, n, ell), ep)
+    m = np.inf
+    for k in range(2, len(Y)):
+        sv = np.linalg.svd(W[k], compute_uv=False)
+        m = min(m, float(np.min(np.abs(sv / sv[0] / ep - 1.0))))
+    return m, kept
+
+
+def small_random():
+    n = [6, 5, 7, 4, 6, 5]
+    return (wl.gaussian_tt(n, [1, 4, 5, 6, 5, 3, 1], 11),
+            wl.gaussian_tt(n, [1, 3, 4, 3, 4, 2, 1], 12))
+
+
+def test_hatt2_ep_zero_equals_hatt1(B):
+    """P6 on the GPU: ep = 0 keeps every term."""
+    Y, Z = small_random()
+    X1 = run_gpu(B, Y, Z, sketch_rank=12, seed=3)
+    X2 = run_gpu(B, Y, Z, sketch_rank=12, seed=3, variant=2, ep=0.0)
+    A = ohatt.hadamard_recompress(Y, Z, sketch_rank=12, seed=3)
+    assert rel_diff(X2, X1) <= 1e-12
+    assert rel_diff(X2, A) <= 1e-12
+
+
+@pytest.mark.parametrize("which", ["random", "sin"])
+@pytest.mark.parametrize("ep", [3e-2, 0.3, 0.95])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_hatt2_matches_oracle(B, which, ep, seed):
+    if which == "random":
+        Y, Z = small_random()
+    else:
+        Y, Z, _ = wl.workload_small_sin_times_random()
+    margin, kept = cut_margin(Y, Z, 12, seed, ep)
+    assert margin > 1e-3
+    X = run_gpu(B, Y, Z, sketch_rank=12, seed=seed, variant=2, ep=ep)
+    A = ohatt.hadamard_recompress(Y, Z, sketch_rank=12, seed=seed, variant=2, ep=ep)
+    assert rel_diff(X, A) <= REL_TOL
+
+
+def test_hatt2_several_tiles_with_truncation(B):
+    """Ranks and modes that span several GEMM tiles, a ragged sketch rank,
+    and the final tolerance truncation on top of the truncated sketches."""
+    n = [16, 12, 20, 16, 12, 16, 20]
+    Y = wl.gaussian_tt(n, [1, 14, 22, 30, 25, 18, 9, 1], 21)
+    Z = wl.gaussian_tt(n, [1, 5, 7, 6, 8, 6, 3, 1], 22)
+    ep = 0.5
+    margin, kept = cut_margin(Y, Z, 45, 5, ep)
+    assert margin > 1e-3 and max(kept) < 45
+    X = run_gpu(B, Y, Z, sketch_rank=45, seed=5, variant=2, ep=ep, max_rank=30, tol=1e-8)
+    A = ohatt.hadamard_recompress(Y, Z, sketch_rank=45, seed=5, variant=2, ep=ep, max_rank=30,
+                                  tol=1e-8)
+    assert ott.ranks(X) == ott.ranks(A)
+    assert rel_diff(X, A) <= REL_TOL
+
+
+def test_hatt2_refuses_stream_capture(B):
+    """The kept ranks are read on the host, so a capturing stream is refused
+    before anything is enqueued (status TT_ERR_ARG)."""
+    Y, Z = small_random()
+    h = B.HadamardRecompressor(to_gpu(Y), to_gpu(Z), sketch_rank=12, variant=2, ep=0.3)
+    h.run()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    status = None
+    with torch.cuda.graph(g):
+        try:
+            h.run()
+        except B.HattError as e:
+            status = e.status
+    assert status == 3
+    h.run()          # still usable afterwards
+    torch.cuda.synchronize()

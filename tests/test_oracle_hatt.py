@@ -284,3 +284,42 @@ def test_package_cost_model_agrees_with_oracle_flop_model():
         a = costmodel.hatt1_flops(n, r, s, ell)
         b = flops.hatt1_flops(n, r, s, ell)
         assert np.allclose(a, b, rtol=1e-12)
+
+
+def test_hatt2_with_ep_zero_equals_hatt1():
+    """P6: with ep = 0 every nonzero singular value is kept, so HPCRL-2 forms
+    the same sketches as HPCRL-1 and HaTT-2 equals HaTT-1 (same sketch)."""
+    n = [5, 4, 6, 3, 5]
+    Y = wl.gaussian_tt(n, [1, 3, 4, 4, 2, 1], 71)
+    Z = wl.gaussian_tt(n, [1, 2, 3, 2, 3, 1], 72)
+    W1 = hatt.hpcrl1_contract(Y, Z, philox.sketch_tt(4, n, hatt.plan_ranks(n, tt.ranks(Y), tt.ranks(Z), 7)))
+    W2, kept = hatt.hpcrl2(Y, Z, philox.sketch_tt(4, n, hatt.plan_ranks(n, tt.ranks(Y), tt.ranks(Z), 7)), 0.0)
+    for a, b in zip(W1[1:-1], W2[1:-1]):
+        assert np.allclose(a, b, atol=1e-12 * np.abs(a).max())
+    X1 = hatt.hadamard_recompress(Y, Z, sketch_rank=7, seed=4)
+    X2 = hatt.hadamard_recompress(Y, Z, sketch_rank=7, seed=4, variant=2, ep=0.0)
+    assert tt.tt_diff_norm(X1, X2) <= 1e-12 * tt.tt_norm(X1)
+
+
+def test_hatt2_truncation_keeps_range_until_ep_is_large():
+    """Y = sin(sum x) (rank 2) times a random rank-5 TT has TT ranks of 10 at
+    most. Truncating W^{(k)} only shortens the next contraction: while the
+    n*R rank-one terms still span the range, HaTT-2 stays exact, and the kept
+    ranks R fall as ep grows. At ep = 0.95 only the dominant direction
+    survives and the result is far off."""
+    Y, Z, _ = wl.workload_small_sin_times_random()
+    A = tt.tt_full(Y) * tt.tt_full(Z)
+    n = [c.shape[1] for c in Y]
+    ell = hatt.plan_ranks(n, tt.ranks(Y), tt.ranks(Z), 12)
+    kept_prev = None
+    for ep in (1e-12, 1e-2, 3e-1, 0.95):
+        X = hatt.hadamard_recompress(Y, Z, sketch_rank=12, seed=0, variant=2, ep=ep)
+        err = np.linalg.norm(tt.tt_full(X) - A) / np.linalg.norm(A)
+        _, kept = hatt.hpcrl2(Y, Z, philox.sketch_tt(0, n, ell), ep)
+        if kept_prev is not None:
+            assert all(a <= b for a, b in zip(kept, kept_prev))
+        kept_prev = kept
+        if ep < 0.5:
+            assert err <= 1e-13
+        else:
+            assert err > 1e-2 and max(kept) == 1
