@@ -766,6 +766,12 @@ struct Fp64TcScope {
   ~Fp64TcScope() { hatt::set_fp64_tensor_cores(false); }
 };
 
+// Keeps the truncation sweep from synchronizing while a batch issues its lanes.
+struct NoHostSyncScope {
+  NoHostSyncScope() { hatt::set_host_sync(false); }
+  ~NoHostSyncScope() { hatt::set_host_sync(true); }
+};
+
 // Makes a tile-counter array current for the calling thread during one call.
 struct TileCounterScope {
   explicit TileCounterScope(int *p) { hatt::set_tile_counters(p); }
@@ -1032,6 +1038,7 @@ int tt_hadamard_recompress_batch(int32_t count, const tt_t *Y, const tt_t *Z,
     p += lane_bytes[l];
   }
   int first_error = TT_OK;
+  NoHostSyncScope no_sync;
   for (int j = 0; j < count && first_error == TT_OK; ++j) {
     const int l = j % lanes;
     first_error = tt_hadamard_recompress(&Y[j], &Z[j], &opts[j], &X[j], base[l], lane_bytes[l],

@@ -143,6 +143,10 @@ size_t trunc_scratch_doubles(int la, int n, int lb, int lm, int nm);
 cudaError_t trunc_step(double *Xk, int la, int n, int lb, double *Xkm1, int lm, int nm,
                        int cap, const double *delta2_dev, long long *ranks_dev, int k, bool deep,
                        double *scratch, cudaStream_t st);
+// Whether the truncation sweep may synchronize the stream (outside capture) to
+// stop its cluster levels early; the batched entry point switches it off for
+// the calling thread while it issues its lanes.
+void set_host_sync(bool allowed);
 // Eigenvectors (columns of U, c x c row-major) of the symmetric c x c matrix G.
 size_t sym_eig_scratch_doubles(int c);
 cudaError_t sym_eig(const double *G, int c, double *U, double *scratch, cudaStream_t st);

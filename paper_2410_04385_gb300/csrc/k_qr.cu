@@ -16,6 +16,14 @@
 // stays zero (its Gram row and column vanish), which leaves a partial
 // isometry whose zero columns carry nothing into the next core.
 //
+// An S of exactly lower rank than c (a raw TT representation, a sketch of an
+// exact low-rank product) has null directions at the rounding level, ~u ||S||.
+// Each shifted pass multiplies them by about 1/sqrt(s / ||S||^2), i.e. by 1e4
+// to 1e6 for the sizes here, so they need four shifted passes to reach unit
+// size and then one or two plain ones: six passes in all. Stopping earlier
+// leaves Q far from orthonormal, and the projection Q Q^T C of the callers
+// then loses about 1e-9 of C.
+//
 // All passes are launched unconditionally (fixed launch sequence, capturable
 // in a CUDA graph); a device flag set by the convergence test turns the
 // remaining launches into no-ops.
@@ -25,7 +33,7 @@
 namespace hatt {
 namespace {
 
-constexpr int kPasses = 4;
+constexpr int kPasses = 6;
 constexpr int kCholThreads = 256;
 constexpr int kTrsmThreads = 256;
 

@@ -497,35 +497,51 @@ __global__ void select_result_kernel(const int *state, int nsteps, const double 
 }
 
 // ---------------------------------------------------------------------------
-// Second level (tolerance mode only). The Gram matrix G = B B^T holds every
-// entry to an absolute u ||G||, so eigenvalues below ~64 c u ||G||_F stay
-// mixed after the refinement (their energies can be off by ~u^2 ||G||^2 /
-// lambda, far above delta^2 for small tolerances). G1 = B1 B1^T, formed from
-// the rotated rows B1 = U^T B, holds its entries to u times the row norms, so
-// the low-energy rows can be diagonalized again on their own scale:
-//   cluster C = {i : G1_ii < 1024 c u ||G1||_F},  s = sum_{i in C} G1_ii,
-//   H = G1[C, C] / s on the cluster, H_ii = 1.25 + i/(2c) (distinct, above
-//   the cluster's spectrum, no coupling) elsewhere,
-// and its eigenvectors V (same FP32 start + FP64 refinement, floor taken from
-// the cluster's norm, 1) rotate U <- U V. The step is skipped (V = I) when C
-// has fewer than two rows or when the whole cluster fits under delta^2, in
-// which case the cut cannot fall inside it.
-//   flags[0] = skip the second level
+// Further levels (tolerance mode only). The FP32 start resolves eigenvalues
+// only down to ~1e-7 of the matrix it is given, and the refinement cannot
+// split what the start leaves mixed: its cluster test compares gaps with the
+// size of the unresolved block itself (~1e-7 ||G||). Eigenvalues below that
+// stay mixed after the first level. G1 = B1 B1^T, formed from the rotated rows
+// B1 = U^T B, holds its entries to u times the row norms, so the low-energy
+// rows can be diagonalized again on their own scale, and again below that:
+//   level 0:  cluster C = {i : G1_ii < kLevelCut ||G1||_F}
+//   level j:  cluster C = {i : G1_ii < kLevelCut s_{j-1}}
+//   s_j = sum_{i in C} G1_ii,  H = G1[C, C] / s_j on the cluster,
+//   H_ii = 1.25 + i/(2c) (distinct, above the cluster's spectrum, no
+//   coupling) elsewhere,
+// and the eigenvectors V of H (same FP32 start + FP64 refinement, floor taken
+// from the cluster's norm, 1) rotate U <- U V. Each level resolves about
+// seven decades of energy below its scale; its cut, 1e-6 of the scale, stays
+// above what the previous level resolved. A level is skipped (V = I, and so
+// are all later levels) when its cluster has fewer than two rows or fits
+// under delta^2 as a whole, in which case the cut cannot fall inside it.
+//   flags[0] = this level (and every later one) skipped
 //   flags[1] = skip the cross step (delta^2 > 1e-16 ||G1||_F: the level-one
-//              leakage, ~u^2 ||G1|| / 1e-12, is then irrelevant)
-//   flags[2] = both skipped: B1 needs no recomputation
-constexpr double kClusterFloor = 1024.0;
+//              leakage, ~u^2 ||G1|| / 1e-12, is then irrelevant); level 0
+//   flags[2] = level 0 and the cross step skipped: B1 needs no recomputation
+//   scale[0] = s of the last level applied
+constexpr double kLevelCut = 1e-6;
+constexpr int kLevels = 6;
+
+// Outside stream capture the host reads flags[0] after each level's
+// preparation and stops launching once a level is skipped (every later one
+// would be too): one short synchronization instead of ~25 no-op launches
+// per remaining level. Captured streams, and the batched entry point (whose
+// lanes share one issuing thread), launch every level.
+thread_local bool t_host_sync = true;
 
 __global__ void __launch_bounds__(kThreads)
-l2_prep_kernel(const double *G1, int c, const double *delta2, double *H, double *V, int *flags,
-               int *eig_state) {
+level_prep_kernel(const double *G1, int c, const double *delta2, int level, double *scale,
+                  double *H, double *V, int *flags, int *eig_state) {
   __shared__ double red[kThreads];
   __shared__ int inc[kMaxSmall];
   const int tid = threadIdx.x;
+  const int prev_skip = level > 0 && flags[0];   // read by every thread before any write
   double f2 = 0.0;
-  for (int e = tid; e < c * c; e += kThreads) f2 = fma(G1[e], G1[e], f2);
+  if (level == 0)
+    for (int e = tid; e < c * c; e += kThreads) f2 = fma(G1[e], G1[e], f2);
   const double fn = sqrt(block_sum(f2, red));
-  const double thr = kClusterFloor * c * 1.1102230246251565e-16 * fn;
+  const double thr = kLevelCut * (level == 0 ? fn : scale[0]);
   double s = 0.0, m = 0.0;
   for (int i = tid; i < c; i += kThreads) {
     const double ei = G1[i * c + i];
@@ -535,18 +551,21 @@ l2_prep_kernel(const double *G1, int c, const double *delta2, double *H, double 
   s = block_sum(s, red);
   m = block_sum(m, red);
   const double d2 = delta2[0];
-  const int skip_l2 = (m < 2.0) || !(s > d2);
-  const int skip_cross = d2 > 1e-16 * fn;
+  const int skip = prev_skip || (m < 2.0) || !(s > d2);
   if (tid == 0) {
-    flags[0] = skip_l2;
-    flags[1] = skip_cross;
-    flags[2] = skip_l2 && skip_cross;
+    flags[0] = skip;
+    if (level == 0) {
+      const int skip_cross = d2 > 1e-16 * fn;
+      flags[1] = skip_cross;
+      flags[2] = skip && skip_cross;
+    }
+    if (!skip) scale[0] = s;
   }
-  if (tid < kEigSteps) eig_state[tid] = skip_l2;
-  const double inv_s = skip_l2 ? 0.0 : 1.0 / s;
+  if (tid < kEigSteps) eig_state[tid] = skip;
+  const double inv_s = skip ? 0.0 : 1.0 / s;
   for (int e = tid; e < c * c; e += kThreads) {
     const int i = e / c, j = e % c;
-    if (skip_l2) {
+    if (skip) {
       V[e] = (i == j) ? 1.0 : 0.0;
     } else if (inc[i] && inc[j]) {
       H[e] = G1[e] * inv_s;
@@ -697,7 +716,7 @@ __global__ void set_ranks_kernel(RankTable t, long long *ranks) {
 size_t eig_smem(int c) { return ((size_t)2 * c * (c + 1) + (size_t)c * c + 5 * (size_t)c) * sizeof(float); }
 
 struct Layout {
-  double *G, *U0, *U1, *UtU, *T, *S, *E, *H, *V0, *V1, *B1, *e, *sigma, *K, *tmp, *gs;
+  double *G, *U0, *U1, *UtU, *T, *S, *E, *H, *V0, *V1, *B1, *e, *sigma, *K, *tmp, *gs, *scale;
   int *perm, *flags;
 };
 
@@ -716,7 +735,8 @@ Layout carve(double *base, int la, long long N, long long mrows) {
   L.H = p; p += c2;
   L.V0 = p; p += c2;
   L.V1 = p; p += c2;
-  L.flags = (int *)p; p += 12;       // 24 ints: level-two flags, two eigvecs states
+  L.flags = (int *)p; p += 12;       // 24 ints: level flags, two eigvecs states
+  L.scale = p; p += 1;
   L.e = p; p += la;
   L.sigma = p; p += la;
   L.perm = (int *)p; p += la;
@@ -727,7 +747,7 @@ Layout carve(double *base, int la, long long N, long long mrows) {
 }
 
 size_t carve_doubles(int la, long long N, long long mrows) {
-  return (size_t)11 * la * la + 12 + 3 * (size_t)la + (size_t)la * N + (size_t)mrows * la;
+  return (size_t)11 * la * la + 13 + 3 * (size_t)la + (size_t)la * N + (size_t)mrows * la;
 }
 
 Gemm g_gram(const double *B, int la, long long N, double *G) {
@@ -832,35 +852,52 @@ cudaError_t trunc_step(double *Xk, int la, int n, int lb, double *Xkm1, int lm, 
   double *U = L.U0;
   HATT_TRY(gemm_f64(g_tn(U, Xk, la, N, N, L.B1, N), L.gs, st));
   if (deep) {
-    // second level on the low-energy rows of B1, then the cross step
-    HATT_TRY(gemm_f64(g_gram(L.B1, la, N, L.G), L.gs, st));
-    l2_prep_kernel<<<1, kThreads, 0, st>>>(L.G, la, delta2_dev, L.H, L.V0, L.flags, state2);
-    note_launch();
-    HATT_TRY(cudaGetLastError());
-    HATT_TRY(eigvecs(L.H, la, L.V0, L.V1, 1.0, state2, L, st));
-    HATT_TRY(gemm_f64(g_nn(L.U0, L.V0, la, la, la, L.U1), L.gs, st));          // U1 = U V
-    Gemm g = g_tn(L.U1, Xk, la, N, N, L.B1, N);                                 // B1 = U1^T B
-    g.skip_dev = L.flags + 2;
-    HATT_TRY(gemm_f64(g, L.gs, st));
-    g = g_gram(L.B1, la, N, L.G);                                               // G1 = B1 B1^T
+    // further levels on the low-energy rows of B1, then the cross step
+    double *Ua = L.U0, *Ub = L.U1;       // Ua holds the current U
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    HATT_TRY(cudaStreamIsCapturing(st, &cs));
+    const bool host_exit = t_host_sync && cs == cudaStreamCaptureStatusNone;
+    for (int level = 0; level < kLevels; ++level) {
+      Gemm g = g_gram(L.B1, la, N, L.G);                                        // G1 = B1 B1^T
+      if (level > 0) g.skip_dev = L.flags;
+      HATT_TRY(gemm_f64(g, L.gs, st));
+      level_prep_kernel<<<1, kThreads, 0, st>>>(L.G, la, delta2_dev, level, L.scale, L.H, L.V0,
+                                                L.flags, state2);
+      note_launch();
+      HATT_TRY(cudaGetLastError());
+      if (host_exit) {
+        int skip = 0;
+        HATT_TRY(cudaMemcpyAsync(&skip, L.flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+        HATT_TRY(cudaStreamSynchronize(st));
+        if (skip) break;
+      }
+      HATT_TRY(eigvecs(L.H, la, L.V0, L.V1, 1.0, state2, L, st));
+      HATT_TRY(gemm_f64(g_nn(Ua, L.V0, la, la, la, Ub), L.gs, st));              // Ub = Ua V
+      g = g_tn(Ub, Xk, la, N, N, L.B1, N);                                      // B1 = Ub^T B
+      g.skip_dev = L.flags;               // skipped level: V = I, B1 is already Ua^T B
+      HATT_TRY(gemm_f64(g, L.gs, st));
+      std::swap(Ua, Ub);
+    }
+    Gemm g = g_gram(L.B1, la, N, L.G);                                          // G1 = B1 B1^T
     g.skip_dev = L.flags + 1;
     HATT_TRY(gemm_f64(g, L.gs, st));
     cross_kernel<<<1, kOaThreads, 0, st>>>(L.G, la, L.flags, L.E);
     note_launch();
     HATT_TRY(cudaGetLastError());
-    HATT_TRY(gemm_f64(g_nn(L.U1, L.E, la, la, la, L.U0), L.gs, st));           // U0 = U1 (I + E)
-    for (int it = 0; it < 2; ++it) {                                            // U0 -> U1 -> U0
-      double *Ua = it == 0 ? L.U0 : L.U1, *Ub = it == 0 ? L.U1 : L.U0;
+    HATT_TRY(gemm_f64(g_nn(Ua, L.E, la, la, la, Ub), L.gs, st));               // Ub = Ua (I + E)
+    std::swap(Ua, Ub);
+    for (int it = 0; it < 2; ++it) {                                            // orthonormalize
       HATT_TRY(gemm_f64(g_tn(Ua, Ua, la, la, la, L.UtU, la), L.gs, st));
       oa_update_kernel<<<1, kOaThreads, 0, st>>>(L.UtU, L.S, L.G, la, 1, 0.0, nullptr, 0, 0, L.E);
       note_launch();
       HATT_TRY(cudaGetLastError());
       HATT_TRY(gemm_f64(g_nn(Ua, L.E, la, la, la, Ub), L.gs, st));
+      std::swap(Ua, Ub);
     }
-    g = g_tn(L.U0, Xk, la, N, N, L.B1, N);                                      // B1 = U^T B
+    g = g_tn(Ua, Xk, la, N, N, L.B1, N);                                        // B1 = U^T B
     g.skip_dev = L.flags + 2;
     HATT_TRY(gemm_f64(g, L.gs, st));
-    U = L.U0;
+    U = Ua;
   }
   rownorm_kernel<<<la, kThreads, 0, st>>>(L.B1, N, L.e);
   note_launch();
@@ -885,6 +922,8 @@ cudaError_t trunc_step(double *Xk, int la, int n, int lb, double *Xkm1, int lm, 
 
 // Eigenvectors of a symmetric c x c matrix G (columns of U), the same FP32
 // start and FP64 refinement as the truncation sweep uses.
+void set_host_sync(bool allowed) { t_host_sync = allowed; }
+
 size_t sym_eig_scratch_doubles(int c) {
   size_t gs = 0;
   gs = std::max(gs, gemm_scratch_doubles(g_tn(nullptr, nullptr, c, c, c, nullptr, c)));

@@ -1,0 +1,153 @@
+"""Exactly low-rank inputs through the C ABI: raw TT representations whose
+unfoldings have far lower rank than their bond dimension (the folded
+Fourier series of the paper's Example 1), where the Cholesky QR meets null
+directions at the rounding level and the truncation meets noise-only rows.
+
+Checks against the closed form of the series (not a TT computation), the
+FP64 oracle's ranks, and the left-orthonormality every result must have.
+"""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import hatt as ohatt
+from oracle import rounding as oround
+from oracle import tt as ott
+from paper_2410_04385_gb300 import workloads as wl
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+D, N, J = 5, 16, 20
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2410_04385_gb300 import binding, build
+    if not os.path.exists(binding.LIB_PATH):
+        build.build()
+    binding.load()
+    return binding
+
+
+@pytest.fixture(scope="module")
+def series():
+    """y = sum_j a_j sin(j t), z = sum_j b_j cos(j t) on 16^5 points, raw rank
+    2J = 40, with 4000 sampled multi-indices and the closed-form values."""
+    rng = np.random.default_rng(5)
+    a, b = rng.uniform(0.1, 10.1, J), rng.uniform(0.1, 10.1, J)
+    Y = wl.fourier_series_tt(D, N, a, "sin")
+    Z = wl.fourier_series_tt(D, N, b, "cos")
+    idx = rng.integers(0, N, size=(4000, D))
+    t = 2.0 * np.pi * (1.0 + (idx * (float(N) ** np.arange(D))).sum(axis=1)) / float(N) ** D
+    j = np.arange(1, J + 1)
+    ys = np.sin(np.outer(t, j)) @ a
+    zs = np.cos(np.outer(t, j)) @ b
+    return Y, Z, idx, ys, zs
+
+
+def sampled(cores, idx):
+    M = np.ones((idx.shape[0], 1))
+    for k, c in enumerate(cores):
+        M = np.einsum("sa,sab->sb", M, c[:, idx[:, k], :].transpose(1, 0, 2))
+    return M[:, 0]
+
+
+def rel(x, ex):
+    return float(np.sqrt(np.sum((x - ex) ** 2) / np.sum(ex ** 2)))
+
+
+def gpu(cores):
+    return [torch.from_numpy(np.ascontiguousarray(c)).cuda() for c in cores]
+
+
+def host(cores):
+    return [c.cpu().numpy() for c in cores]
+
+
+def assert_left_orthonormal(X, tol=1e-13):
+    """HaTT without a final truncation: cores 1..d-1 of the left-to-right pass."""
+    for c in X[:-1]:
+        Q = c.reshape(-1, c.shape[2])
+        assert np.linalg.norm(Q.T @ Q - np.eye(Q.shape[1])) <= tol
+
+
+def right_gram_deviation(X):
+    """After the right-to-left truncation sweep, cores 2..d hold the kept rows
+    U^T B scaled to unit length. A row of singular value sigma_i carries the
+    absolute rounding of its products with the leading rows, so the rows are
+    orthonormal only to ~u sigma_1 / sigma_i: this returns the largest
+    deviation over the cores, for information."""
+    dev = 0.0
+    for c in X[1:]:
+        Q = c.reshape(c.shape[0], -1)
+        dev = max(dev, float(np.abs(Q @ Q.T - np.eye(Q.shape[0])).max()))
+    return dev
+
+
+def test_round_without_tolerance_keeps_the_tensor(B, series):
+    """tol = 0: only the orthogonalization and a rank-preserving sweep. The
+    bond ranks are bounded by the mode products on the left, and the tensor
+    is kept to rounding accuracy (a Cholesky QR stopped before its null
+    directions are orthonormal loses ~1e-9 here)."""
+    Y, Z, idx, ys, zs = series
+    Xr = host(B.tt_round(gpu(Y), tol=0.0))
+    assert rel(sampled(Xr, idx), ys) <= 1e-13
+    r = ott.ranks(Xr)
+    for k in range(1, D):
+        assert r[k] <= min(N ** k, 2 * J)
+
+
+@pytest.mark.parametrize("tol", [1e-12, 1e-10])
+def test_round_with_tolerance_finds_the_oracle_ranks(B, series, tol):
+    Y, Z, idx, ys, zs = series
+    for T, ex in ((Y, ys), (Z, zs)):
+        Xr = host(B.tt_round(gpu(T), tol=tol))
+        Ar, _ = oround.tt_round(T, tol=tol)
+        assert ott.ranks(Xr) == ott.ranks(Ar)
+        assert rel(sampled(Xr, idx), ex) <= tol
+        assert right_gram_deviation(Xr) < 1e-2
+
+
+def test_round_at_the_rounding_floor(B, series):
+    """tol = 1e-14 sits a few units of rounding above the noise of the sweep:
+    the ranks fall to those of the exact series (at most the oracle's plus
+    one per bond) and the error stays within the tolerance."""
+    Y, Z, idx, ys, zs = series
+    for T, ex in ((Y, ys), (Z, zs)):
+        Xr = host(B.tt_round(gpu(T), tol=1e-14))
+        Ar, _ = oround.tt_round(T, tol=1e-14)
+        assert all(g <= o + 1 for g, o in zip(ott.ranks(Xr), ott.ranks(Ar)))
+        assert rel(sampled(Xr, idx), ex) <= 3e-14
+
+
+def test_round_of_the_example_series_at_the_floor(B):
+    """The full Example 1 series (d = 7, n = 20, 60 terms, raw rank 120), whose
+    unfolding spectra fall through 16 decades: tol = 1e-14 needs every level
+    of the cluster refinement to find the oracle's ranks."""
+    rng = np.random.default_rng(11)
+    a, b = rng.uniform(0.1, 10.1, 60), rng.uniform(0.1, 10.1, 60)
+    for coef, kind in ((a, "sin"), (b, "cos")):
+        T = wl.fourier_series_tt(7, 20, coef, kind)
+        Xr = host(B.tt_round(gpu(T), tol=1e-14))
+        Ar, _ = oround.tt_round(T, tol=1e-14)
+        assert all(g <= o + 1 for g, o in zip(ott.ranks(Xr), ott.ranks(Ar)))
+        assert ott.tt_diff_norm(Xr, Ar) <= 3e-14 * ott.tt_norm(Ar)
+
+
+@pytest.mark.parametrize("variant,ep", [(1, 0.0), (2, 1e-3)])
+def test_hadamard_of_rounded_series(B, series, variant, ep):
+    """Y * Z from inputs rounded to 1e-12, with a sketch rank (24) above the
+    product's numerical rank: the sketches are exactly rank-deficient, the
+    result is still accurate to the inputs' tolerance and left-orthonormal."""
+    Y, Z, idx, ys, zs = series
+    Yr = B.tt_round(gpu(Y), tol=1e-12)
+    Zr = B.tt_round(gpu(Z), tol=1e-12)
+    X = host(B.tt_hadamard_recompress(Yr, Zr, sketch_rank=24, seed=2, variant=variant, ep=ep))
+    assert rel(sampled(X, idx), ys * zs) <= 5e-12
+    assert_left_orthonormal(X, 1e-12)
+    A = ohatt.hadamard_recompress(host(Yr), host(Zr), sketch_rank=24, seed=2, variant=variant, ep=ep)
+    assert rel(sampled(X, idx), sampled(A, idx)) <= 5e-12
