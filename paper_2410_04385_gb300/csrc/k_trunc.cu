@@ -514,7 +514,9 @@ __global__ void select_result_kernel(const int *state, int nsteps, const double 
 // seven decades of energy below its scale; its cut, 1e-6 of the scale, stays
 // above what the previous level resolved. A level is skipped (V = I, and so
 // are all later levels) when its cluster has fewer than two rows or fits
-// under delta^2 as a whole, in which case the cut cannot fall inside it.
+// under delta^2 as a whole, in which case the cut cannot fall inside it, or
+// when the rank cap keeps fewer rows than lie above the cluster (the cut is
+// then made above it).
 //   flags[0] = this level (and every later one) skipped
 //   flags[1] = skip the cross step (delta^2 > 1e-16 ||G1||_F: the level-one
 //              leakage, ~u^2 ||G1|| / 1e-12, is then irrelevant); level 0
@@ -531,8 +533,8 @@ constexpr int kLevels = 6;
 thread_local bool t_host_sync = true;
 
 __global__ void __launch_bounds__(kThreads)
-level_prep_kernel(const double *G1, int c, const double *delta2, int level, double *scale,
-                  double *H, double *V, int *flags, int *eig_state) {
+level_prep_kernel(const double *G1, int c, int cap, const double *delta2, int level,
+                  double *scale, double *H, double *V, int *flags, int *eig_state) {
   __shared__ double red[kThreads];
   __shared__ int inc[kMaxSmall];
   const int tid = threadIdx.x;
@@ -551,7 +553,7 @@ level_prep_kernel(const double *G1, int c, const double *delta2, int level, doub
   s = block_sum(s, red);
   m = block_sum(m, red);
   const double d2 = delta2[0];
-  const int skip = prev_skip || (m < 2.0) || !(s > d2);
+  const int skip = prev_skip || (m < 2.0) || !(s > d2) || (cap > 0 && c - (int)m >= cap);
   if (tid == 0) {
     flags[0] = skip;
     if (level == 0) {
@@ -861,8 +863,8 @@ cudaError_t trunc_step(double *Xk, int la, int n, int lb, double *Xkm1, int lm, 
       Gemm g = g_gram(L.B1, la, N, L.G);                                        // G1 = B1 B1^T
       if (level > 0) g.skip_dev = L.flags;
       HATT_TRY(gemm_f64(g, L.gs, st));
-      level_prep_kernel<<<1, kThreads, 0, st>>>(L.G, la, delta2_dev, level, L.scale, L.H, L.V0,
-                                                L.flags, state2);
+      level_prep_kernel<<<1, kThreads, 0, st>>>(L.G, la, cap, delta2_dev, level, L.scale, L.H,
+                                                L.V0, L.flags, state2);
       note_launch();
       HATT_TRY(cudaGetLastError());
       if (host_exit) {
