@@ -7,10 +7,41 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stddef.h>
+#include <utility>
 
 namespace hatt {
 
 constexpr int kMaxSmall = 128;   // TT_MAX_SMALL_RANK
+
+// Programmatic dependent launch. The path is a chain of ~1000 dependent small
+// kernels, so the gap between one kernel's end and the next one's start is a
+// large part of a step. Every kernel is launched with programmatic stream
+// serialization (launch_k) and begins with pdl_enter: griddepcontrol.wait
+// holds the grid until the grids it depends on have completed and their
+// memory is visible, and launch_dependents then lets the following kernel be
+// scheduled while this one runs (its blocks wait at their own pdl_enter).
+// Since the wait comes before any load or store, every read-after-write and
+// write-after-read order of the stream is kept.
+template <typename... P, typename... A>
+inline cudaError_t launch_k(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem,
+                            cudaStream_t st, A &&...args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
+
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 
 // Process-wide count of kernels enqueued by this library (each launch site
 // calls note_launch once).

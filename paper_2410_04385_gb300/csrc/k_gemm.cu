@@ -53,6 +53,7 @@ template <int OUT, bool LOWP>
 __global__ void __launch_bounds__(kThreads)
 gemm_f64_kernel(Gemm g, int bm, int bn, int tiles_n, int tiles_m, int ksplit, int kchunk,
                 double *partial, int *counters) {
+  pdl_enter();
   using T = typename std::conditional<LOWP, float, double>::type;
   if (g.skip_dev && *g.skip_dev) return;
   __shared__ T As[kBK][kMaxTile + 1];
@@ -269,10 +270,10 @@ void launch_tile(const Gemm &g, const Launch &L, double *scratch, int *counters,
                  cudaStream_t st) {
   const long long blocks = (long long)L.tiles_n * L.tiles_m * L.ksplit * g.batch;
   if (g.prec == kPrecFP64)
-    gemm_f64_kernel<OUT, false><<<(unsigned)blocks, kThreads, 0, st>>>(
+    launch_k(gemm_f64_kernel<OUT, false>, (unsigned)blocks, kThreads, 0, st, 
         g, L.bm, L.bn, L.tiles_n, L.tiles_m, L.ksplit, L.kchunk, scratch, counters);
   else
-    gemm_f64_kernel<OUT, true><<<(unsigned)blocks, kThreads, 0, st>>>(
+    launch_k(gemm_f64_kernel<OUT, true>, (unsigned)blocks, kThreads, 0, st, 
         g, L.bm, L.bn, L.tiles_n, L.tiles_m, L.ksplit, L.kchunk, scratch, counters);
   note_launch();
 }

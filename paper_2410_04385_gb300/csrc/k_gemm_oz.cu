@@ -67,6 +67,7 @@ struct OzOperand {                       // logical (row, k) view of an FP64 ope
 __global__ void __launch_bounds__(256)
 oz_split_kernel(OzOperand op, int nbatch, int bdiv, int rows_pad, int k_pad, uint16_t *out,
                 int *exps, const int *skip) {
+  pdl_enter();
   if (skip && *skip) return;
   const int lane = threadIdx.x & 31;
   const long long w = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -116,6 +117,7 @@ __global__ void __launch_bounds__(kOzThreads)
 oz_mma_kernel(Gemm g, int swap, int tiles_n, int tiles_m, const uint16_t *Psl, const int *Pexp,
               int P_pad, int P_batched, const uint16_t *Qsl, const int *Qexp, int Q_pad,
               int Q_batched, int k_pad) {
+  pdl_enter();
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ uint32_t s_taddr;
   __shared__ __align__(8) uint64_t s_bar;
@@ -310,10 +312,10 @@ cudaError_t gemm_oz(const Gemm &g, double *scratch, cudaStream_t st) {
   int *Pex = (int *)p; p += align256(L.P_ex * 4);
   int *Qex = (int *)p;
   const long long prow = (long long)L.Pb * L.P_pad, qrow = (long long)L.Qb * L.Q_pad;
-  oz_split_kernel<<<(unsigned)ozdiv(prow, 8), 256, 0, st>>>(L.P, L.Pb, g.bdiv, L.P_pad, L.k_pad,
+  launch_k(oz_split_kernel, (unsigned)ozdiv(prow, 8), 256, 0, st, L.P, L.Pb, g.bdiv, L.P_pad, L.k_pad,
                                                             Psl, Pex, g.skip_dev);
   note_launch();
-  oz_split_kernel<<<(unsigned)ozdiv(qrow, 8), 256, 0, st>>>(L.Q, L.Qb, g.bdiv, L.Q_pad, L.k_pad,
+  launch_k(oz_split_kernel, (unsigned)ozdiv(qrow, 8), 256, 0, st, L.Q, L.Qb, g.bdiv, L.Q_pad, L.k_pad,
                                                             Qsl, Qex, g.skip_dev);
   note_launch();
   cudaError_t e = cudaFuncSetAttribute(oz_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -321,7 +323,7 @@ cudaError_t gemm_oz(const Gemm &g, double *scratch, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   const long long blocks = (long long)L.tiles_m * L.tiles_n * g.batch;
   if (blocks >= (1LL << 31)) return cudaErrorInvalidConfiguration;
-  oz_mma_kernel<<<(unsigned)blocks, kOzThreads, kOzSmem, st>>>(
+  launch_k(oz_mma_kernel, (unsigned)blocks, kOzThreads, kOzSmem, st, 
       g, L.swap, L.tiles_n, L.tiles_m, Psl, Pex, L.P_pad, L.P_batched, Qsl, Qex, L.Q_pad,
       L.Q_batched, L.k_pad);
   note_launch();

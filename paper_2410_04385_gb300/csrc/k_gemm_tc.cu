@@ -94,6 +94,7 @@ template <bool TF32>
 __global__ void __launch_bounds__(kTcThreads)
 gemm_tc_kernel(Gemm g, int swap, int bn, int tiles_n, int tiles_m, int ksplit, int kchunk,
                int tmem_cols, double *partial, int *counters) {
+  pdl_enter();
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ uint32_t s_taddr;
   __shared__ __align__(8) uint64_t s_bar;
@@ -308,12 +309,12 @@ cudaError_t gemm_tc(const Gemm &g, double *scratch, int *counters, cudaStream_t 
   if (g.prec == kPrecTF32) {
     e = cudaFuncSetAttribute(gemm_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
     if (e != cudaSuccess) return e;
-    gemm_tc_kernel<true><<<(unsigned)blocks, kTcThreads, kTcSmem, st>>>(
+    launch_k(gemm_tc_kernel<true>, (unsigned)blocks, kTcThreads, kTcSmem, st, 
         g, L.swap, L.bn, L.tiles_n, L.tiles_m, L.ksplit, L.kchunk, L.tmem_cols, scratch, counters);
   } else {
     e = cudaFuncSetAttribute(gemm_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
     if (e != cudaSuccess) return e;
-    gemm_tc_kernel<false><<<(unsigned)blocks, kTcThreads, kTcSmem, st>>>(
+    launch_k(gemm_tc_kernel<false>, (unsigned)blocks, kTcThreads, kTcSmem, st, 
         g, L.swap, L.bn, L.tiles_n, L.tiles_m, L.ksplit, L.kchunk, L.tmem_cols, scratch, counters);
   }
   note_launch();

@@ -45,6 +45,7 @@ __device__ __forceinline__ double sketch_gaussian(uint32_t flat, uint32_t core, 
 }
 
 __global__ void __launch_bounds__(kThreads) sketch_kernel(SketchTable t, double *base) {
+  pdl_enter();
   const long long total = t.offset[t.d];
   const uint32_t k0 = (uint32_t)(t.seed & 0xFFFFFFFFull);
   const uint32_t k1 = (uint32_t)(t.seed >> 32);
@@ -64,6 +65,7 @@ __global__ void __launch_bounds__(kThreads) sketch_kernel(SketchTable t, double 
 __global__ void __launch_bounds__(kThreads)
 sketch_core_kernel(double *out, int a, int n, int b, uint32_t core, uint32_t pair,
                    uint64_t seed) {
+  pdl_enter();
   const long long total = (long long)a * n * b;
   const uint32_t k0 = (uint32_t)(seed & 0xFFFFFFFFull);
   const uint32_t k1 = (uint32_t)(seed >> 32);
@@ -75,6 +77,7 @@ sketch_core_kernel(double *out, int a, int n, int b, uint32_t core, uint32_t pai
 
 __global__ void philox_raw_kernel(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out,
                                   long long count) {
+  pdl_enter();
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < count;
        j += (long long)gridDim.x * blockDim.x) {
     uint32_t x[4] = {ctr[4 * j], ctr[4 * j + 1], ctr[4 * j + 2], ctr[4 * j + 3]};
@@ -89,6 +92,7 @@ __global__ void philox_raw_kernel(const uint32_t *ctr, uint32_t k0, uint32_t k1,
 __global__ void __launch_bounds__(kThreads)
 inv_norm_kernel(const double *x, long long count, double *out, double *partials,
                 unsigned int *ticket) {
+  pdl_enter();
   __shared__ double red[kThreads];
   __shared__ bool last;
   double s = 0.0;
@@ -126,6 +130,7 @@ inv_norm_kernel(const double *x, long long count, double *out, double *partials,
 
 __global__ void pkp_first_kernel(const double *Y, const double *Z, int n, int r1, int s1,
                                  double *C) {
+  pdl_enter();
   const long long total = (long long)n * r1 * s1;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
@@ -137,12 +142,14 @@ __global__ void pkp_first_kernel(const double *Y, const double *Z, int n, int r1
 }
 
 __global__ void set_kernel(double *x, long long count, double v) {
+  pdl_enter();
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
        e += (long long)gridDim.x * blockDim.x)
     x[e] = v;
 }
 
 __global__ void eye_kernel(double *X, int m) {
+  pdl_enter();
   const long long total = (long long)m * m;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x)
@@ -151,6 +158,7 @@ __global__ void eye_kernel(double *X, int m) {
 
 // x[i] /= *divisor (a device scalar, e.g. a norm just computed on the stream).
 __global__ void div_kernel(double *x, long long count, const double *divisor) {
+  pdl_enter();
   const double q = *divisor;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
        i += (long long)gridDim.x * blockDim.x)
@@ -158,6 +166,7 @@ __global__ void div_kernel(double *x, long long count, const double *divisor) {
 }
 
 __global__ void copy_kernel(const double *src, double *dst, long long count) {
+  pdl_enter();
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
        e += (long long)gridDim.x * blockDim.x)
     dst[e] = src[e];
@@ -165,6 +174,7 @@ __global__ void copy_kernel(const double *src, double *dst, long long count) {
 
 __global__ void compact_kernel(const double *src, double *dst, int la, int n, int lb,
                                const long long *ranks, int k) {
+  pdl_enter();
   const int ra = (int)ranks[k], rb = (int)ranks[k + 1];
   const long long total = (long long)ra * n * rb;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
@@ -176,6 +186,7 @@ __global__ void compact_kernel(const double *src, double *dst, int la, int n, in
 }
 
 __global__ void sqrt_kernel(const double *x, double *out) {
+  pdl_enter();
   out[0] = sqrt(fmax(x[0], 0.0));
 }
 
@@ -188,7 +199,7 @@ int grid_for(long long count) {
 cudaError_t sketch_fill(const SketchTable &t, double *base, cudaStream_t st) {
   const long long total = t.offset[t.d];
   if (total <= 0) return cudaSuccess;
-  sketch_kernel<<<grid_for(total), kThreads, 0, st>>>(t, base);
+  launch_k(sketch_kernel, grid_for(total), kThreads, 0, st, t, base);
   note_launch();
   return cudaGetLastError();
 }
@@ -198,7 +209,7 @@ cudaError_t sketch_fill_ptrs(int d, const int64_t *n, const int64_t *ell, uint64
   for (int k = 0; k < d; ++k) {
     const long long total = (long long)ell[k] * n[k] * ell[k + 1];
     if (total <= 0) continue;
-    sketch_core_kernel<<<grid_for(total), kThreads, 0, st>>>(
+    launch_k(sketch_core_kernel, grid_for(total), kThreads, 0, st, 
         cores[k], (int)ell[k], (int)n[k], (int)ell[k + 1], (uint32_t)k, pair, seed);
     note_launch();
     cudaError_t e = cudaGetLastError();
@@ -210,7 +221,7 @@ cudaError_t sketch_fill_ptrs(int d, const int64_t *n, const int64_t *ell, uint64
 cudaError_t philox_raw(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out,
                        long long count, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
-  philox_raw_kernel<<<grid_for(count), kThreads, 0, st>>>(ctr, k0, k1, out, count);
+  launch_k(philox_raw_kernel, grid_for(count), kThreads, 0, st, ctr, k0, k1, out, count);
   note_launch();
   return cudaGetLastError();
 }
@@ -218,7 +229,7 @@ cudaError_t philox_raw(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *
 cudaError_t inv_norm(const double *x, long long count, double *out, double *partials,
                      unsigned int *ticket, cudaStream_t st) {
   const int blocks = (int)std::max<long long>(1, std::min<long long>((count + kThreads - 1) / kThreads, 2 * 152));
-  inv_norm_kernel<<<blocks, kThreads, 0, st>>>(x, count, out, partials, ticket);
+  launch_k(inv_norm_kernel, blocks, kThreads, 0, st, x, count, out, partials, ticket);
   note_launch();
   return cudaGetLastError();
 }
@@ -226,14 +237,14 @@ cudaError_t inv_norm(const double *x, long long count, double *out, double *part
 cudaError_t pkp_first(const double *Y, const double *Z, int n, int r1, int s1, double *C,
                       cudaStream_t st) {
   const long long total = (long long)n * r1 * s1;
-  pkp_first_kernel<<<grid_for(total), kThreads, 0, st>>>(Y, Z, n, r1, s1, C);
+  launch_k(pkp_first_kernel, grid_for(total), kThreads, 0, st, Y, Z, n, r1, s1, C);
   note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t set_value(double *x, long long count, double v, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
-  set_kernel<<<grid_for(count), kThreads, 0, st>>>(x, count, v);
+  launch_k(set_kernel, grid_for(count), kThreads, 0, st, x, count, v);
   note_launch();
   return cudaGetLastError();
 }
@@ -241,21 +252,21 @@ cudaError_t set_value(double *x, long long count, double v, cudaStream_t st) {
 cudaError_t set_identity(double *X, int m, cudaStream_t st) {
   const long long total = (long long)m * m;
   if (total <= 0) return cudaSuccess;
-  eye_kernel<<<grid_for(total), kThreads, 0, st>>>(X, m);
+  launch_k(eye_kernel, grid_for(total), kThreads, 0, st, X, m);
   note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t div_by_scalar(double *x, long long count, const double *divisor, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
-  div_kernel<<<grid_for(count), kThreads, 0, st>>>(x, count, divisor);
+  launch_k(div_kernel, grid_for(count), kThreads, 0, st, x, count, divisor);
   note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t copy_f64(const double *src, double *dst, long long count, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
-  copy_kernel<<<grid_for(count), kThreads, 0, st>>>(src, dst, count);
+  launch_k(copy_kernel, grid_for(count), kThreads, 0, st, src, dst, count);
   note_launch();
   return cudaGetLastError();
 }
@@ -263,13 +274,13 @@ cudaError_t copy_f64(const double *src, double *dst, long long count, cudaStream
 cudaError_t compact_core(const double *src, double *dst, int la, int n, int lb,
                          const long long *ranks_dev, int k, cudaStream_t st) {
   const long long total = (long long)la * n * lb;
-  compact_kernel<<<grid_for(total), kThreads, 0, st>>>(src, dst, la, n, lb, ranks_dev, k);
+  launch_k(compact_kernel, grid_for(total), kThreads, 0, st, src, dst, la, n, lb, ranks_dev, k);
   note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t sqrt_scalar(const double *x, double *out, cudaStream_t st) {
-  sqrt_kernel<<<1, 1, 0, st>>>(x, out);
+  launch_k(sqrt_kernel, 1, 1, 0, st, x, out);
   note_launch();
   return cudaGetLastError();
 }

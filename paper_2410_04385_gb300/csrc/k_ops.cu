@@ -27,6 +27,7 @@ __device__ __forceinline__ double stencil(const double *u, int n, int b, int alp
 // 2 = middle [[u, D u], [0, u]], 3 = last [[D u], [u]]. u is a x n x b.
 __global__ void laplacian_core_kernel(const double *u, int a, int n, int b, int pos,
                                       double inv_h2, double *out) {
+  pdl_enter();
   const int oa = (pos == 2 || pos == 3) ? 2 * a : a;
   const int ob = (pos == 1 || pos == 2) ? 2 * b : b;
   const long long total = (long long)oa * n * ob;
@@ -56,6 +57,7 @@ __global__ void laplacian_core_kernel(const double *u, int a, int n, int b, int 
 // left corner is (ra, rb), or adds it there when accumulate is set.
 __global__ void put_block_kernel(const double *src, int a, int n, int b, double coef, double *dst,
                                  int A, int B, int ra, int rb, int accumulate) {
+  pdl_enter();
   const long long total = (long long)a * n * b;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
@@ -79,6 +81,7 @@ constexpr int kSelThreads = 1024;
 __global__ void __launch_bounds__(kSelThreads)
 select_directions_kernel(const double *Uf, const double *V, long long x, int c, double ep,
                          double *UR, double *VR, int *Rout) {
+  pdl_enter();
   __shared__ double e[kMaxSmall];
   __shared__ int pos[kMaxSmall];
   __shared__ int s_R;
@@ -136,7 +139,7 @@ cudaError_t laplacian_core(const double *u, int a, int n, int b, int pos, double
                            double *out, cudaStream_t st) {
   const int oa = (pos == 2 || pos == 3) ? 2 * a : a;
   const int ob = (pos == 1 || pos == 2) ? 2 * b : b;
-  laplacian_core_kernel<<<op_grid((long long)oa * n * ob), kOpThreads, 0, st>>>(u, a, n, b, pos,
+  launch_k(laplacian_core_kernel, op_grid((long long)oa * n * ob), kOpThreads, 0, st, u, a, n, b, pos,
                                                                                inv_h2, out);
   note_launch();
   return cudaGetLastError();
@@ -144,7 +147,7 @@ cudaError_t laplacian_core(const double *u, int a, int n, int b, int pos, double
 
 cudaError_t put_block(const double *src, int a, int n, int b, double coef, double *dst, int A,
                       int B, int ra, int rb, bool accumulate, cudaStream_t st) {
-  put_block_kernel<<<op_grid((long long)a * n * b), kOpThreads, 0, st>>>(src, a, n, b, coef, dst,
+  launch_k(put_block_kernel, op_grid((long long)a * n * b), kOpThreads, 0, st, src, a, n, b, coef, dst,
                                                                         A, B, ra, rb, accumulate);
   note_launch();
   return cudaGetLastError();
@@ -153,7 +156,7 @@ cudaError_t put_block(const double *src, int a, int n, int b, double coef, doubl
 cudaError_t select_directions(const double *Uf, const double *V, long long x, int c, double ep,
                               double *UR, double *VR, int *R, cudaStream_t st) {
   if (c < 1 || c > kMaxSmall) return cudaErrorInvalidValue;
-  select_directions_kernel<<<1, kSelThreads, 0, st>>>(Uf, V, x, c, ep, UR, VR, R);
+  launch_k(select_directions_kernel, 1, kSelThreads, 0, st, Uf, V, x, c, ep, UR, VR, R);
   note_launch();
   return cudaGetLastError();
 }

@@ -59,6 +59,7 @@ __device__ __forceinline__ double rsqrt_newton(double x) {
 //   flags[2] passes applied, flags[3] shifted passes (diagnostics)
 __global__ void __launch_bounds__(kCholThreads)
 chol_inv_kernel(const double *Gg, double *Ut_g, double *y_g, int c, int m, int *flags) {
+  pdl_enter();
   if (flags[0]) {
     if (threadIdx.x == 0) flags[1] = 1;
     return;
@@ -195,6 +196,7 @@ chol_inv_kernel(const double *Gg, double *Ut_g, double *y_g, int c, int m, int *
 __global__ void __launch_bounds__(kTrsmThreads)
 trsm_rows_kernel(double *S, int m, int c, long long ldS, const double *Ut, const double *y,
                  const int *flags) {
+  pdl_enter();
   if (flags[1]) return;
   extern __shared__ double sm[];
   double *Us = sm;                       // c x c
@@ -268,11 +270,11 @@ cudaError_t qr_inplace(double *S, int m, int c, long long ldS, double *scratch, 
   for (int p = 0; p < kPasses; ++p) {
     e = gemm_f64(gd, gs, st);
     if (e != cudaSuccess) return e;
-    chol_inv_kernel<<<1, kCholThreads, chol_smem(c), st>>>(G, Ut, y, c, m, flags);
+    launch_k(chol_inv_kernel, 1, kCholThreads, chol_smem(c), st, G, Ut, y, c, m, flags);
     note_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    trsm_rows_kernel<<<blocks, kTrsmThreads, trsm_smem(c), st>>>(S, m, c, ldS, Ut, y, flags);
+    launch_k(trsm_rows_kernel, blocks, kTrsmThreads, trsm_smem(c), st, S, m, c, ldS, Ut, y, flags);
     note_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -171,6 +171,7 @@ __device__ void tridiag_shifted_solve(const float *d, const float *e, int c, flo
 
 __global__ void __launch_bounds__(kEigThreads)
 eig_tridiag32_kernel(const double *G, int c, double *U, const int *skip) {
+  pdl_enter();
   if (skip && *skip) return;
   extern __shared__ float fs[];
   const int ld = c + 1;
@@ -414,6 +415,7 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 __global__ void __launch_bounds__(kOaThreads)
 oa_update_kernel(const double *UtU, const double *S, const double *G, int c, int orth_only,
                  double floor_norm, int *state, int step, int nsteps, double *Eout) {
+  pdl_enter();
   if (state && state[step]) return;
   __shared__ double wred[3][kOaThreads / 32];
   __shared__ double lam[kMaxSmall];
@@ -488,6 +490,7 @@ oa_update_kernel(const double *UtU, const double *S, const double *G, int c, int
 // result sits in Ub and is copied to Ua.
 __global__ void select_result_kernel(const int *state, int nsteps, const double *Ub, double *Ua,
                                      int count) {
+  pdl_enter();
   int applied = nsteps;
   for (int j = 0; j < nsteps; ++j)
     if (state[j]) { applied = j; break; }
@@ -535,6 +538,7 @@ thread_local bool t_host_sync = true;
 __global__ void __launch_bounds__(kThreads)
 level_prep_kernel(const double *G1, int c, int cap, const double *delta2, int level,
                   double *scale, double *H, double *V, int *flags, int *eig_state) {
+  pdl_enter();
   __shared__ double red[kThreads];
   __shared__ int inc[kMaxSmall];
   const int tid = threadIdx.x;
@@ -586,6 +590,7 @@ level_prep_kernel(const double *G1, int c, int cap, const double *delta2, int le
 // first-order step would not converge. Eout = I + E (I when skipped).
 __global__ void __launch_bounds__(kOaThreads)
 cross_kernel(const double *G1, int c, const int *flags, double *Eout) {
+  pdl_enter();
   const int skip = flags[1];
   for (int e = threadIdx.x; e < c * c; e += kOaThreads) {
     const int i = e / c, j = e % c;
@@ -604,6 +609,7 @@ cross_kernel(const double *G1, int c, const int *flags, double *Eout) {
 
 __global__ void __launch_bounds__(kThreads)
 rownorm_kernel(const double *B1, long long N, double *e) {
+  pdl_enter();
   __shared__ double red[kThreads];
   const int row = blockIdx.x;
   double s = 0.0;
@@ -619,6 +625,7 @@ rownorm_kernel(const double *B1, long long N, double *e) {
 __global__ void __launch_bounds__(kThreads)
 rank_kernel(const double *e, int c, int cap, const double *delta2, long long *ranks, int k,
             int *perm, double *sigma) {
+  pdl_enter();
   __shared__ double sorted[kMaxSmall];
   const int tid = threadIdx.x;
   for (int i = tid; i < c; i += kThreads) {
@@ -655,6 +662,7 @@ rank_kernel(const double *e, int c, int cap, const double *delta2, long long *ra
 
 __global__ void newcore_kernel(const double *B1, int c, long long N, const int *perm,
                                const double *sigma, const long long *ranks, int k, double *Xk) {
+  pdl_enter();
   const int rho = (int)ranks[k];
   const long long total = (long long)c * N;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
@@ -672,6 +680,7 @@ __global__ void newcore_kernel(const double *B1, int c, long long N, const int *
 
 __global__ void kmat_kernel(const double *U, int c, const int *perm, const double *sigma,
                             const long long *ranks, int k, double *K) {
+  pdl_enter();
   const int rho = (int)ranks[k];
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < c * c; t += gridDim.x * blockDim.x) {
     const int l = t / c, j = t % c;
@@ -682,6 +691,7 @@ __global__ void kmat_kernel(const double *U, int c, const int *perm, const doubl
 __global__ void __launch_bounds__(kThreads)
 delta2_kernel(const double *x, long long count, double tol, int d, double *out, double *partials,
               unsigned int *ticket) {
+  pdl_enter();
   __shared__ double red[kThreads];
   __shared__ bool last;
   double s = 0.0;
@@ -712,6 +722,7 @@ struct RankTable {
 };
 
 __global__ void set_ranks_kernel(RankTable t, long long *ranks) {
+  pdl_enter();
   for (int i = threadIdx.x; i < t.count; i += blockDim.x) ranks[i] = t.r[i];
 }
 
@@ -804,7 +815,7 @@ static cudaError_t eigvecs(const double *A, int c, double *Ua, double *Ub, doubl
 #define HATT_TRY(x) do { e = (x); if (e != cudaSuccess) return e; } while (0)
   HATT_TRY(cudaFuncSetAttribute(eig_tridiag32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)eig_smem(kMaxSmall)));
-  eig_tridiag32_kernel<<<1, kEigThreads, eig_smem(c), st>>>(A, c, Ua, state);
+  launch_k(eig_tridiag32_kernel, 1, kEigThreads, eig_smem(c), st, A, c, Ua, state);
   note_launch();
   HATT_TRY(cudaGetLastError());
   double *U = Ua, *Un = Ub;
@@ -821,7 +832,7 @@ static cudaError_t eigvecs(const double *A, int c, double *Ua, double *Ub, doubl
       g.skip_dev = state + it;
       HATT_TRY(gemm_f64(g, L.gs, st));
     }
-    oa_update_kernel<<<1, kOaThreads, 0, st>>>(L.UtU, L.S, A, c, orth_only, floor_norm, state, it,
+    launch_k(oa_update_kernel, 1, kOaThreads, 0, st, L.UtU, L.S, A, c, orth_only, floor_norm, state, it,
                                                 kEigSteps, L.E);
     note_launch();
     HATT_TRY(cudaGetLastError());
@@ -831,7 +842,7 @@ static cudaError_t eigvecs(const double *A, int c, double *Ua, double *Ub, doubl
     std::swap(U, Un);
   }
   static_assert(kEigSteps % 2 == 0, "with every step applied the result is in Ua");
-  select_result_kernel<<<4, kThreads, 0, st>>>(state, kEigSteps, Ub, Ua, c * c);
+  launch_k(select_result_kernel, 4, kThreads, 0, st, state, kEigSteps, Ub, Ua, c * c);
   note_launch();
   HATT_TRY(cudaGetLastError());
 #undef HATT_TRY
@@ -863,7 +874,7 @@ cudaError_t trunc_step(double *Xk, int la, int n, int lb, double *Xkm1, int lm, 
       Gemm g = g_gram(L.B1, la, N, L.G);                                        // G1 = B1 B1^T
       if (level > 0) g.skip_dev = L.flags;
       HATT_TRY(gemm_f64(g, L.gs, st));
-      level_prep_kernel<<<1, kThreads, 0, st>>>(L.G, la, cap, delta2_dev, level, L.scale, L.H,
+      launch_k(level_prep_kernel, 1, kThreads, 0, st, L.G, la, cap, delta2_dev, level, L.scale, L.H,
                                                 L.V0, L.flags, state2);
       note_launch();
       HATT_TRY(cudaGetLastError());
@@ -883,14 +894,14 @@ cudaError_t trunc_step(double *Xk, int la, int n, int lb, double *Xkm1, int lm, 
     Gemm g = g_gram(L.B1, la, N, L.G);                                          // G1 = B1 B1^T
     g.skip_dev = L.flags + 1;
     HATT_TRY(gemm_f64(g, L.gs, st));
-    cross_kernel<<<1, kOaThreads, 0, st>>>(L.G, la, L.flags, L.E);
+    launch_k(cross_kernel, 1, kOaThreads, 0, st, L.G, la, L.flags, L.E);
     note_launch();
     HATT_TRY(cudaGetLastError());
     HATT_TRY(gemm_f64(g_nn(Ua, L.E, la, la, la, Ub), L.gs, st));               // Ub = Ua (I + E)
     std::swap(Ua, Ub);
     for (int it = 0; it < 2; ++it) {                                            // orthonormalize
       HATT_TRY(gemm_f64(g_tn(Ua, Ua, la, la, la, L.UtU, la), L.gs, st));
-      oa_update_kernel<<<1, kOaThreads, 0, st>>>(L.UtU, L.S, L.G, la, 1, 0.0, nullptr, 0, 0, L.E);
+      launch_k(oa_update_kernel, 1, kOaThreads, 0, st, L.UtU, L.S, L.G, la, 1, 0.0, nullptr, 0, 0, L.E);
       note_launch();
       HATT_TRY(cudaGetLastError());
       HATT_TRY(gemm_f64(g_nn(Ua, L.E, la, la, la, Ub), L.gs, st));
@@ -901,18 +912,18 @@ cudaError_t trunc_step(double *Xk, int la, int n, int lb, double *Xkm1, int lm, 
     HATT_TRY(gemm_f64(g, L.gs, st));
     U = Ua;
   }
-  rownorm_kernel<<<la, kThreads, 0, st>>>(L.B1, N, L.e);
+  launch_k(rownorm_kernel, la, kThreads, 0, st, L.B1, N, L.e);
   note_launch();
   HATT_TRY(cudaGetLastError());
-  rank_kernel<<<1, kThreads, 0, st>>>(L.e, la, cap, delta2_dev, ranks_dev, k, L.perm, L.sigma);
+  launch_k(rank_kernel, 1, kThreads, 0, st, L.e, la, cap, delta2_dev, ranks_dev, k, L.perm, L.sigma);
   note_launch();
   HATT_TRY(cudaGetLastError());
   const long long tot = (long long)la * N;
   const int blocks = (int)std::min<long long>((tot + kThreads - 1) / kThreads, 8 * 152);
-  newcore_kernel<<<blocks, kThreads, 0, st>>>(L.B1, la, N, L.perm, L.sigma, ranks_dev, k, Xk);
+  launch_k(newcore_kernel, blocks, kThreads, 0, st, L.B1, la, N, L.perm, L.sigma, ranks_dev, k, Xk);
   note_launch();
   HATT_TRY(cudaGetLastError());
-  kmat_kernel<<<(la * la + kThreads - 1) / kThreads, kThreads, 0, st>>>(U, la, L.perm, L.sigma,
+  launch_k(kmat_kernel, (la * la + kThreads - 1) / kThreads, kThreads, 0, st, U, la, L.perm, L.sigma,
                                                                          ranks_dev, k, L.K);
   note_launch();
   HATT_TRY(cudaGetLastError());
@@ -947,7 +958,7 @@ cudaError_t sym_eig(const double *G, int c, double *U, double *scratch, cudaStre
 cudaError_t trunc_delta2(const double *x, long long count, double tol, int d, double *delta2_dev,
                          double *partials, unsigned int *ticket, cudaStream_t st) {
   const int blocks = (int)std::max<long long>(1, std::min<long long>((count + kThreads - 1) / kThreads, 2 * 152));
-  delta2_kernel<<<blocks, kThreads, 0, st>>>(x, count, tol, d, delta2_dev, partials, ticket);
+  launch_k(delta2_kernel, blocks, kThreads, 0, st, x, count, tol, d, delta2_dev, partials, ticket);
   note_launch();
   return cudaGetLastError();
 }
@@ -958,7 +969,7 @@ cudaError_t set_ranks(long long *ranks_dev, const long long *ranks_host, int cou
   RankTable t;
   t.count = count;
   for (int i = 0; i < count; ++i) t.r[i] = ranks_host[i];
-  set_ranks_kernel<<<1, 256, 0, st>>>(t, ranks_dev);
+  launch_k(set_ranks_kernel, 1, 256, 0, st, t, ranks_dev);
   note_launch();
   return cudaGetLastError();
 }
