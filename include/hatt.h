@@ -105,7 +105,14 @@ typedef enum {
  *                on the host: the call synchronizes `stream` once per core and
  *                returns TT_ERR_ARG while the stream is being captured; the
  *                batched entry point rejects it.
- *   ep           HaTT-2 truncation threshold, 0 <= ep < 1 (ignored by variant 1) */
+ *   ep           HaTT-2 truncation threshold, 0 <= ep < 1 (ignored by variant 1)
+ *   fixed_ranks  0 = the output cores are compacted to the ranks the truncation kept and
+ *                X->r is written from the device by an asynchronous copy (valid once the
+ *                stream reaches it); 1 = the output keeps the rank bound of the plan call
+ *                (min(l_k, max_rank) when truncating with a cap, else l_k): rows and
+ *                columns past the kept ranks are zero, X->r is set on the host before the
+ *                call returns, and nothing is read back, so a call whose inputs have fixed
+ *                shapes can be captured in a CUDA graph and replayed (time stepping) */
 typedef struct {
   int64_t max_rank;
   double tol;
@@ -115,6 +122,7 @@ typedef struct {
   int32_t precision;
   int32_t variant;
   double ep;
+  int32_t fixed_ranks;
 } tt_opts;
 
 /* Rank plan and workspace size of tt_hadamard_recompress.
@@ -178,8 +186,9 @@ int tt_hadamard_recompress_batch(int32_t count, const tt_t *Y, const tt_t *Z,
                                  const tt_opts *opts, tt_t *X, int32_t lanes, void *workspace,
                                  size_t workspace_bytes, void *stream);
 
-/* Workspace size of tt_round and its output rank bound (min(r_k, max_rank)
- * clamped by the mode-size products), both host outputs. */
+/* Workspace size of tt_round and its output rank bound b_k = min(r_k, b_{k-1} n_{k-1})
+ * (the bound of the left-to-right QR sweep; the ranks kept are also <= max_rank when
+ * max_rank > 0), both host outputs. */
 int tt_round_plan(const tt_t *A, int64_t max_rank, double tol, int64_t *out_rank_bound,
                   size_t *workspace_bytes);
 
@@ -190,6 +199,15 @@ int tt_round_plan(const tt_t *A, int64_t max_rank, double tol, int64_t *out_rank
  * must be <= TT_MAX_SMALL_RANK. */
 int tt_round(const tt_t *A, int64_t max_rank, double tol, tt_t *B, void *workspace,
              size_t workspace_bytes, void *stream);
+
+/* tt_round_plan / tt_round with the fixed_ranks option of tt_opts: with
+ * fixed_ranks = 1 the output bound is min(b_k, max_rank) (max_rank > 0), B keeps it
+ * with zeros past the kept ranks, B->r is set on the host and nothing is read back
+ * (capturable). fixed_ranks = 0 is tt_round_plan / tt_round. */
+int tt_round_ex_plan(const tt_t *A, int64_t max_rank, double tol, int32_t fixed_ranks,
+                     int64_t *out_rank_bound, size_t *workspace_bytes);
+int tt_round_ex(const tt_t *A, int64_t max_rank, double tol, int32_t fixed_ranks, tt_t *B,
+                void *workspace, size_t workspace_bytes, void *stream);
 
 /* Workspace of tt_dot / tt_norm (host output). */
 int tt_dot_plan(const tt_t *A, const tt_t *B, size_t *workspace_bytes);

@@ -5,8 +5,9 @@ box [0, 2 pi)^d with central differences,
 u^2 = HaTT-1(u ⊙ u) and u^3 = HaTT-1(u^2 ⊙ u) (never the explicit Kronecker
 cores), tt_round at a relative tolerance after every step, and the discrete
 energy E = h^d [eps^2/2 (-<u, Lap_h u>) + 1/4 (<u^2, u^2> - 2 <u, u> + n^d)].
-The module only sequences library calls (each call synchronizes to learn the
-data-dependent output ranks)."""
+`step` sequences library calls (each call synchronizes to learn the
+data-dependent output ranks); `FixedRankStepper` keeps every shape fixed and
+replays one captured step."""
 from __future__ import annotations
 
 import math
@@ -38,3 +39,78 @@ def step(u: Sequence[torch.Tensor], h: float, eps: float, dt: float, max_rank: i
     w = binding.tt_lincomb([u, lap, u3], [1.0 + dt, dt * eps * eps, -dt])
     un = binding.tt_round(w, max_rank, tol)
     return [c.contiguous() for c in un], u2
+
+
+def pad_ranks(u: Sequence[torch.Tensor], rank: int) -> List[torch.Tensor]:
+    """The same TT with every inner rank raised to `rank` by zero rows and
+    columns (no rank is lowered)."""
+    d = len(u)
+    rk = [1] + [max(int(c.shape[2]), rank) for c in u[:-1]] + [1]
+    out = []
+    for k, c in enumerate(u):
+        p = torch.zeros((rk[k], c.shape[1], rk[k + 1]), dtype=c.dtype, device=c.device)
+        p[: c.shape[0], :, : c.shape[2]] = c
+        out.append(p)
+    return out
+
+
+class FixedRankStepper:
+    """Explicit Euler steps with every shape fixed, so one step can be captured
+    in a CUDA graph and replayed: u is held at the padded rank `rank` (zero
+    past the ranks the rounding keeps), both HaTT-1 calls and the rounding run
+    with fixed_ranks=1, and the Laplacian, the combination and the rounding
+    write into buffers planned once. The graph fixes the sketch seeds, so every
+    step uses `seed` and `seed + 1`."""
+
+    def __init__(self, u0: Sequence[torch.Tensor], h: float, eps: float, dt: float, rank: int,
+                 tol: float, hatt_tol: float, hatt_rank: int, seed: int,
+                 precision: int = binding.TT_FP64):
+        self.h, self.eps, self.dt = h, eps, dt
+        self.u = [c.contiguous().clone() for c in pad_ranks(u0, rank)]
+        ranks = [int(self.u[0].shape[0])] + [int(c.shape[2]) for c in self.u]
+        self.h1 = binding.HadamardRecompressor(self.u, self.u, max_rank=hatt_rank, tol=hatt_tol,
+                                               seed=seed, precision=precision, fixed_ranks=1)
+        self.u2 = self.h1.result()
+        self.h2 = binding.HadamardRecompressor(self.u2, self.u, max_rank=hatt_rank, tol=hatt_tol,
+                                               seed=seed + 1, precision=precision, fixed_ranks=1)
+        self.u3 = self.h2.result()
+        self.lap = binding.tt_laplacian(self.u, 1.0 / (h * h))
+        self.coef = [1.0 + dt, dt * eps * eps, -dt]
+        self.w = binding.tt_lincomb([self.u, self.lap, self.u3], self.coef)
+        self.rnd = binding.Rounder(self.w, max_rank=rank, tol=tol, fixed_ranks=1)
+        self.un = self.rnd.result()
+        if [int(self.un[0].shape[0])] + [int(c.shape[2]) for c in self.un] != ranks:
+            raise ValueError("the rounding bound differs from the padded rank: lower `rank` to "
+                             "at most the mode-size products")
+        self.graph = None
+
+    def step(self):
+        """One step, enqueued on the current stream (nothing is read back)."""
+        self.h1.run()
+        self.h2.run()
+        binding.tt_laplacian(self.u, 1.0 / (self.h * self.h), out=self.lap)
+        binding.tt_lincomb([self.u, self.lap, self.u3], self.coef, out=self.w)
+        self.rnd.run()
+        for a, b in zip(self.u, self.un):
+            a.copy_(b)
+
+    def capture(self):
+        """Capture one step in a CUDA graph. The eager warm-up before the
+        capture is a real step: u has advanced by one step on return."""
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.step()
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.step()
+        self.graph = g
+        return g
+
+    def replay(self):
+        self.graph.replay()
+
+    def energy(self) -> float:
+        return energy(self.u, self.u2, self.h, self.eps)

@@ -44,6 +44,7 @@ class OptsStruct(ctypes.Structure):
         ("precision", ctypes.c_int32),
         ("variant", ctypes.c_int32),
         ("ep", ctypes.c_double),
+        ("fixed_ranks", ctypes.c_int32),
     ]
 
 
@@ -56,6 +57,7 @@ class HattError(RuntimeError):
 _lib = None
 
 EXPORTS = ("tt_hadamard_recompress_plan", "tt_hadamard_recompress", "tt_round_plan", "tt_round",
+           "tt_round_ex_plan", "tt_round_ex",
            "tt_dot_plan", "tt_dot", "tt_dot_noalloc", "tt_norm", "tt_sketch_tt",
            "tt_philox4x32_10", "tt_launch_count", "tt_kernel_timer_start",
            "tt_kernel_timer_stop", "tt_device_error", "tt_hadamard_recompress_batch_plan",
@@ -85,6 +87,10 @@ def load(path: Optional[str] = None):
                                   P(ctypes.c_size_t)]
     lib.tt_round.argtypes = [P(TTStruct), ctypes.c_int64, ctypes.c_double, P(TTStruct), vp,
                              ctypes.c_size_t, vp]
+    lib.tt_round_ex_plan.argtypes = [P(TTStruct), ctypes.c_int64, ctypes.c_double, ctypes.c_int32,
+                                     P(ctypes.c_int64), P(ctypes.c_size_t)]
+    lib.tt_round_ex.argtypes = [P(TTStruct), ctypes.c_int64, ctypes.c_double, ctypes.c_int32,
+                                P(TTStruct), vp, ctypes.c_size_t, vp]
     lib.tt_dot_plan.argtypes = [P(TTStruct), P(TTStruct), P(ctypes.c_size_t)]
     lib.tt_dot.argtypes = [P(TTStruct), P(TTStruct), vp, vp, ctypes.c_size_t, vp]
     lib.tt_dot_noalloc.argtypes = [P(TTStruct), P(TTStruct), vp, vp]
@@ -127,27 +133,32 @@ def tt_scale(x: torch.Tensor, divisor: torch.Tensor, stream=None) -> None:
                                        ctypes.c_void_p(divisor.data_ptr()), _stream_ptr(stream)))
 
 
-def tt_laplacian(A: Sequence[torch.Tensor], inv_h2: float, stream=None) -> List[torch.Tensor]:
-    """Periodic central-difference Laplacian of the TT A (ranks doubled)."""
+def tt_laplacian(A: Sequence[torch.Tensor], inv_h2: float, out=None,
+                 stream=None) -> List[torch.Tensor]:
+    """Periodic central-difference Laplacian of the TT A (ranks doubled);
+    `out` may hold preallocated cores of the result's shapes."""
     Ad = TT(A)
     d, n, r = Ad.d, Ad.n, Ad.r
     rl = [1] + [2 * v for v in r[1:-1]] + [1] if d > 1 else [1, 1]
-    out = [torch.empty((rl[k], n[k], rl[k + 1]), dtype=torch.float64, device=A[0].device)
-           for k in range(d)]
+    if out is None:
+        out = [torch.empty((rl[k], n[k], rl[k + 1]), dtype=torch.float64, device=A[0].device)
+               for k in range(d)]
     Ld = TT(out)
     _check("tt_laplacian", load().tt_laplacian(Ad.ref(), float(inv_h2), Ld.ref(), _stream_ptr(stream)))
     return out
 
 
-def tt_lincomb(terms: Sequence[Sequence[torch.Tensor]], coef: Sequence[float],
+def tt_lincomb(terms: Sequence[Sequence[torch.Tensor]], coef: Sequence[float], out=None,
                stream=None) -> List[torch.Tensor]:
-    """sum_j coef[j] terms[j] as one TT (block-diagonal cores)."""
+    """sum_j coef[j] terms[j] as one TT (block-diagonal cores); `out` may
+    hold preallocated cores of the result's shapes."""
     Td = [TT(t) for t in terms]
     d, n = Td[0].d, Td[0].n
     rs = [sum(t.r[k] for t in Td) for k in range(d + 1)]
     rs[0] = rs[d] = 1
-    out = [torch.empty((rs[k], n[k], rs[k + 1]), dtype=torch.float64, device=terms[0][0].device)
-           for k in range(d)]
+    if out is None:
+        out = [torch.empty((rs[k], n[k], rs[k + 1]), dtype=torch.float64,
+                           device=terms[0][0].device) for k in range(d)]
     Sd = TT(out)
     Ta = (TTStruct * len(Td))(*[t.s for t in Td])
     ca = (ctypes.c_double * len(coef))(*[float(c) for c in coef])
@@ -241,9 +252,10 @@ class TT:
 
 
 def make_opts(max_rank=0, tol=0.0, sketch_rank=0, oversample=10, seed=0, precision=TT_FP64,
-              variant=1, ep=0.0):
+              variant=1, ep=0.0, fixed_ranks=0):
     return OptsStruct(int(max_rank), float(tol), int(sketch_rank), int(oversample),
-                      int(seed) & 0xFFFFFFFFFFFFFFFF, int(precision), int(variant), float(ep))
+                      int(seed) & 0xFFFFFFFFFFFFFFFF, int(precision), int(variant), float(ep),
+                      int(fixed_ranks))
 
 
 class HadamardRecompressor:
@@ -310,40 +322,64 @@ class HadamardRecompressor:
 
 
 def tt_hadamard_recompress(Y, Z, max_rank=0, tol=0.0, sketch_rank=0, oversample=10, seed=0,
-                           precision=TT_FP64, variant=1, ep=0.0,
+                           precision=TT_FP64, variant=1, ep=0.0, fixed_ranks=0,
                            stream=None) -> List[torch.Tensor]:
     """HaTT recompression of Y ⊙ Z; returns the output cores (synchronizes).
     precision: TT_FP64, TT_MIXED_FP32 / TF32 / BF16 or TT_FP64_TC;
     variant 1 = HaTT-1, 2 = HaTT-2 with threshold ep."""
     h = HadamardRecompressor(Y, Z, max_rank=max_rank, tol=tol, sketch_rank=sketch_rank,
                              oversample=oversample, seed=seed, precision=precision,
-                             variant=variant, ep=ep)
+                             variant=variant, ep=ep, fixed_ranks=fixed_ranks)
     h.run(stream)
     (stream or torch.cuda.current_stream()).synchronize()
     return [c.clone() for c in h.result()]
 
 
-def tt_round(A, max_rank=0, tol=0.0, stream=None) -> List[torch.Tensor]:
-    lib = load()
-    Ad = TT(A)
-    d = Ad.d
-    bound = (ctypes.c_int64 * (d + 1))()
-    ws = ctypes.c_size_t()
-    _check("tt_round_plan", lib.tt_round_plan(Ad.ref(), int(max_rank), float(tol), bound,
-                                              ctypes.byref(ws)))
-    dev = A[0].device
-    work = torch.empty(max(int(ws.value), 1), dtype=torch.uint8, device=dev)
-    n = Ad.n
-    b = [int(v) for v in bound]
-    bufs = [torch.empty(b[k] * n[k] * b[k + 1], dtype=torch.float64, device=dev) for k in range(d)]
-    Bd = TT(n=n, r=b)
-    Bd.set_core_ptrs([t.data_ptr() for t in bufs])
-    _check("tt_round", lib.tt_round(Ad.ref(), int(max_rank), float(tol), Bd.ref(),
-                                    ctypes.c_void_p(work.data_ptr()), int(ws.value),
-                                    _stream_ptr(stream)))
+class Rounder:
+    """tt_round_ex planned once for inputs of fixed shapes: owns the output
+    buffers and the workspace, so `run` allocates nothing and (with
+    fixed_ranks=1, which also keeps the output shapes fixed) can be captured
+    in a CUDA graph."""
+
+    def __init__(self, A: Sequence[torch.Tensor], max_rank=0, tol=0.0, fixed_ranks=0):
+        lib = load()
+        self.Ad = TT(A)
+        self.max_rank, self.tol, self.fixed = int(max_rank), float(tol), int(fixed_ranks)
+        d = self.Ad.d
+        bound = (ctypes.c_int64 * (d + 1))()
+        ws = ctypes.c_size_t()
+        _check("tt_round_ex_plan", lib.tt_round_ex_plan(self.Ad.ref(), self.max_rank, self.tol,
+                                                        self.fixed, bound, ctypes.byref(ws)))
+        dev = A[0].device
+        self.workspace_bytes = int(ws.value)
+        self.workspace = torch.empty(max(self.workspace_bytes, 1), dtype=torch.uint8, device=dev)
+        n = self.Ad.n
+        b = [int(v) for v in bound]
+        self.out_bufs = [torch.empty(b[k] * n[k] * b[k + 1], dtype=torch.float64, device=dev)
+                         for k in range(d)]
+        self.Bd = TT(n=n, r=b, pinned_ranks=True)
+        self.Bd.set_core_ptrs([t.data_ptr() for t in self.out_bufs])
+
+    def run(self, stream=None):
+        _check("tt_round_ex", load().tt_round_ex(self.Ad.ref(), self.max_rank, self.tol, self.fixed,
+                                                 self.Bd.ref(),
+                                                 ctypes.c_void_p(self.workspace.data_ptr()),
+                                                 self.workspace_bytes, _stream_ptr(stream)))
+
+    def result(self) -> List[torch.Tensor]:
+        """Output cores as views (call after the stream has completed)."""
+        r, n = self.Bd.r, self.Bd.n
+        return [self.out_bufs[k][: r[k] * n[k] * r[k + 1]].view(r[k], n[k], r[k + 1])
+                for k in range(self.Bd.d)]
+
+
+def tt_round(A, max_rank=0, tol=0.0, fixed_ranks=0, stream=None) -> List[torch.Tensor]:
+    """TT rounding of A (synchronizes); fixed_ranks=1 keeps the bound ranks
+    min(b_k, max_rank), zero past the ranks kept."""
+    h = Rounder(A, max_rank=max_rank, tol=tol, fixed_ranks=fixed_ranks)
+    h.run(stream)
     (stream or torch.cuda.current_stream()).synchronize()
-    r = Bd.r
-    return [bufs[k][: r[k] * n[k] * r[k + 1]].view(r[k], n[k], r[k + 1]).clone() for k in range(d)]
+    return [c.clone() for c in h.result()]
 
 
 def _dot_common(fn, A, B, stream):

@@ -204,11 +204,14 @@ struct HattArgs {
   int prec = hatt::kPrecFP64;   // arithmetic of the HPCRL-1 products (A2/A3)
   int variant = 1;              // 1 = HPCRL-1 (Eq. (3.6)), 2 = HPCRL-2 (Eq. (3.7))
   double ep = 0.0;              // HPCRL-2: keep sigma > ep * ||W^{(k)}||_2
+  bool fixed = false;           // output in the bound layout, zero past the kept ranks
+  std::vector<ll> outb;         // output rank bound reported by the plan
 };
 
 struct HattBufs {
   double *R, *W, *winv, *T1, *T2, *Ca, *Cb, *Mb, *U1, *Xpad, *partials, *delta2;
   ll *ranks;
+  ll *oranks;                   // fixed-rank output: the bound ranks on the device
   int *flags;
   unsigned int *ticket;
   std::vector<ll> Roff, Woff, Xoff;
@@ -257,6 +260,7 @@ HattBufs carve_hatt(Ws &ws, const HattArgs &a) {
   b.partials = ws.take<double>(1024);
   b.delta2 = ws.take<double>(1);
   b.ranks = ws.take<ll>(d + 1);
+  b.oranks = ws.take<ll>(d + 1);
   b.flags = ws.take<int>(8);
   b.ticket = ws.take<unsigned int>(1);
   if (a.variant == 2) {
@@ -522,10 +526,14 @@ void run_hatt(Runner &run, const HattArgs &a, const HattBufs &b) {
   for (int k = d - 1; k >= 1; --k)
     run.trunc(Xk(k), (int)l[k], (int)n[k], (int)l[k + 1], Xk(k - 1), (int)l[k - 1], (int)n[k - 1],
               a.cap, b.delta2, b.ranks, k, a.tol > 0.0);
+  // compact to the kept ranks, or (fixed ranks) to the bound layout, where the
+  // rows and columns past the kept ranks are already zero
+  if (run.live() && a.fixed)
+    run.check(hatt::set_ranks(b.oranks, a.outb.data(), d + 1, run.st));
   if (run.live())
     for (int k = 0; k < d; ++k)
-      run.check(hatt::compact_core(Xk(k), a.Xout[k], (int)l[k], (int)n[k], (int)l[k + 1], b.ranks,
-                                   k, run.st));
+      run.check(hatt::compact_core(Xk(k), a.Xout[k], (int)l[k], (int)n[k], (int)l[k + 1],
+                                   a.fixed ? b.oranks : b.ranks, k, run.st));
 }
 
 // Planning + argument checks shared by plan and execute.
@@ -544,8 +552,10 @@ int prepare_hatt(const tt_t *Y, const tt_t *Z, const tt_opts *o, bool need_cores
   if (o->precision < TT_FP64 || o->precision > TT_FP64_TC) return TT_ERR_ARG;
   if (o->variant != 1 && o->variant != 2) return TT_ERR_ARG;
   if (o->variant == 2 && (!(o->ep >= 0.0) || !(o->ep < 1.0))) return TT_ERR_ARG;
+  if (o->fixed_ranks != 0 && o->fixed_ranks != 1) return TT_ERR_ARG;
   a.variant = o->variant;
   a.ep = o->ep;
+  a.fixed = o->fixed_ranks == 1;
   a.prec = o->precision == TT_FP64_TC ? hatt::kPrecFP64 : o->precision;
   const int d = Y->d;
   a.d = d;
@@ -574,6 +584,9 @@ int prepare_hatt(const tt_t *Y, const tt_t *Z, const tt_opts *o, bool need_cores
   bool below = false;
   for (int k = 1; k < d; ++k) below = below || (o->max_rank > 0 && a.ell[k] > o->max_rank);
   a.trunc = d > 1 && (o->tol > 0.0 || below);
+  a.outb = a.ell;
+  if (a.fixed && a.trunc && a.cap > 0)
+    for (int k = 0; k <= d; ++k) a.outb[k] = std::min<ll>(a.ell[k], a.cap);
   return TT_OK;
 }
 
@@ -587,11 +600,13 @@ struct RoundArgs {
   double *const *Bout;
   int cap;
   double tol;
+  bool fixed = false;     // output in the bound layout outb, zero past the kept ranks
+  std::vector<ll> outb;   // output rank bound reported by the plan
 };
 
 struct RoundBufs {
   double *Xpad, *Ca, *Cb, *Mb, *partials, *delta2;
-  ll *ranks;
+  ll *ranks, *oranks;
   int *flags;
   unsigned int *ticket;
   std::vector<ll> Xoff;
@@ -614,6 +629,7 @@ RoundBufs carve_round(Ws &ws, const RoundArgs &a) {
   u.partials = ws.take<double>(1024);
   u.delta2 = ws.take<double>(1);
   u.ranks = ws.take<ll>(d + 1);
+  u.oranks = ws.take<ll>(d + 1);
   u.flags = ws.take<int>(8);
   u.ticket = ws.take<unsigned int>(1);
   return u;
@@ -668,16 +684,20 @@ void run_round(Runner &run, const RoundArgs &a, const RoundBufs &u) {
   for (int k = d - 1; k >= 1; --k)
     run.trunc(Xk(k), (int)bnd[k], (int)n[k], (int)bnd[k + 1], Xk(k - 1), (int)bnd[k - 1],
               (int)n[k - 1], a.cap, u.delta2, u.ranks, k, a.tol > 0.0);
+  if (run.live() && a.fixed)
+    run.check(hatt::set_ranks(u.oranks, a.outb.data(), d + 1, run.st));
   if (run.live())
     for (int k = 0; k < d; ++k)
       run.check(hatt::compact_core(Xk(k), a.Bout[k], (int)bnd[k], (int)n[k], (int)bnd[k + 1],
-                                   u.ranks, k, run.st));
+                                   a.fixed ? u.oranks : u.ranks, k, run.st));
 }
 
-int prepare_round(const tt_t *A, ll max_rank, double tol, bool need_cores, RoundArgs &a) {
+int prepare_round(const tt_t *A, ll max_rank, double tol, int fixed, bool need_cores,
+                  RoundArgs &a) {
   int st = check_tt(A, need_cores);
   if (st != TT_OK) return st;
   if (max_rank < 0 || !(tol >= 0.0) || !std::isfinite(tol)) return TT_ERR_ARG;
+  if (fixed != 0 && fixed != 1) return TT_ERR_ARG;
   const int d = A->d;
   a.d = d;
   a.n = A->n;
@@ -690,6 +710,10 @@ int prepare_round(const tt_t *A, ll max_rank, double tol, bool need_cores, Round
     if (a.b[k] * A->n[k] > kIntMax) return TT_ERR_RANK;
   a.cap = (int)std::min<ll>(max_rank, hatt::kMaxSmall);
   a.tol = tol;
+  a.fixed = fixed == 1;
+  a.outb = a.b;
+  if (a.fixed && a.cap > 0)
+    for (int k = 0; k <= d; ++k) a.outb[k] = std::min<ll>(a.b[k], a.cap);
   return TT_OK;
 }
 
@@ -876,7 +900,7 @@ int tt_hadamard_recompress_plan(const tt_t *Y, const tt_t *Z, const tt_opts *opt
   HattArgs a;
   int st = prepare_hatt(Y, Z, opts, false, a);
   if (st != TT_OK) return st;
-  for (int k = 0; k <= a.d; ++k) out_rank_bound[k] = a.ell[k];
+  for (int k = 0; k <= a.d; ++k) out_rank_bound[k] = a.outb[k];
   a.Y = nullptr;
   a.Z = nullptr;
   a.Xout = nullptr;
@@ -900,7 +924,7 @@ int tt_hadamard_recompress(const tt_t *Y, const tt_t *Z, const tt_opts *opts, tt
   if (!workspace || !aligned(workspace)) return TT_ERR_WORKSPACE;
   // outputs must not overlap inputs
   for (int k = 0; k < a.d; ++k) {
-    const size_t xb = (size_t)a.ell[k] * a.n[k] * a.ell[k + 1] * sizeof(double);
+    const size_t xb = (size_t)a.outb[k] * a.n[k] * a.outb[k + 1] * sizeof(double);
     for (int j = 0; j < a.d; ++j) {
       const size_t yb = (size_t)Y->r[j] * Y->n[j] * Y->r[j + 1] * sizeof(double);
       const size_t zb = (size_t)Z->r[j] * Z->n[j] * Z->r[j + 1] * sizeof(double);
@@ -927,12 +951,12 @@ int tt_hadamard_recompress(const tt_t *Y, const tt_t *Z, const tt_opts *opts, tt
                },
                [&](Runner &run, const HattBufs &b) { run_hatt(run, a, b); });
   if (st != TT_OK) return st;
-  if (a.trunc) {
+  if (a.trunc && !a.fixed) {
     cudaError_t e = cudaMemcpyAsync(X->r, bufs_for_ranks.ranks, (a.d + 1) * sizeof(int64_t),
                                     cudaMemcpyDeviceToHost, strm);
     if (e != cudaSuccess) return from_cuda(e);
   } else {
-    for (int k = 0; k <= a.d; ++k) X->r[k] = a.ell[k];
+    for (int k = 0; k <= a.d; ++k) X->r[k] = a.outb[k];
   }
   return TT_OK;
 }
@@ -1054,13 +1078,13 @@ int tt_hadamard_recompress_batch(int32_t count, const tt_t *Y, const tt_t *Z,
   return first_error;
 }
 
-int tt_round_plan(const tt_t *A, int64_t max_rank, double tol, int64_t *out_rank_bound,
-                  size_t *workspace_bytes) {
+int tt_round_ex_plan(const tt_t *A, int64_t max_rank, double tol, int32_t fixed_ranks,
+                     int64_t *out_rank_bound, size_t *workspace_bytes) {
   if (!out_rank_bound || !workspace_bytes) return TT_ERR_ARG;
   RoundArgs a;
-  int st = prepare_round(A, max_rank, tol, false, a);
+  int st = prepare_round(A, max_rank, tol, fixed_ranks, false, a);
   if (st != TT_OK) return st;
-  for (int k = 0; k <= a.d; ++k) out_rank_bound[k] = a.b[k];
+  for (int k = 0; k <= a.d; ++k) out_rank_bound[k] = a.outb[k];
   a.A = nullptr;
   a.Bout = nullptr;
   *workspace_bytes = measure([&](Ws &ws) { return carve_round(ws, a); },
@@ -1068,10 +1092,15 @@ int tt_round_plan(const tt_t *A, int64_t max_rank, double tol, int64_t *out_rank
   return TT_OK;
 }
 
-int tt_round(const tt_t *A, int64_t max_rank, double tol, tt_t *B, void *workspace,
-             size_t workspace_bytes, void *stream) {
+int tt_round_plan(const tt_t *A, int64_t max_rank, double tol, int64_t *out_rank_bound,
+                  size_t *workspace_bytes) {
+  return tt_round_ex_plan(A, max_rank, tol, 0, out_rank_bound, workspace_bytes);
+}
+
+int tt_round_ex(const tt_t *A, int64_t max_rank, double tol, int32_t fixed_ranks, tt_t *B,
+                void *workspace, size_t workspace_bytes, void *stream) {
   RoundArgs a;
-  int st = prepare_round(A, max_rank, tol, true, a);
+  int st = prepare_round(A, max_rank, tol, fixed_ranks, true, a);
   if (st != TT_OK) return st;
   if (!B || !B->cores || !B->r || !B->n) return TT_ERR_ARG;
   if (B->d != A->d) return TT_ERR_SHAPE;
@@ -1081,7 +1110,7 @@ int tt_round(const tt_t *A, int64_t max_rank, double tol, tt_t *B, void *workspa
   }
   if (!workspace || !aligned(workspace)) return TT_ERR_WORKSPACE;
   for (int k = 0; k < a.d; ++k) {
-    const size_t bb = (size_t)a.b[k] * a.n[k] * a.b[k + 1] * sizeof(double);
+    const size_t bb = (size_t)a.outb[k] * a.n[k] * a.outb[k + 1] * sizeof(double);
     for (int j = 0; j < a.d; ++j) {
       const size_t ab = (size_t)A->r[j] * A->n[j] * A->r[j + 1] * sizeof(double);
       if (overlap(B->cores[k], bb, A->cores[j], ab)) return TT_ERR_SHAPE;
@@ -1099,9 +1128,18 @@ int tt_round(const tt_t *A, int64_t max_rank, double tol, tt_t *B, void *workspa
                },
                [&](Runner &run, const RoundBufs &u) { run_round(run, a, u); });
   if (st != TT_OK) return st;
+  if (a.fixed) {
+    for (int k = 0; k <= a.d; ++k) B->r[k] = a.outb[k];
+    return TT_OK;
+  }
   cudaError_t e = cudaMemcpyAsync(B->r, keep.ranks, (a.d + 1) * sizeof(int64_t),
                                   cudaMemcpyDeviceToHost, strm);
   return from_cuda(e);
+}
+
+int tt_round(const tt_t *A, int64_t max_rank, double tol, tt_t *B, void *workspace,
+             size_t workspace_bytes, void *stream) {
+  return tt_round_ex(A, max_rank, tol, 0, B, workspace, workspace_bytes, stream);
 }
 
 int tt_dot_plan(const tt_t *A, const tt_t *B, size_t *workspace_bytes) {

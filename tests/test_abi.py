@@ -268,3 +268,28 @@ def test_hatt2_plan_and_batch_rejection(lib):
     o = (B.OptsStruct * 1)(B.make_opts(sketch_rank=9, variant=2, ep=1e-3))
     bound = ctypes.c_size_t()
     assert B.load().tt_hadamard_recompress_batch_plan(1, Ys, Zs, o, 1, ctypes.byref(bound)) == 3
+
+
+def test_fixed_ranks_plan_bounds(lib):
+    """fixed_ranks = 1 reports the bound the output keeps: min(l_k, max_rank)
+    for a truncating HaTT call, min(b_k, max_rank) for tt_round_ex; 0 keeps the
+    unpadded bounds; other values are rejected."""
+    n = [6] * 5
+    Yr, Zr = [1, 4, 5, 5, 3, 1], [1, 3, 4, 2, 3, 1]
+    st, b0, _ = _plan(Yr, Zr, n, max_rank=5, sketch_rank=9)
+    st1, b1, _ = _plan(Yr, Zr, n, max_rank=5, sketch_rank=9, fixed_ranks=1)
+    assert st == st1 == 0
+    assert b1 == [min(v, 5) for v in b0] and max(b0) > 5
+    st2, _, _ = _plan(Yr, Zr, n, max_rank=5, sketch_rank=9, fixed_ranks=2)
+    assert st2 == 3
+    A = B.TT(n=[8] * 4, r=[1, 8, 30, 8, 1])
+    for fixed, cap in ((0, 6), (1, 6), (1, 0)):
+        bound = (ctypes.c_int64 * 5)()
+        ws = ctypes.c_size_t()
+        assert lib.tt_round_ex_plan(A.ref(), cap, 1e-8, fixed, bound, ctypes.byref(ws)) == 0
+        base = [1, 8, 30, 8, 1]
+        want = [min(v, cap) for v in base] if (fixed and cap) else base
+        want[0] = want[-1] = 1
+        assert list(bound) == want
+    bound = (ctypes.c_int64 * 5)()
+    assert lib.tt_round_ex_plan(A.ref(), 6, 1e-8, 3, bound, ctypes.byref(ws)) == 3

@@ -96,3 +96,76 @@ def test_full_configuration_energy_decays(B):
     assert all(b <= a * (1 + 1e-9) for a, b in zip(energies, energies[1:]))
     assert max(c.shape[2] for c in u) <= 24
     assert B.device_error() == 0
+
+
+def _pad_np(u, rank):
+    rk = [1] + [max(c.shape[2], rank) for c in u[:-1]] + [1]
+    out = []
+    for k, c in enumerate(u):
+        p = np.zeros((rk[k], c.shape[1], rk[k + 1]))
+        p[: c.shape[0], :, : c.shape[2]] = c
+        out.append(p)
+    return out
+
+
+def test_fixed_rank_graph_matches_oracle(B):
+    """d = 3, n = 8, every bond held at rank 8 (the largest these modes allow):
+    five steps (the capture's warm-up step and four graph replays) against five
+    oracle steps with the same sketch seeds, the oracle's result padded back
+    to rank 8 after every step so both sides sketch the same shapes."""
+    from paper_2410_04385_gb300 import allen_cahn as ac
+    d, n, eps, dt = 3, 8, 0.1, 1e-3
+    h = 2 * np.pi / n
+    u0 = _pad_np(oac.initial_condition(d, n, seed=3), 8)
+    st = ac.FixedRankStepper(to_gpu(u0), h, eps, dt, rank=8, tol=1e-12, hatt_tol=0.0,
+                             hatt_rank=8, seed=100)
+    st.capture()
+    for _ in range(4):
+        st.replay()
+    torch.cuda.synchronize()
+    assert [c.shape for c in st.u] == [c.shape for c in u0]
+    u = u0
+    for _ in range(5):
+        u, _ = oac.step(u, h, eps, dt, max_rank=8, tol=1e-12, hatt_tol=0.0, seed=100)
+        u = _pad_np(u, 8)
+    X = to_np(st.u)
+    assert ott.tt_diff_norm(X, u) <= 1e-10 * ott.tt_norm(u)
+
+
+def test_fixed_rank_graph_equals_eager_steps(B):
+    """The captured step replays exactly what the eager step does."""
+    from paper_2410_04385_gb300 import allen_cahn as ac
+    d, n, eps, dt = 4, 16, 0.1, 1e-3
+    h = 2 * np.pi / n
+    u0 = to_gpu(oac.initial_condition(d, n, seed=5))
+    a = ac.FixedRankStepper(u0, h, eps, dt, rank=12, tol=1e-8, hatt_tol=1e-10, hatt_rank=12,
+                            seed=7)
+    b = ac.FixedRankStepper(u0, h, eps, dt, rank=12, tol=1e-8, hatt_tol=1e-10, hatt_rank=12,
+                            seed=7)
+    for _ in range(4):
+        a.step()
+    b.capture()
+    for _ in range(3):
+        b.replay()
+    torch.cuda.synchronize()
+    for x, y in zip(a.u, b.u):
+        assert torch.allclose(x, y, rtol=0.0, atol=1e-13 * float(y.abs().max()))
+
+
+def test_fixed_rank_graph_full_configuration(B):
+    """d = 8, n = 64 held at rank 24: 20 graph-replayed steps, energy
+    non-increasing, no device wait ran out."""
+    from paper_2410_04385_gb300 import allen_cahn as ac
+    d, n, eps, dt = 8, 64, 0.1, 1e-3
+    h = 2 * np.pi / n
+    st = ac.FixedRankStepper(to_gpu(oac.initial_condition(d, n, seed=0)), h, eps, dt, rank=24,
+                             tol=1e-8, hatt_tol=1e-10, hatt_rank=24, seed=10)
+    st.capture()
+    energies = []
+    for _ in range(20):
+        st.replay()
+        torch.cuda.synchronize()
+        energies.append(st.energy())
+    assert all(np.isfinite(energies))
+    assert all(b <= a * (1 + 1e-9) for a, b in zip(energies, energies[1:]))
+    assert B.device_error() == 0
