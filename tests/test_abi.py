@@ -293,3 +293,18 @@ def test_fixed_ranks_plan_bounds(lib):
         assert list(bound) == want
     bound = (ctypes.c_int64 * 5)()
     assert lib.tt_round_ex_plan(A.ref(), 6, 1e-8, 3, bound, ctypes.byref(ws)) == 3
+
+
+def test_pad_ranks_keeps_the_tensor():
+    """Host-only: zero padding raises every inner rank and leaves the tensor
+    (the contraction of the cores) unchanged."""
+    import torch
+    from paper_2410_04385_gb300 import allen_cahn as ac
+    g = torch.Generator().manual_seed(0)
+    u = [torch.randn(1, 5, 2, generator=g, dtype=torch.float64),
+         torch.randn(2, 5, 3, generator=g, dtype=torch.float64),
+         torch.randn(3, 5, 1, generator=g, dtype=torch.float64)]
+    p = ac.pad_ranks(u, 4)
+    assert [tuple(c.shape) for c in p] == [(1, 5, 4), (4, 5, 4), (4, 5, 1)]
+    full = lambda cs: torch.einsum("aib,bjc,ckd->ijk", *cs)
+    assert torch.allclose(full(u), full(p), rtol=1e-13, atol=1e-13)
