@@ -401,7 +401,7 @@ eig_tridiag32_kernel(const double *G, int c, double *U, const int *skip) {
 // for this step). With orth_only set, every pair is treated as clustered: E = (I - U^T U)/2,
 // one Newton-Schulz orthonormalization step (S and G are not read). A
 // positive floor_norm replaces ||G||_F in the floor (the deflated matrix of
-// the second level has an exactly diagonal part that must not raise it).
+// the cluster levels has an exactly diagonal part that must not raise it).
 //
 // The quotient of a separated pair is formed in FP32 after scaling numerator
 // and denominator by 1/||G||_F (the denominator exceeds 64 c u ||G||, so it
