@@ -323,3 +323,27 @@ def test_hatt2_truncation_keeps_range_until_ep_is_large():
             assert err <= 1e-13
         else:
             assert err > 1e-2 and max(kept) == 1
+
+
+def test_hatt2_step_is_the_kronecker_definition_on_the_truncated_sketch():
+    """Against the defining formula with explicit partial Kronecker cores
+    A_k(i) = Y_k(i) (x) Z_k(i) (what HaTT never forms): every HPCRL-2 step is
+    W^{(k-1)} = sum_i A_k(i) W~ R_k(i)^T / ||.||_F with W~ the rank-R_k
+    truncated SVD of W^{(k)}, the R_k the recursion reports. ep = 0.3 cuts in
+    the middle of the spectra, so the truncation is active at every step."""
+    n = [4, 5, 3, 4, 5]
+    Y = wl.gaussian_tt(n, [1, 3, 4, 3, 2, 1], 81)
+    Z = wl.gaussian_tt(n, [1, 2, 3, 4, 2, 1], 82)
+    ell = hatt.plan_ranks(n, tt.ranks(Y), tt.ranks(Z), 8)
+    R = philox.sketch_tt(6, n, ell)
+    W, kept = hatt.hpcrl2(Y, Z, R, 0.3)
+    cut = 0
+    for k in range(len(n) - 1, 0, -1):
+        u, sv, vt = np.linalg.svd(W[k + 1], full_matrices=False)
+        Rk = kept[k + 1]
+        cut += Rk < len(sv)
+        Wt = (u[:, :Rk] * sv[:Rk]) @ vt[:Rk]
+        E = sum(np.kron(Y[k][:, i, :], Z[k][:, i, :]) @ Wt @ R[k][:, i, :].T for i in range(n[k]))
+        E = E / np.linalg.norm(E)
+        assert np.allclose(W[k], E, rtol=0, atol=1e-13)
+    assert cut >= 2
