@@ -23,6 +23,10 @@ namespace {
 std::atomic<long long> g_launches{0};
 }
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+thread_local bool t_programmatic = true;
+void set_programmatic_launch(bool on) { t_programmatic = on; }
+bool programmatic_launch() { return t_programmatic; }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 // Kernel timer state (tt_kernel_timer_start / _stop). Guarded by a mutex;
@@ -790,10 +794,17 @@ struct Fp64TcScope {
   ~Fp64TcScope() { hatt::set_fp64_tensor_cores(false); }
 };
 
-// Keeps the truncation sweep from synchronizing while a batch issues its lanes.
-struct NoHostSyncScope {
-  NoHostSyncScope() { hatt::set_host_sync(false); }
-  ~NoHostSyncScope() { hatt::set_host_sync(true); }
+// While a batch issues its lanes: the truncation sweep does not synchronize,
+// and kernels are launched without programmatic serialization.
+struct BatchScope {
+  BatchScope() {
+    hatt::set_host_sync(false);
+    hatt::set_programmatic_launch(false);
+  }
+  ~BatchScope() {
+    hatt::set_host_sync(true);
+    hatt::set_programmatic_launch(true);
+  }
 };
 
 // Makes a tile-counter array current for the calling thread during one call.
@@ -1062,7 +1073,7 @@ int tt_hadamard_recompress_batch(int32_t count, const tt_t *Y, const tt_t *Z,
     p += lane_bytes[l];
   }
   int first_error = TT_OK;
-  NoHostSyncScope no_sync;
+  BatchScope batch_scope;
   for (int j = 0; j < count && first_error == TT_OK; ++j) {
     const int l = j % lanes;
     first_error = tt_hadamard_recompress(&Y[j], &Z[j], &opts[j], &X[j], base[l], lane_bytes[l],

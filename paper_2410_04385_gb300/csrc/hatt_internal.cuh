@@ -21,7 +21,11 @@ constexpr int kMaxSmall = 128;   // TT_MAX_SMALL_RANK
 // memory is visible, and launch_dependents then lets the following kernel be
 // scheduled while this one runs (its blocks wait at their own pdl_enter).
 // Since the wait comes before any load or store, every read-after-write and
-// write-after-read order of the stream is kept.
+// write-after-read order of the stream is kept. The batched entry point turns
+// it off for the calling thread: with many streams in flight, the blocks that
+// wait early hold SM slots that the other streams' kernels could use.
+void set_programmatic_launch(bool on);
+bool programmatic_launch();
 template <typename... P, typename... A>
 inline cudaError_t launch_k(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem,
                             cudaStream_t st, A &&...args) {
@@ -34,7 +38,7 @@ inline cudaError_t launch_k(void (*kernel)(P...), dim3 grid, dim3 block, size_t 
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = programmatic_launch() ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
 }
 
