@@ -308,3 +308,24 @@ def test_pad_ranks_keeps_the_tensor():
     assert [tuple(c.shape) for c in p] == [(1, 5, 4), (4, 5, 4), (4, 5, 1)]
     full = lambda cs: torch.einsum("aib,bjc,ckd->ijk", *cs)
     assert torch.allclose(full(u), full(p), rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("n,Yr,Zr", [
+    ([5], [1, 1], [1, 1]),                     # d = 1: one core, no recursion
+    ([4, 6], [1, 3, 1], [1, 2, 1]),            # d = 2: one HPCRL step on W^(2) = [1]
+    ([1, 7, 1, 3], [1, 1, 2, 2, 1], [1, 1, 3, 2, 1]),   # unit modes clamp the sketch to 1
+])
+@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("fixed", [0, 1])
+def test_plan_edge_shapes_every_variant(lib, n, Yr, Zr, variant, fixed):
+    """Host-only: planning (which walks the whole launch sequence without
+    launching) accepts orders 1 and 2 and unit mode sizes in every variant and
+    output mode, and reports bounds no larger than the mode products allow."""
+    st, bound, ws = _plan(Yr, Zr, n, max_rank=3, tol=1e-10, sketch_rank=4, variant=variant,
+                          ep=0.1, fixed_ranks=fixed)
+    assert st == 0 and ws > 0
+    d = len(n)
+    assert bound[0] == 1 and bound[d] == 1
+    for k in range(1, d):
+        left = int(np.prod(n[:k]))
+        assert 1 <= bound[k] <= left
