@@ -150,16 +150,22 @@ int tt_hadamard_recompress_plan(const tt_t *Y, const tt_t *Z, const tt_opts *opt
  *      truncation sweep of the left-orthogonal result.
  *   Y, Z       inputs (Y.d == Z.d, Y.n[k] == Z.n[k], r_0 = r_d = s_0 = s_d = 1)
  *   X          output: X->d and X->n must match; X->cores[k] must hold at least
- *              l_k*n_k*l_{k+1} doubles (the plan's bound). On return (stream
+ *              b_k*n_k*b_{k+1} doubles, b the plan's bound. On return (stream
  *              ordered) core k holds the r_k x n_k x r_{k+1} result densely in the
  *              prefix of its buffer, and X->r (host[d+1]) receives the ranks
  *              through a stream-ordered device-to-host copy: read X->r after the
  *              stream has been synchronized (pinned host memory keeps the call
- *              asynchronous; pageable memory makes the copy block).
+ *              asynchronous; pageable memory makes the copy block). With
+ *              opts->fixed_ranks = 1, r = b, set on the host (see tt_opts).
  *              Output buffers must not alias input cores (TT_ERR_SHAPE).
  *   workspace  device, at least the plan's workspace_bytes, 256-byte aligned.
  * Without truncation the result is left-orthogonal (cores 0..d-2 have
- * orthonormal vertical unfoldings). */
+ * orthonormal vertical unfoldings).
+ * Synchronization: with tol > 0 and a stream that is not being captured, the
+ * truncation sweep reads one device flag per cluster level (a short
+ * synchronization of `stream`) to stop launching levels that would be skipped;
+ * a captured stream gets every level instead. Variant 2 synchronizes once per
+ * core (see tt_opts). */
 int tt_hadamard_recompress(const tt_t *Y, const tt_t *Z, const tt_opts *opts, tt_t *X,
                            void *workspace, size_t workspace_bytes, void *stream);
 
@@ -192,7 +198,8 @@ int tt_hadamard_recompress_batch(int32_t count, const tt_t *Y, const tt_t *Z,
 int tt_round_plan(const tt_t *A, int64_t max_rank, double tol, int64_t *out_rank_bound,
                   size_t *workspace_bytes);
 
-/* TT rounding of A (Algorithm 1, Oseledets): orthogonalization sweep with QR
+/* TT rounding of A (Algorithm 1, Oseledets), synchronizing like
+ * tt_hadamard_recompress's truncation when tol > 0: orthogonalization sweep with QR
  * of each vertical unfolding (left to right), then a right-to-left truncation
  * sweep with the same rule as tt_hadamard_recompress (max_rank cap, tol with
  * delta = tol * ||A|| / sqrt(d-1)). B is written like X above; all ranks of A
