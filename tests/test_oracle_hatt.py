@@ -347,3 +347,33 @@ def test_hatt2_step_is_the_kronecker_definition_on_the_truncated_sketch():
         E = E / np.linalg.norm(E)
         assert np.allclose(W[k], E, rtol=0, atol=1e-13)
     assert cut >= 2
+
+
+def test_hatt_accuracy_below_the_numerical_rank_within_the_randomized_bound():
+    """At a target rank r below the numerical rank the paper states no bound.
+    A bound that holds in expectation follows from two published results: a
+    rank-(r+p) Gaussian range finder leaves at most sqrt(1 + r/(p-1)) times
+    the optimal tail at a bond (Halko, Martinsson, Tropp 2011, Thm 10.5), and
+    a TT built by successive projections errs by at most the root sum of
+    squares of its bond errors (Oseledets 2011, Thm 2.2). So
+    ||A - X|| <= sqrt(sum_k (1 + r/(p-1)) tail_k(r)^2) in expectation, tail_k
+    the optimal rank-r error of the k-th unfolding. Checked with a factor 2
+    over five seeds on products of smooth TTs with decaying spectra; a
+    transposed operand or a wrong index gives errors of order one."""
+    d, n, p = 6, 8, 10
+    for trial in range(2):
+        Y = wl.smooth_tt(d, n, 6, seed=10 + trial)
+        Z = wl.smooth_tt(d, n, 6, seed=20 + trial)
+        A = tt.tt_full(Y) * tt.tt_full(Z)
+        na = np.linalg.norm(A)
+        for r in (3, 8):
+            tails = [np.sqrt(np.sum(np.linalg.svd(A.reshape(n ** k, -1), compute_uv=False)[r:] ** 2))
+                     for k in range(1, d)]
+            bound = np.sqrt(np.sum((1.0 + r / (p - 1.0)) * np.square(tails)))
+            lower = max(tails)
+            for seed in range(5):
+                X = hatt.hadamard_recompress(Y, Z, max_rank=r, oversample=p, seed=seed)
+                err = np.linalg.norm(tt.tt_full(X) - A)
+                assert lower * (1 - 1e-12) <= err <= 2.0 * bound
+                assert max(tt.ranks(X)) <= r
+            assert lower > 1e-3 * na          # the target is really below the numerical rank
