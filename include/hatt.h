@@ -225,11 +225,11 @@ int tt_dot_plan(const tt_t *A, const tt_t *B, size_t *workspace_bytes);
 int tt_dot(const tt_t *A, const tt_t *B, double *out, void *workspace, size_t workspace_bytes,
            void *stream);
 
-/* <A, B> like tt_dot, for callers that cannot allocate device memory: code
- * that runs while a stream is being captured into a CUDA graph in global
- * capture mode (allocation calls are illegal there), latency-critical loops
- * that forbid allocation, or plugins whose host framework owns all device
- * memory through its own allocator. No counterpart in the paper.
+/* <A, B> like tt_dot, for callers that cannot allocate device memory:
+ * latency-critical loops whose rules forbid any allocation once running, and
+ * plugins whose host framework owns all device memory through its own
+ * allocator and gives them no way to reserve a workspace. No counterpart in
+ * the paper.
  *   A, B, out  as tt_dot (out: device scalar)
  * Allocates nothing and calls no allocating routine: its scratch is one fixed
  * 8 MiB array in the device memory of every GPU that loads this library
@@ -239,7 +239,10 @@ int tt_dot(const tt_t *A, const tt_t *B, double *out, void *workspace, size_t wo
  * that overlap on the GPU (other streams, other host threads) race and must be
  * ordered by the caller. Nothing in the array must start at zero; every buffer
  * is written before it is read. Returns TT_ERR_WORKSPACE, before launching
- * anything, when the workspace tt_dot_plan reports for A, B exceeds 8 MiB. */
+ * anything, when the workspace tt_dot_plan reports for A, B exceeds 8 MiB.
+ * The cached address belongs to the device's context at the first call: after
+ * a cudaDeviceReset of that device the process must not call tt_dot_noalloc
+ * on it again. */
 int tt_dot_noalloc(const tt_t *A, const tt_t *B, double *out, void *stream);
 
 /* Frobenius norm ||A||_F = sqrt(<A, A>); out: device scalar. Workspace as tt_dot(A, A). */

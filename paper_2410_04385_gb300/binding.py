@@ -413,11 +413,16 @@ def tt_dot_noalloc(A, B, out: Optional[torch.Tensor] = None, stream=None) -> tor
     the call allocates nothing on the Python side either."""
     Ad = TT(A)
     Bd = TT(B)
+    dev = A[0].device
     if out is None:
-        out = torch.empty(1, dtype=torch.float64, device=A[0].device)
-    _check("tt_dot_noalloc", load().tt_dot_noalloc(Ad.ref(), Bd.ref(),
-                                                   ctypes.c_void_p(out.data_ptr()),
-                                                   _stream_ptr(stream)))
+        out = torch.empty(1, dtype=torch.float64, device=dev)
+    elif out.device != dev or out.dtype != torch.float64 or out.numel() < 1:
+        raise ValueError("out must be a float64 tensor on the cores' device")
+    # the library takes its scratch array and stream from the current device
+    with torch.cuda.device(dev):
+        _check("tt_dot_noalloc", load().tt_dot_noalloc(Ad.ref(), Bd.ref(),
+                                                       ctypes.c_void_p(out.data_ptr()),
+                                                       _stream_ptr(stream)))
     return out
 
 

@@ -1,5 +1,5 @@
 """GPU test of tt_dot_noalloc, the inner product for callers that cannot
-allocate device memory (for example code running inside a CUDA-graph capture,
+allocate device memory (for example a real-time loop that forbids allocation,
 or a plugin whose host framework owns the GPU's memory). Its scratch is a fixed
 per-GPU array inside the library, so the test checks that two calls in a row
 on the same array give the same result as tt_dot with a caller-owned
@@ -59,6 +59,11 @@ def test_noalloc_dot_matches_tt_dot_on_two_calls(B, case):
         out.fill_(float("nan"))
         assert call_noalloc(B, A, C, out) == B.TT_OK
         assert abs(out.item() - ref) <= REL_TOL * scale
+    # the Python wrapper, into a preallocated result
+    out.fill_(float("nan"))
+    assert B.tt_dot_noalloc(A, C, out=out) is out
+    torch.cuda.synchronize()
+    assert abs(out.item() - ref) <= REL_TOL * scale
 
 
 def test_noalloc_dot_refuses_problems_beyond_its_scratch(B):
