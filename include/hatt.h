@@ -288,6 +288,18 @@ int64_t tt_launch_count(void);
  * launches through this library. */
 int tt_kernel_timer_start(int32_t capacity);
 int tt_kernel_timer_stop(double *ms, double *flops, int32_t capacity, int64_t *count);
+/* As tt_kernel_timer_stop, and role[i] (host, `capacity` int32, may be NULL)
+ * tells what launch i computed: TT_ROLE_METHOD for the contractions HaTT
+ * itself is made of (the HPCRL products of Algorithm 3 / eq. (3.6) or (3.7),
+ * the core sketch C_k W, the projection Q^T C_k and the core update of
+ * eq. (3.10)), which always do their work; TT_ROLE_AUX for every other FP64
+ * GEMM launch (Gram matrices and triangular steps of the QR, the truncation
+ * sweep and its eigen refinement, inner products, TT rounding), some of which
+ * a device flag turns into no-ops once a loop has converged. */
+#define TT_ROLE_AUX 0
+#define TT_ROLE_METHOD 1
+int tt_kernel_timer_stop_ex(double *ms, double *flops, int32_t *role, int32_t capacity,
+                            int64_t *count);
 
 /* Periodic central-difference Laplacian of a TT (Section 5, Example 4):
  * L = sum_k I x .. x D_k x .. x I applied to A, D the n_k x n_k second

@@ -60,7 +60,7 @@ EXPORTS = ("tt_hadamard_recompress_plan", "tt_hadamard_recompress", "tt_round_pl
            "tt_round_ex_plan", "tt_round_ex",
            "tt_dot_plan", "tt_dot", "tt_dot_noalloc", "tt_norm", "tt_sketch_tt",
            "tt_philox4x32_10", "tt_launch_count", "tt_kernel_timer_start",
-           "tt_kernel_timer_stop", "tt_device_error", "tt_hadamard_recompress_batch_plan",
+           "tt_kernel_timer_stop", "tt_kernel_timer_stop_ex", "tt_device_error", "tt_hadamard_recompress_batch_plan",
            "tt_hadamard_recompress_batch", "tt_scale", "tt_laplacian", "tt_lincomb",
            "tt_status_string")
 
@@ -113,6 +113,8 @@ def load(path: Optional[str] = None):
                                                  ctypes.c_size_t, vp]
     lib.tt_kernel_timer_stop.argtypes = [P(ctypes.c_double), P(ctypes.c_double), ctypes.c_int32,
                                          P(ctypes.c_int64)]
+    lib.tt_kernel_timer_stop_ex.argtypes = [P(ctypes.c_double), P(ctypes.c_double),
+                                            P(ctypes.c_int32), ctypes.c_int32, P(ctypes.c_int64)]
     for name in EXPORTS:
         getattr(lib, name)
     if path is None:
@@ -180,15 +182,24 @@ def kernel_timer_start(capacity: int) -> None:
     _check("tt_kernel_timer_start", load().tt_kernel_timer_start(int(capacity)))
 
 
-def kernel_timer_stop(capacity: int):
+TT_ROLE_AUX = 0
+TT_ROLE_METHOD = 1
+
+
+def kernel_timer_stop(capacity: int, with_roles: bool = False):
     """Stop the timer; returns (ms, flops, recorded): per-launch durations in
     milliseconds and algorithmic flop counts of the first min(recorded,
-    capacity) timed launches."""
+    capacity) timed launches; with_roles adds the list of launch roles
+    (TT_ROLE_METHOD / TT_ROLE_AUX) as a fourth item."""
     ms = (ctypes.c_double * max(capacity, 1))()
     fl = (ctypes.c_double * max(capacity, 1))()
+    ro = (ctypes.c_int32 * max(capacity, 1))()
     cnt = ctypes.c_int64(0)
-    _check("tt_kernel_timer_stop", load().tt_kernel_timer_stop(ms, fl, int(capacity), ctypes.byref(cnt)))
+    _check("tt_kernel_timer_stop_ex",
+           load().tt_kernel_timer_stop_ex(ms, fl, ro, int(capacity), ctypes.byref(cnt)))
     k = min(int(cnt.value), int(capacity))
+    if with_roles:
+        return list(ms[:k]), list(fl[:k]), int(cnt.value), list(ro[:k])
     return list(ms[:k]), list(fl[:k]), int(cnt.value)
 
 

@@ -34,6 +34,19 @@ def hatt1_flops(n, r, s, ell):
     return hp, sw
 
 
+def hatt1_contraction_flops(n, r, s, ell):
+    """The part of hatt1_flops that the HaTT contractions themselves carry
+    (HPCRL, C W, M = Q^T C, core update), i.e. everything but the QR term:
+    the work of the launches the library tags as method products."""
+    hp, sw = hatt1_flops(n, r, s, ell)
+    d = len(n)
+    for k in range(d - 1):
+        rows = ell[k] * n[k]
+        lp = ell[k + 1]
+        sw -= 4.0 * rows * lp * lp - 4.0 * lp ** 3 / 3.0
+    return hp + sw
+
+
 def truncation_flops(n, ell):
     """Leading-order flops of the right-to-left truncation sweep as implemented:
     per core k >= 1 the Gram B B^T and the projection U^T B (2 l^2 N each,

@@ -38,6 +38,7 @@ struct KernelTimer {
   std::atomic<bool> active{false};
   std::vector<cudaEvent_t> ev;     // 2 per slot
   std::vector<double> flops;
+  std::vector<int> role;
   int used = 0;
 };
 KernelTimer g_timer;
@@ -61,7 +62,7 @@ int timer_begin(cudaStream_t st) {
   return slot;
 }
 
-void timer_end(int slot, cudaStream_t st, double flops) {
+void timer_end(int slot, cudaStream_t st, double flops, int role) {
   if (slot < 0) return;
   std::lock_guard<std::mutex> lk(g_timer.mu);
   if (slot >= (int)g_timer.flops.size()) return;
@@ -72,6 +73,7 @@ void timer_end(int slot, cudaStream_t st, double flops) {
     return;
   }
   g_timer.flops[slot] = flops;
+  g_timer.role[slot] = role;
 }
 
 namespace {
@@ -80,6 +82,7 @@ void timer_release() {   // caller holds g_timer.mu
   for (cudaEvent_t e : g_timer.ev) cudaEventDestroy(e);
   g_timer.ev.clear();
   g_timer.flops.clear();
+  g_timer.role.clear();
   g_timer.used = 0;
 }
 }  // namespace
@@ -336,6 +339,7 @@ void hpcrl2_step(Runner &run, const HattArgs &a, const HattBufs &b, int k, doubl
   auto contract = [&](int R) {
     {   // Rv = R_k V_R
       Gemm g;
+      g.role = hatt::kRoleMethod;
       g.M = l0 * nk; g.N = R; g.K = c;
       g.A = Rk; g.sAm = c; g.sAk = 1;
       g.B = b.VR; g.sBk = R; g.sBn = 1;
@@ -345,6 +349,7 @@ void hpcrl2_step(Runner &run, const HattArgs &a, const HattBufs &b, int k, doubl
     }
     {   // P2, batched over (i, a')
       Gemm g;
+      g.role = hatt::kRoleMethod;
       g.M = s0; g.N = R; g.K = s1;
       g.batch = nk * r1; g.bdiv = r1;
       g.A = a.Z ? a.Z[k] : nullptr; g.sA1 = s1; g.sA2 = 0; g.sAm = (ll)nk * s1; g.sAk = 1;
@@ -355,6 +360,7 @@ void hpcrl2_step(Runner &run, const HattArgs &a, const HattBufs &b, int k, doubl
     }
     {   // P3, batched over (i, b)
       Gemm g;
+      g.role = hatt::kRoleMethod;
       g.M = r0; g.N = R; g.K = r1;
       g.batch = nk * s0; g.bdiv = s0;
       g.A = a.Y ? a.Y[k] : nullptr; g.sA1 = r1; g.sA2 = 0; g.sAm = (ll)nk * r1; g.sAk = 1;
@@ -365,6 +371,7 @@ void hpcrl2_step(Runner &run, const HattArgs &a, const HattBufs &b, int k, doubl
     }
     {   // W^{(k)} = W_L W_R^T
       Gemm g;
+      g.role = hatt::kRoleMethod;
       g.M = r0 * s0; g.N = l0; g.K = nk * R;
       g.A = b.P3; g.sAm = (ll)nk * R; g.sAk = 1;
       g.B = b.Rv; g.sBk = 1; g.sBn = (ll)nk * R;
@@ -438,6 +445,7 @@ void run_hatt(Runner &run, const HattArgs &a, const HattBufs &b) {
     }
     {   // S1: T1[i][x][lam] = sum_g W[x][g] R_k[lam][i][g] / ||W||
       Gemm g;
+      g.role = hatt::kRoleMethod;
       g.M = r1 * s1; g.N = l0; g.K = l1;
       g.batch = nk; g.bdiv = 1;
       g.A = Wk(k + 1); g.sA1 = 0; g.sAm = l1; g.sAk = 1;
@@ -449,6 +457,7 @@ void run_hatt(Runner &run, const HattArgs &a, const HattBufs &b) {
     }
     {   // S2: T2[i][a'][b][lam] = sum_b' Z_k[b][i][b'] T1[i][a'][b'][lam]
       Gemm g;
+      g.role = hatt::kRoleMethod;
       g.M = s0; g.N = l0; g.K = s1;
       g.batch = nk * r1; g.bdiv = r1;
       g.A = a.Y ? a.Z[k] : nullptr; g.sA1 = s1; g.sA2 = 0; g.sAm = (ll)nk * s1; g.sAk = 1;
@@ -459,6 +468,7 @@ void run_hatt(Runner &run, const HattArgs &a, const HattBufs &b) {
     }
     {   // S3: W[a][b][lam] = sum_{i,a'} Y_k[a][i][a'] T2[i][a'][b][lam]
       Gemm g;
+      g.role = hatt::kRoleMethod;
       g.M = r0; g.N = s0 * l0; g.K = nk * r1;
       g.A = a.Y ? a.Y[k] : nullptr; g.sAm = (ll)nk * r1; g.sAk = 1;
       g.B = b.T2; g.sBk = (ll)s0 * l0; g.sBn = 1;
@@ -483,6 +493,7 @@ void run_hatt(Runner &run, const HattArgs &a, const HattBufs &b) {
     double *Q = Xk(k);
     {   // A5: S = C_k W^{(k+1)} / ||W||
       Gemm g;
+      g.role = hatt::kRoleMethod;
       g.M = (int)m; g.N = L; g.K = rs;
       g.A = C; g.sAm = rs; g.sAk = 1;
       g.B = Wk(k + 1); g.sBk = L; g.sBn = 1;
@@ -493,6 +504,7 @@ void run_hatt(Runner &run, const HattArgs &a, const HattBufs &b) {
     run.qr(Q, (int)m, L, L, b.flags);                // A6
     {   // A7: M = Q^T C_k
       Gemm g;
+      g.role = hatt::kRoleMethod;
       g.M = L; g.N = rs; g.K = (int)m;
       g.A = Q; g.sAm = 1; g.sAk = L;
       g.B = C; g.sBk = rs; g.sBn = 1;
@@ -501,6 +513,7 @@ void run_hatt(Runner &run, const HattArgs &a, const HattBufs &b) {
     }
     {   // A8 stage 1: U1[(g,a)][(i,b')] = sum_b M[g][a][b] Z_{k+1}[b][i][b']
       Gemm g;
+      g.role = hatt::kRoleMethod;
       g.M = L * r1; g.N = n1 * s2; g.K = s1;
       g.A = b.Mb; g.sAm = s1; g.sAk = 1;
       g.B = a.Z ? a.Z[k + 1] : nullptr; g.sBk = (ll)n1 * s2; g.sBn = 1;
@@ -510,6 +523,7 @@ void run_hatt(Runner &run, const HattArgs &a, const HattBufs &b) {
     double *dst = (k + 2 == d) ? Xk(d - 1) : Cn;
     {   // A8 stage 2: C_{k+1}[g][i][a'][b'] = sum_a Y_{k+1}[a][i][a'] U1[g][a][i][b']
       Gemm g;
+      g.role = hatt::kRoleMethod;
       g.M = r2; g.N = s2; g.K = r1;
       g.batch = L * n1; g.bdiv = n1;
       g.A = a.Y ? a.Y[k + 1] : nullptr; g.sA1 = 0; g.sA2 = r2; g.sAm = 1; g.sAk = (ll)n1 * r2;
@@ -1304,12 +1318,18 @@ int tt_kernel_timer_start(int32_t capacity) {
     }
   }
   hatt::g_timer.flops.assign((size_t)capacity, 0.0);
+  hatt::g_timer.role.assign((size_t)capacity, hatt::kRoleAux);
   hatt::g_timer.used = 0;
   hatt::g_timer.active.store(true);
   return TT_OK;
 }
 
 int tt_kernel_timer_stop(double *ms, double *flops, int32_t capacity, int64_t *count) {
+  return tt_kernel_timer_stop_ex(ms, flops, nullptr, capacity, count);
+}
+
+int tt_kernel_timer_stop_ex(double *ms, double *flops, int32_t *role, int32_t capacity,
+                            int64_t *count) {
   if (capacity < 0 || (capacity > 0 && (ms == nullptr || flops == nullptr))) return TT_ERR_ARG;
   std::lock_guard<std::mutex> lk(hatt::g_timer.mu);
   if (!hatt::g_timer.active.load()) return TT_ERR_ARG;
@@ -1322,6 +1342,7 @@ int tt_kernel_timer_stop(double *ms, double *flops, int32_t capacity, int64_t *c
     if (f < 0.0) {
       ms[i] = -1.0;
       flops[i] = 0.0;
+      if (role) role[i] = hatt::g_timer.role[i];
       continue;
     }
     if (cudaEventSynchronize(hatt::g_timer.ev[2 * i + 1]) != cudaSuccess ||
@@ -1332,6 +1353,7 @@ int tt_kernel_timer_stop(double *ms, double *flops, int32_t capacity, int64_t *c
     }
     ms[i] = (double)t;
     flops[i] = f;
+    if (role) role[i] = hatt::g_timer.role[i];
   }
   if (count) *count = used;
   hatt::timer_release();

@@ -60,9 +60,12 @@ void set_tile_counters(int *counters);
 int *tile_counters();
 // Kernel timer (see tt_kernel_timer_start): timer_begin returns a slot and
 // records its start event on st, or -1 when the timer is off, full, or st is
-// capturing; timer_end records the stop event and the launch's flops.
+// capturing; timer_end records the stop event, the launch's flops and its
+// role (kRoleAux or kRoleMethod, the values of tt_kernel_timer_stop_ex).
 int timer_begin(cudaStream_t st);
-void timer_end(int slot, cudaStream_t st, double flops);
+void timer_end(int slot, cudaStream_t st, double flops, int role);
+constexpr int kRoleAux = 0;      // QR, truncation, refinement and inner-product products
+constexpr int kRoleMethod = 1;   // the HaTT contractions: HPCRL (Alg. 3), C_k W, Q^T C_k, eq. (3.10)
 constexpr int kMaxOrder = 512;   // largest d handled by the parameter tables
 
 // ------------------------------------------------------------------ GEMM ---
@@ -91,6 +94,7 @@ struct Gemm {
   const double *alpha_dev = nullptr;
   const int *skip_dev = nullptr;   // if set and *skip_dev != 0 the launch does nothing
   int prec = 0;                    // kPrecFP64, or the operand type of a low-precision product
+  int role = kRoleAux;             // kernel-timer tag: kRoleMethod for the HaTT contractions
 };
 
 // Doubles of split-K scratch this GEMM needs (0 if it runs unsplit).

@@ -296,13 +296,13 @@ cudaError_t gemm_f64(const Gemm &g, double *scratch, cudaStream_t st) {
   if (gemm_tc_supported(g)) {                     // TF32 / BF16 operands: tensor cores
     const int slot = timer_begin(st);
     const cudaError_t e = gemm_tc(g, scratch, tile_counters(), st);
-    timer_end(slot, st, 2.0 * g.M * g.N * (double)g.K * g.batch);
+    timer_end(slot, st, 2.0 * g.M * g.N * (double)g.K * g.batch, g.role);
     return e;
   }
   if (gemm_oz_applicable(g)) {                    // FP64 accuracy on BF16 tensor cores
     const int slot = timer_begin(st);
     const cudaError_t e = gemm_oz(g, scratch, st);
-    timer_end(slot, st, 2.0 * g.M * g.N * (double)g.K * g.batch);
+    timer_end(slot, st, 2.0 * g.M * g.N * (double)g.K * g.batch, g.role);
     return e;
   }
   const Launch L = plan(g);
@@ -319,7 +319,7 @@ cudaError_t gemm_f64(const Gemm &g, double *scratch, cudaStream_t st) {
     case 12: launch_tile<12>(g, L, scratch, counters, st); break;
     default: launch_tile<16>(g, L, scratch, counters, st); break;
   }
-  timer_end(slot, st, 2.0 * g.M * g.N * (double)g.K * g.batch);
+  timer_end(slot, st, 2.0 * g.M * g.N * (double)g.K * g.batch, g.role);
   return cudaGetLastError();
 }
 
