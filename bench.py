@@ -41,6 +41,7 @@ FP64_PEAK_NOTE = ("derived: 152 SMs x 2 FP64 FMA lanes/SM/clk x 2 flop x 2070 MH
 
 
 GEMM_TIMING_STEPS = 3
+CFG3_GOLDEN = os.path.join(ROOT, "tests", "golden", "cfg3_oracle_samples.npz")
 GEMM_PROFILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles",
                             "gemm_f64_kernel_d20_traffic.json")
 GEMM_SOURCE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2410_04385_gb300",
@@ -228,6 +229,13 @@ def run_mixed_cfg3(binding, workloads, dev, samples=2000, steps=2):
     Zg = [torch.from_numpy(c).to(dev) for c in Z]
     out = {"workload": "smooth TT pair d=50, n=64, ranks 40, sketch 90, max rank 80, tol 1e-8",
            "error": f"relative, on {samples} sampled entries, against Y*Z", "per_precision": {}}
+    gold = None
+    if os.path.exists(CFG3_GOLDEN):
+        gold = dict(np.load(CFG3_GOLDEN))
+        out["oracle_comparison"] = ("relative difference on the 4000 entries stored by "
+                                    "tests/golden/make_cfg3_oracle.py (FP64 oracle, same sketch seed; "
+                                    "and the oracle emulating the sketch format); c7_bound = "
+                                    "10 max(oracle FP64 error, emulated error, tol) against Y*Z")
     for prec, name in ((0, "fp64"), (1, "fp32"), (2, "tf32"), (3, "bf16")):
         h = binding.HadamardRecompressor(Yg, Zg, seed=SKETCH_SEED, precision=prec, **opts)
         h.run()
@@ -247,6 +255,18 @@ def run_mixed_cfg3(binding, workloads, dev, samples=2000, steps=2):
         err = float(np.sqrt(np.sum((x - exact) ** 2) / np.sum(exact ** 2)))
         out["per_precision"][name] = {"ms_per_recompression": min(ms), "rel_error_sampled": err,
                                       "max_rank": int(max(h.Xd.r))}
+        if gold is not None:
+            xg = sampled_entries(X, gold["idx"])
+            ex = gold["exact"]
+            rd = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+            e_emul = rd(gold[f"x_{name}"], ex)
+            out["per_precision"][name].update({
+                "rel_diff_vs_fp64_oracle": rd(xg, gold["x_fp64"]),
+                "rel_diff_vs_emulated_oracle": rd(xg, gold[f"x_{name}"]),
+                "rel_error_vs_exact_oracle_samples": rd(xg, ex),
+                "oracle_fp64_error_vs_exact": rd(gold["x_fp64"], ex),
+                "oracle_emulated_error_vs_exact": e_emul,
+                "c7_bound": 10.0 * max(rd(gold["x_fp64"], ex), e_emul, 1e-8)})
         del h
     out["device_error"] = binding.device_error()
     return out

@@ -35,7 +35,8 @@ typedef enum {
   TT_ERR_ARG = 3,        /* null pointer, negative option, unknown precision/variant */
   TT_ERR_WORKSPACE = 4,  /* workspace smaller than the size reported by the *_plan call */
   TT_ERR_CUDA = 5,       /* a CUDA launch or copy failed; cudaGetLastError() has been cleared */
-  TT_ERR_NONFINITE = 6   /* reserved: a non-finite input or result was detected */
+  TT_ERR_NONFINITE = 6,  /* reserved: a non-finite input or result was detected */
+  TT_ERR_TIMEOUT = 7     /* a bounded device wait ran out (tt_batched_status) */
 } tt_status;
 
 /* Largest sketch / output rank the small dense factorizations accept
@@ -269,6 +270,55 @@ int tt_philox4x32_10(const uint32_t *ctr, uint32_t key0, uint32_t key1, uint32_t
  * counterpart in the paper: the difference around a call is that call's
  * launch count. Host only; never fails. */
 int64_t tt_launch_count(void);
+
+/* ---------------------------------------------------------------- batched
+ * Many independent recompressions in ONE persistent launch. Each pair runs
+ * HaTT-1 (Algorithm 3, then Algorithm 4) exactly as tt_hadamard_recompress
+ * does, with the sketch rank as output rank (no truncation sweep). The paper
+ * recompresses one product at a time; the task engine has no counterpart in
+ * it. Every pair's launch sequence becomes a chain of stages (its GEMMs, the
+ * Cholesky QR passes, norms, sketch cores) split into tasks (output tiles,
+ * row blocks, element chunks). One queue holds the tasks of all pairs,
+ * interleaved so that the pairs with the longest chains (most stages) start
+ * first and, within a round of stages, the pairs with the most predicted
+ * flops go first. Resident CTAs take tasks in queue order; a task waits, by a
+ * bounded poll of its pair's completion counter, for the pair's earlier
+ * stages. Since a task only waits on tasks earlier in the queue, which
+ * running CTAs already hold, the launch cannot deadlock.
+ *
+ * create: plans every pair (Y[j], Z[j], opts[j]; the same checks as
+ *   tt_hadamard_recompress_plan) and writes the output ranks (the clamped
+ *   sketch ranks) into X[j].r (host). Refuses (TT_ERR_ARG) a pair whose
+ *   options need the truncation sweep (tol > 0, or max_rank below a sketch
+ *   rank), variant 2, or a precision other than TT_FP64 / TT_MIXED_FP32.
+ *   X[j].cores must be device buffers of X[j].r[k]*n[k]*X[j].r[k+1] doubles.
+ *   The descriptors' host arrays and device buffers must stay valid while the
+ *   plan is used. *workspace_bytes: the device workspace to bind. The plan is
+ *   host memory owned by the caller (free it with tt_batched_plan_destroy).
+ * bind: lays out the workspace (caller-owned, 256-byte aligned, >= the size
+ *   reported), and with autotune = 1 times the candidate tile shapes of each
+ *   GEMM shape bucket not yet in the process-wide cache; uploads the task
+ *   tables. Synchronizes `stream`; not allowed while it is being captured.
+ * run: clears the control words and enqueues the persistent launch on
+ *   `stream` (no synchronization; capturable once bound). spin_cap bounds each
+ *   wait (polls of ~0.25 us; once any wait has run out every later wait gives
+ *   up at once and the results are invalid).
+ * status: reads the status word of the last run (synchronizes `stream`):
+ *   TT_OK, or TT_ERR_TIMEOUT if a wait ran out.
+ * info: number of stages and tasks of the bound plan and resident CTAs.
+ * tune_cache: save (save = 1) or load (save = 0) the process-wide tile cache
+ *   as text lines "prec M N K batch bm bn" at `path` (host string). */
+typedef struct tt_batch_plan tt_batch_plan;
+int tt_batched_plan_create(int32_t count, const tt_t *Y, const tt_t *Z, const tt_opts *opts,
+                           tt_t *X, tt_batch_plan **plan, size_t *workspace_bytes);
+int tt_batched_plan_bind(tt_batch_plan *plan, void *workspace, size_t workspace_bytes,
+                         int32_t autotune, void *stream);
+int tt_batched_run(tt_batch_plan *plan, int64_t spin_cap, void *stream);
+int tt_batched_status(tt_batch_plan *plan, void *stream, int32_t *status);
+int tt_batched_plan_info(const tt_batch_plan *plan, int64_t *stages, int64_t *tasks,
+                         int32_t *blocks);
+int tt_batched_plan_destroy(tt_batch_plan *plan);
+int tt_batched_tune_cache(const char *path, int32_t save);
 
 /* Kernel timer, a diagnostic with no counterpart in the paper: between
  * tt_kernel_timer_start and tt_kernel_timer_stop, each launch of the FP64

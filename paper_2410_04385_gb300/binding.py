@@ -62,7 +62,9 @@ EXPORTS = ("tt_hadamard_recompress_plan", "tt_hadamard_recompress", "tt_round_pl
            "tt_philox4x32_10", "tt_launch_count", "tt_kernel_timer_start",
            "tt_kernel_timer_stop", "tt_kernel_timer_stop_ex", "tt_device_error", "tt_hadamard_recompress_batch_plan",
            "tt_hadamard_recompress_batch", "tt_scale", "tt_laplacian", "tt_lincomb",
-           "tt_status_string")
+           "tt_status_string", "tt_batched_plan_create", "tt_batched_plan_bind", "tt_batched_run",
+           "tt_batched_status", "tt_batched_plan_info", "tt_batched_plan_destroy",
+           "tt_batched_tune_cache")
 
 
 def load(path: Optional[str] = None):
@@ -108,6 +110,14 @@ def load(path: Optional[str] = None):
     lib.tt_hadamard_recompress_batch_plan.argtypes = [ctypes.c_int32, P(TTStruct), P(TTStruct),
                                                       P(OptsStruct), ctypes.c_int32,
                                                       P(ctypes.c_size_t)]
+    lib.tt_batched_plan_create.argtypes = [ctypes.c_int32, P(TTStruct), P(TTStruct),
+                                           P(OptsStruct), P(TTStruct), P(vp), P(ctypes.c_size_t)]
+    lib.tt_batched_plan_bind.argtypes = [vp, vp, ctypes.c_size_t, ctypes.c_int32, vp]
+    lib.tt_batched_run.argtypes = [vp, ctypes.c_int64, vp]
+    lib.tt_batched_status.argtypes = [vp, vp, P(ctypes.c_int32)]
+    lib.tt_batched_plan_info.argtypes = [vp, P(ctypes.c_int64), P(ctypes.c_int64), P(ctypes.c_int32)]
+    lib.tt_batched_plan_destroy.argtypes = [vp]
+    lib.tt_batched_tune_cache.argtypes = [ctypes.c_char_p, ctypes.c_int32]
     lib.tt_hadamard_recompress_batch.argtypes = [ctypes.c_int32, P(TTStruct), P(TTStruct),
                                                  P(OptsStruct), P(TTStruct), ctypes.c_int32, vp,
                                                  ctypes.c_size_t, vp]
@@ -535,3 +545,84 @@ class BatchRecompressor:
         r, n = self.Xd[j].r, self.Xd[j].n
         return [self.out_bufs[j][k][: r[k] * n[k] * r[k + 1]].view(r[k], n[k], r[k + 1])
                 for k in range(self.Xd[j].d)]
+
+
+TT_ERR_TIMEOUT = 7
+DEFAULT_SPIN_CAP = 1 << 26
+
+
+class BatchedRecompressor:
+    """Many independent pairs recompressed by ONE persistent launch of the task
+    engine (tt_batched_*). Plans once, owns every output buffer and the
+    workspace; `run` enqueues the launch (capturable after construction)."""
+
+    def __init__(self, pairs, autotune: bool = True, stream=None):
+        """pairs: list of (Y cores, Z cores, options dict) with CUDA float64
+        cores; options as tt_hadamard_recompress (no truncation: sketch rank =
+        output rank), precision TT_FP64 or TT_MIXED_FP32."""
+        lib = load()
+        self.count = len(pairs)
+        self.pairs = pairs                       # keeps the input tensors alive
+        self.Yd = [TT(Y) for Y, _, _ in pairs]
+        self.Zd = [TT(Z) for _, Z, _ in pairs]
+        self.opts = [make_opts(**o) for _, _, o in pairs]
+        self.Xd, self.out_bufs = [], []
+        for (Y, _, _), yd, zd, op in zip(pairs, self.Yd, self.Zd, self.opts):
+            bound = (ctypes.c_int64 * (yd.d + 1))()
+            ws = ctypes.c_size_t()
+            _check("tt_hadamard_recompress_plan",
+                   lib.tt_hadamard_recompress_plan(yd.ref(), zd.ref(), ctypes.byref(op), bound,
+                                                   ctypes.byref(ws)))
+            n, b = yd.n, [int(v) for v in bound]
+            bufs = [torch.empty(b[k] * n[k] * b[k + 1], dtype=torch.float64, device=Y[0].device)
+                    for k in range(yd.d)]
+            xd = TT(n=n, r=b, pinned_ranks=True)
+            xd.set_core_ptrs([t.data_ptr() for t in bufs])
+            self.Xd.append(xd)
+            self.out_bufs.append(bufs)
+        self.Ya = (TTStruct * self.count)(*[t.s for t in self.Yd])
+        self.Za = (TTStruct * self.count)(*[t.s for t in self.Zd])
+        self.Xa = (TTStruct * self.count)(*[t.s for t in self.Xd])
+        self.Oa = (OptsStruct * self.count)(*self.opts)
+        self.plan = ctypes.c_void_p()
+        ws = ctypes.c_size_t()
+        _check("tt_batched_plan_create",
+               lib.tt_batched_plan_create(self.count, self.Ya, self.Za, self.Oa, self.Xa,
+                                          ctypes.byref(self.plan), ctypes.byref(ws)))
+        self.workspace_bytes = int(ws.value)
+        dev = pairs[0][0][0].device
+        self.workspace = torch.empty(max(self.workspace_bytes, 1), dtype=torch.uint8, device=dev)
+        _check("tt_batched_plan_bind",
+               lib.tt_batched_plan_bind(self.plan, ctypes.c_void_p(self.workspace.data_ptr()),
+                                        self.workspace_bytes, 1 if autotune else 0,
+                                        _stream_ptr(stream)))
+
+    def run(self, spin_cap: int = DEFAULT_SPIN_CAP, stream=None):
+        _check("tt_batched_run", load().tt_batched_run(self.plan, int(spin_cap), _stream_ptr(stream)))
+
+    def status(self, stream=None) -> int:
+        v = ctypes.c_int32(0)
+        _check("tt_batched_status", load().tt_batched_status(self.plan, _stream_ptr(stream),
+                                                             ctypes.byref(v)))
+        return int(v.value)
+
+    def info(self):
+        st, tk, bl = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        _check("tt_batched_plan_info", load().tt_batched_plan_info(self.plan, ctypes.byref(st),
+                                                                   ctypes.byref(tk), ctypes.byref(bl)))
+        return {"stages": int(st.value), "tasks": int(tk.value), "blocks": int(bl.value)}
+
+    def result(self, j: int) -> List[torch.Tensor]:
+        r, n = self.Xd[j].r, self.Xd[j].n
+        return [self.out_bufs[j][k][: r[k] * n[k] * r[k + 1]].view(r[k], n[k], r[k + 1])
+                for k in range(self.Xd[j].d)]
+
+    def __del__(self):
+        if getattr(self, "plan", None) is not None and self.plan.value and _lib is not None:
+            _lib.tt_batched_plan_destroy(self.plan)
+            self.plan = ctypes.c_void_p()
+
+
+def batched_tune_cache(path: str, save: bool) -> None:
+    """Save or load the engine's process-wide tile cache (text lines)."""
+    _check("tt_batched_tune_cache", load().tt_batched_tune_cache(path.encode(), 1 if save else 0))

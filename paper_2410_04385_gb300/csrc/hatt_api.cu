@@ -9,11 +9,16 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdio>
+#include <map>
+#include <memory>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "hatt.h"
 #include "hatt_internal.cuh"
+#include "engine.cuh"
 
 using hatt::Gemm;
 typedef long long ll;
@@ -105,19 +110,42 @@ struct Ws {
   }
 };
 
-// Runs a launch sequence in planning or execution mode.
+// One step of a launch sequence as recorded for the batched task engine.
+struct RecOp {
+  enum Kind { kGemm, kQr, kSketch, kSet, kNorm, kPkpFirst } kind;
+  Gemm g;                                   // kGemm
+  double *S = nullptr;                      // kQr: m x c, leading dimension c
+  int m = 0, c = 0;
+  double *out = nullptr;                    // kSketch core / kSet / kNorm target / kPkpFirst C
+  const double *x = nullptr;                // kNorm input
+  long long count = 0;
+  double value = 0.0;
+  int a = 0, n = 0, b = 0, core = 0;        // kSketch
+  uint64_t seed = 0;
+  const double *Y = nullptr, *Z = nullptr;  // kPkpFirst
+  int r1 = 0, s1 = 0;
+};
+
+// Runs a launch sequence in planning, execution or recording mode.
 struct Runner {
   bool exec = false;
   cudaStream_t st = nullptr;
   size_t scratch_need = 0;       // doubles
   double *scratch = nullptr;
   cudaError_t err = cudaSuccess;
+  std::vector<RecOp> *rec = nullptr;   // recording: collect the steps, launch nothing
 
   bool live() const { return exec && err == cudaSuccess; }
   void check(cudaError_t e) {
     if (err == cudaSuccess && e != cudaSuccess) err = e;
   }
   void gemm(const Gemm &g) {
+    if (rec) {
+      RecOp o{RecOp::kGemm};
+      o.g = g;
+      rec->push_back(o);
+      return;
+    }
     if (!exec) {
       scratch_need = std::max(scratch_need, hatt::gemm_scratch_doubles(g));
       return;
@@ -125,11 +153,68 @@ struct Runner {
     if (err == cudaSuccess) check(hatt::gemm_f64(g, scratch, st));
   }
   void qr(double *S, int m, int c, ll ld, int *flags) {
+    if (rec) {
+      RecOp o{RecOp::kQr};
+      o.S = S;
+      o.m = m;
+      o.c = c;
+      if (ld != c) err = cudaErrorInvalidValue;   // the recorded QR keeps ld = c
+      rec->push_back(o);
+      return;
+    }
     if (!exec) {
       scratch_need = std::max(scratch_need, hatt::qr_scratch_doubles(m, c));
       return;
     }
     if (err == cudaSuccess) check(hatt::qr_inplace(S, m, c, ld, scratch, flags, st));
+  }
+  // Direct launches of the HaTT sequence (no scratch): launched when live,
+  // recorded when recording.
+  void sketch(const hatt::SketchTable &t, double *base) {
+    if (rec) {
+      for (int k = 0; k < t.d; ++k) {
+        RecOp o{RecOp::kSketch};
+        o.out = base + t.offset[k];
+        o.a = t.a[k]; o.n = t.n[k]; o.b = t.b[k]; o.core = k; o.seed = t.seed;
+        rec->push_back(o);
+      }
+      return;
+    }
+    if (live()) check(hatt::sketch_fill(t, base, st));
+  }
+  void set(double *x, double v) {
+    if (rec) {
+      RecOp o{RecOp::kSet};
+      o.out = x;
+      o.value = v;
+      rec->push_back(o);
+      return;
+    }
+    if (live()) check(hatt::set_value(x, 1, v, st));
+  }
+  void zero_ticket(unsigned int *ticket) {
+    if (rec) return;
+    if (live()) check(cudaMemsetAsync(ticket, 0, sizeof(unsigned int), st));
+  }
+  void inv_norm(const double *x, ll count, double *out, double *partials, unsigned int *ticket) {
+    if (rec) {
+      RecOp o{RecOp::kNorm};
+      o.x = x;
+      o.count = count;
+      o.out = out;
+      rec->push_back(o);
+      return;
+    }
+    if (live()) check(hatt::inv_norm(x, count, out, partials, ticket, st));
+  }
+  void pkp_first(const double *Y, const double *Z, int n, int r1, int s1, double *C) {
+    if (rec) {
+      RecOp o{RecOp::kPkpFirst};
+      o.Y = Y; o.Z = Z; o.n = n; o.r1 = r1; o.s1 = s1; o.out = C;
+      rec->push_back(o);
+      return;
+    }
+    if (live()) check(hatt::pkp_first(Y, Z, n, r1, s1, C, st));
   }
   void eig(const double *G, int c, double *U) {
     if (!exec) {
@@ -410,7 +495,7 @@ void run_hatt(Runner &run, const HattArgs &a, const HattBufs &b) {
   };
 
   if (d == 1) {   // the single core Y_1(i) Z_1(i)
-    if (run.live()) run.check(hatt::pkp_first(a.Y[0], a.Z[0], (int)n[0], 1, 1, a.Xout[0], run.st));
+    if (run.exec) run.pkp_first(a.Y[0], a.Z[0], (int)n[0], 1, 1, a.Xout[0]);
     return;
   }
 
@@ -426,10 +511,10 @@ void run_hatt(Runner &run, const HattArgs &a, const HattBufs &b) {
       t.n[k] = (int)n[k];
       t.b[k] = (int)l[k + 1];
     }
-    run.check(hatt::sketch_fill(t, b.R, run.st));
-    run.check(hatt::set_value(Wk(d), 1, 1.0, run.st));          // W^{(d)} = [1]
-    run.check(hatt::set_value(b.winv + d, 1, 1.0, run.st));
-    run.check(cudaMemsetAsync(b.ticket, 0, sizeof(unsigned int), run.st));
+    run.sketch(t, b.R);
+    run.set(Wk(d), 1.0);                                          // W^{(d)} = [1]
+    run.set(b.winv + d, 1.0);
+    run.zero_ticket(b.ticket);
   }
 
   // A2/A3: HPCRL-1, W^{(k)} from W^{(k+1)} and cores k of Y, Z, R (Eq. (3.6))
@@ -439,8 +524,7 @@ void run_hatt(Runner &run, const HattArgs &a, const HattBufs &b) {
     const double *Rk = b.R + b.Roff[k];
     if (a.variant == 2) {
       hpcrl2_step(run, a, b, k, Wk(k + 1), Wk(k));
-      if (run.live())
-        run.check(hatt::inv_norm(Wk(k), (ll)r0 * s0 * l0, b.winv + k, b.partials, b.ticket, run.st));
+      if (run.live()) run.inv_norm(Wk(k), (ll)r0 * s0 * l0, b.winv + k, b.partials, b.ticket);
       continue;
     }
     {   // S1: T1[i][x][lam] = sum_g W[x][g] R_k[lam][i][g] / ||W||
@@ -476,14 +560,12 @@ void run_hatt(Runner &run, const HattArgs &a, const HattBufs &b) {
       g.prec = a.prec;
       run.gemm(g);
     }
-    if (run.live())
-      run.check(hatt::inv_norm(Wk(k), (ll)r0 * s0 * l0, b.winv + k, b.partials, b.ticket, run.st));
+    if (run.live()) run.inv_norm(Wk(k), (ll)r0 * s0 * l0, b.winv + k, b.partials, b.ticket);
   }
 
   // A4-A8: left-to-right pass (Algorithm 4)
   double *C = b.Ca, *Cn = b.Cb;
-  if (run.live())
-    run.check(hatt::pkp_first(a.Y[0], a.Z[0], (int)n[0], (int)r[1], (int)s[1], C, run.st));
+  if (run.live()) run.pkp_first(a.Y[0], a.Z[0], (int)n[0], (int)r[1], (int)s[1], C);
   for (int k = 0; k + 1 < d; ++k) {
     const ll m = l[k] * n[k];
     const int L = (int)l[k + 1];
@@ -853,6 +935,350 @@ int execute(void *workspace, size_t wsb, cudaStream_t st, Carve carve, Run runf)
 
 bool aligned(const void *p) { return ((uintptr_t)p & 255u) == 0; }
 
+// ------------------------------------------------- batched task engine ---
+// Host planner of tt_batched_*: every pair's launch sequence of run_hatt
+// (HaTT-1 without the truncation sweep) becomes a chain of engine stages in
+// the pair's own workspace; the stages of all pairs are interleaved into one
+// task queue for the persistent kernel of k_engine.cu.
+
+struct EnginePair {
+  HattArgs a;
+  size_t ws_off = 0, ws_bytes = 0;   // the pair's region of the workspace
+  double cost = 0.0;                 // predicted flops (Section 4 model)
+  std::vector<hatt::EngineStage> stages;
+  std::vector<int> group;            // stages with the same group id share prerequisites
+};
+
+// Workspace of one pair: carve_hatt's buffers plus the QR's Gram, triangle,
+// diagonal and per-core flags, and the norm partial sums.
+struct EngineBufs {
+  HattBufs h;
+  double *G = nullptr, *Ut = nullptr, *y = nullptr, *part = nullptr;
+  int *qflags = nullptr;
+};
+
+constexpr long long kEngineChunk = 32768;   // elements per element-wise task
+
+EngineBufs carve_engine(Ws &ws, const HattArgs &a) {
+  EngineBufs e;
+  e.h = carve_hatt(ws, a);
+  ll cmax = 1, wmax = 1;
+  for (int k = 0; k <= a.d; ++k) cmax = std::max(cmax, a.ell[k]);
+  for (int k = 1; k <= a.d; ++k) wmax = std::max(wmax, (ll)a.r[k] * a.s[k] * a.ell[k]);
+  e.G = ws.take<double>(cmax * cmax);
+  e.Ut = ws.take<double>(cmax * cmax);
+  e.y = ws.take<double>(cmax);
+  e.part = ws.take<double>((wmax + kEngineChunk - 1) / kEngineChunk + 1);
+  e.qflags = ws.take<int>(4 * (size_t)a.d);
+  return e;
+}
+
+// Tile edge for a dimension X: X itself if it fits under cap, else the edge in
+// [cap/2, cap] with the least padding.
+int eng_edge(int X, int cap) {
+  if (X <= cap) return X;
+  int best = cap;
+  long long best_pad = ((X + cap - 1) / cap) * (long long)cap;
+  for (int t = cap - 1; t >= std::max(1, cap / 2); --t) {
+    const long long pad = ((X + t - 1) / (long long)t) * t;
+    if (pad < best_pad) { best_pad = pad; best = t; }
+  }
+  return best;
+}
+
+void eng_set_tiles(hatt::EngineStage &s, int bm, int bn) {
+  s.bm = bm;
+  s.bn = bn;
+  s.tiles_m = (s.M + bm - 1) / bm;
+  s.tiles_n = (s.N + bn - 1) / bn;
+  s.ntasks = s.tiles_m * s.tiles_n * s.batch;
+}
+
+// Candidate tile shapes (bm x bn <= 4096, each edge <= 128) for a GEMM.
+std::vector<std::pair<int, int>> eng_tile_candidates(const hatt::EngineStage &s) {
+  static const int caps[][2] = {{32, 32}, {64, 32}, {32, 64}, {64, 64}, {128, 32}, {32, 128}};
+  std::vector<std::pair<int, int>> out;
+  for (const auto &cp : caps) {
+    const int bn = eng_edge(s.N, cp[1]);
+    const int bm = eng_edge(s.M, std::min(cp[0], 4096 / bn));
+    if (bm * bn > 4096) continue;
+    std::pair<int, int> t(bm, bn);
+    if (std::find(out.begin(), out.end(), t) == out.end()) out.push_back(t);
+  }
+  return out;
+}
+
+// Analytic default: the candidate with the least padded work per SM, preferring
+// larger tiles (fewer tasks) on ties.
+void eng_default_tiles(hatt::EngineStage &s) {
+  double best = 1e300;
+  int bm = 0, bn = 0;
+  for (const auto &t : eng_tile_candidates(s)) {
+    const double tiles = std::ceil((double)s.M / t.first) * std::ceil((double)s.N / t.second) * s.batch;
+    const double work = tiles * t.first * t.second;       // padded outputs
+    const double cost = work + tiles * 512.0;              // a per-task overhead in output units
+    if (cost < best) { best = cost; bm = t.first; bn = t.second; }
+  }
+  eng_set_tiles(s, bm, bn);
+}
+
+hatt::EngineStage eng_gemm(const Gemm &g, int pair) {
+  hatt::EngineStage s;
+  s.type = hatt::kStGemm;
+  s.pair = pair;
+  s.M = g.M; s.N = g.N; s.K = g.K; s.batch = g.batch; s.bdiv = g.bdiv;
+  s.sA1 = g.sA1; s.sA2 = g.sA2; s.sAm = g.sAm; s.sAk = g.sAk;
+  s.sB1 = g.sB1; s.sB2 = g.sB2; s.sBk = g.sBk; s.sBn = g.sBn;
+  s.sC1 = g.sC1; s.sC2 = g.sC2; s.sCm = g.sCm; s.sCn = g.sCn;
+  s.A = g.A; s.B = g.B; s.C = g.C;
+  s.alpha_dev = g.alpha_dev;
+  s.skip_dev = g.skip_dev;
+  s.prec = g.prec;
+  eng_default_tiles(s);
+  return s;
+}
+
+hatt::EngineStage eng_elem(int type, int pair, long long count) {
+  hatt::EngineStage s;
+  s.type = type;
+  s.pair = pair;
+  s.count = count;
+  s.chunk = kEngineChunk;
+  s.ntasks = (int)std::max<long long>(1, (count + kEngineChunk - 1) / kEngineChunk);
+  return s;
+}
+
+// Expands one pair's recorded launch sequence into engine stages. QR k uses
+// flag words qflags + 4 k (cleared before every run).
+void eng_expand(const std::vector<RecOp> &ops, const EngineBufs &eb, int pair,
+                std::vector<hatt::EngineStage> &out, std::vector<int> &group) {
+  int qr_index = 0, gid = 0;
+  for (size_t i = 0; i < ops.size(); ++i) {
+    const RecOp &o = ops[i];
+    switch (o.kind) {
+      case RecOp::kGemm:
+        out.push_back(eng_gemm(o.g, pair));
+        group.push_back(++gid);
+        break;
+      case RecOp::kSketch: {   // the sketch cores depend on nothing: one group
+        hatt::EngineStage s = eng_elem(hatt::kStSketch, pair, (long long)o.a * o.n * o.b);
+        s.out = o.out; s.a = o.a; s.n = o.n; s.b = o.b; s.core = o.core; s.seed = o.seed;
+        out.push_back(s);
+        group.push_back((i > 0 && ops[i - 1].kind == RecOp::kSketch) ? gid : ++gid);
+        break;
+      }
+      case RecOp::kSet: {
+        hatt::EngineStage s = eng_elem(hatt::kStSet, pair, 1);
+        s.out = o.out; s.value = o.value;
+        out.push_back(s);
+        group.push_back(++gid);
+        break;
+      }
+      case RecOp::kNorm: {
+        hatt::EngineStage p = eng_elem(hatt::kStNormPart, pair, o.count);
+        p.x = o.x; p.part = eb.part;
+        hatt::EngineStage f = eng_elem(hatt::kStNormFin, pair, p.ntasks);
+        f.ntasks = 1; f.part = eb.part; f.out = o.out;
+        out.push_back(p);
+        group.push_back(++gid);
+        out.push_back(f);
+        group.push_back(++gid);
+        break;
+      }
+      case RecOp::kPkpFirst: {
+        hatt::EngineStage s = eng_elem(hatt::kStPkpFirst, pair, (long long)o.n * o.r1 * o.s1);
+        s.Y = o.Y; s.Z = o.Z; s.n = o.n; s.r1 = o.r1; s.s1 = o.s1; s.out = o.out;
+        out.push_back(s);
+        group.push_back(++gid);
+        break;
+      }
+      case RecOp::kQr: {
+        int *flags = eb.qflags + 4 * qr_index++;
+        for (int p = 0; p < 6; ++p) {
+          Gemm g;                                  // G = S^T S, no-op once done
+          g.M = o.c; g.N = o.c; g.K = o.m;
+          g.A = o.S; g.sAm = 1; g.sAk = o.c;
+          g.B = o.S; g.sBk = o.c; g.sBn = 1;
+          g.C = eb.G; g.sCm = o.c; g.sCn = 1;
+          g.skip_dev = flags;
+          out.push_back(eng_gemm(g, pair));
+          group.push_back(++gid);
+          hatt::EngineStage ch;
+          ch.type = hatt::kStChol; ch.pair = pair; ch.ntasks = 1;
+          ch.S = o.S; ch.G = eb.G; ch.Ut = eb.Ut; ch.y = eb.y; ch.flags = flags;
+          ch.m = o.m; ch.c = o.c;
+          out.push_back(ch);
+          group.push_back(++gid);
+          hatt::EngineStage tr = ch;
+          tr.type = hatt::kStTrsm;
+          tr.ntasks = std::max(1, (o.m + hatt::kEngineTrsmRows - 1) / hatt::kEngineTrsmRows);
+          out.push_back(tr);
+          group.push_back(++gid);
+        }
+        break;
+      }
+    }
+  }
+}
+
+double eng_stage_flops(const hatt::EngineStage &s) {
+  switch (s.type) {
+    case hatt::kStGemm: return 2.0 * s.M * (double)s.N * s.K * s.batch;
+    case hatt::kStChol: return (double)s.c * s.c * s.c / 3.0;
+    case hatt::kStTrsm: return (double)s.m * s.c * s.c;
+    default: return (double)std::max<long long>(s.count, 1);
+  }
+}
+
+}  // namespace
+
+// The plan behind tt_batched_* (opaque to callers).
+struct tt_batch_plan {
+  int count = 0;
+  std::vector<EnginePair> pairs;
+  size_t ws_bytes = 0;
+  size_t tables_off = 0;             // stage and task tables in the workspace
+  int max_c = 1;
+  std::vector<hatt::EngineStage> stages;
+  std::vector<hatt::EngineTask> tasks;
+  char *ws = nullptr;                // bound workspace
+  int *head = nullptr, *done = nullptr, *status = nullptr, *qflags_all = nullptr;
+  size_t flags_bytes = 0;            // the per-pair QR flags, cleared every run
+  int blocks = 0;
+  double beta = 0.5;                 // wave shift of the shorter chains (LPT)
+};
+
+namespace {
+
+// Interleaves the pairs' stages into one queue: stage j of a pair with S
+// stages goes to wave j + beta (S_max - S), so the longest chains start
+// first; within a wave the pairs run in decreasing predicted flops (LPT).
+void eng_order(tt_batch_plan &P) {
+  struct Item { double wave; double cost; int pair; int stage; };
+  std::vector<Item> items;
+  size_t smax = 0;
+  for (const EnginePair &ep : P.pairs) smax = std::max(smax, ep.stages.size());
+  std::vector<int> base(P.pairs.size() + 1, 0);
+  for (size_t j = 0; j < P.pairs.size(); ++j) base[j + 1] = base[j] + (int)P.pairs[j].stages.size();
+  for (size_t j = 0; j < P.pairs.size(); ++j) {
+    const EnginePair &ep = P.pairs[j];
+    const double shift = P.beta * (double)(smax - ep.stages.size());
+    for (size_t i = 0; i < ep.stages.size(); ++i)
+      items.push_back({std::floor(i + shift), ep.cost, (int)j, (int)i});
+  }
+  std::stable_sort(items.begin(), items.end(), [](const Item &x, const Item &y) {
+    if (x.wave != y.wave) return x.wave < y.wave;
+    if (x.cost != y.cost) return x.cost > y.cost;
+    return x.pair < y.pair;
+  });
+  P.stages.clear();
+  P.stages.reserve(items.size());
+  for (size_t j = 0; j < P.pairs.size(); ++j)
+    for (const hatt::EngineStage &s : P.pairs[j].stages) P.stages.push_back(s);
+  // prerequisite counts: all tasks of the pair's earlier groups
+  std::vector<std::vector<int>> need(P.pairs.size());
+  for (size_t j = 0; j < P.pairs.size(); ++j) {
+    const EnginePair &ep = P.pairs[j];
+    need[j].assign(ep.stages.size(), 0);
+    int done_before = 0, group_start = 0;
+    for (size_t i = 0; i < ep.stages.size(); ++i) {
+      if (i > 0 && ep.group[i] != ep.group[i - 1]) group_start = done_before;
+      need[j][i] = group_start;
+      done_before += ep.stages[i].ntasks;
+    }
+  }
+  P.tasks.clear();
+  for (const Item &it : items) {
+    const hatt::EngineStage &s = P.pairs[it.pair].stages[it.stage];
+    for (int t = 0; t < s.ntasks; ++t)
+      P.tasks.push_back({base[it.pair] + it.stage, t, it.pair, need[it.pair][it.stage]});
+  }
+}
+
+// Autotuner: the tile shape of every engine GEMM stage, chosen by timing the
+// candidate shapes (engine_gemm_probe: all tiles of the stage as one grid) on
+// the first stage of each shape bucket -- operand dims rounded up to
+// multiples of 16, batch to a power of two, and the operand precision -- and
+// cached for the process. The cache can be saved and loaded as JSON lines
+// (tt_batched_tune_cache).
+struct TuneKey {
+  int prec, M, N, K, B;
+  bool operator<(const TuneKey &o) const {
+    return std::tie(prec, M, N, K, B) < std::tie(o.prec, o.M, o.N, o.K, o.B);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tune;
+
+TuneKey tune_key(const hatt::EngineStage &s) {
+  auto r16 = [](int x) { return (x + 15) / 16 * 16; };
+  int b = 1;
+  while (b < s.batch) b <<= 1;
+  return {s.prec, r16(s.M), r16(s.N), r16(s.K), b};
+}
+
+int eng_autotune(std::vector<hatt::EngineStage> &stages, cudaStream_t st, int *tuned) {
+  for (hatt::EngineStage &s : stages) {
+    if (s.type != hatt::kStGemm) continue;
+    const TuneKey key = tune_key(s);
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_tune.find(key);
+      if (it != g_tune.end()) {
+        const auto cands = eng_tile_candidates(s);
+        // a cached shape is reused when it is among this stage's candidates
+        if (std::find(cands.begin(), cands.end(), it->second) != cands.end()) {
+          eng_set_tiles(s, it->second.first, it->second.second);
+          continue;
+        }
+      }
+    }
+    float best = 1e30f;
+    std::pair<int, int> pick(s.bm, s.bn);
+    for (const auto &t : eng_tile_candidates(s)) {
+      hatt::EngineStage probe = s;
+      probe.skip_dev = nullptr;
+      eng_set_tiles(probe, t.first, t.second);
+      float ms = 0.0f;
+      const cudaError_t e = hatt::engine_gemm_time(probe, st, &ms);
+      if (e != cudaSuccess) return from_cuda(e);
+      if (ms < best) { best = ms; pick = t; }
+    }
+    eng_set_tiles(s, pick.first, pick.second);
+    ++*tuned;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = pick;
+  }
+  return TT_OK;
+}
+
+// Records one pair's sequence (run_hatt in recording mode) on the given base.
+int eng_record_pair(EnginePair &ep, char *base, int *qflags, int pair, std::vector<RecOp> &ops) {
+  Ws ws;
+  ws.exec = true;
+  ws.base = base;
+  EngineBufs eb = carve_engine(ws, ep.a);
+  eb.qflags = qflags;
+  Runner run;
+  run.exec = true;
+  run.rec = &ops;
+  ops.clear();
+  run_hatt(run, ep.a, eb.h);
+  if (run.err != cudaSuccess) return TT_ERR_ARG;
+  ep.stages.clear();
+  ep.group.clear();
+  eng_expand(ops, eb, pair, ep.stages, ep.group);
+  ep.cost = 0.0;
+  for (const auto &s : ep.stages) ep.cost += eng_stage_flops(s);
+  return TT_OK;
+}
+
+size_t eng_pair_bytes(const HattArgs &a) {
+  Ws ws;
+  carve_engine(ws, a);
+  return (ws.off + 255) & ~(size_t)255;
+}
+
 }  // namespace
 
 // ------------------------------------------------- allocation-free dot ---
@@ -915,6 +1341,7 @@ const char *tt_status_string(int status) {
     case TT_ERR_WORKSPACE: return "workspace too small or misaligned";
     case TT_ERR_CUDA: return "CUDA launch or copy failed";
     case TT_ERR_NONFINITE: return "non-finite value";
+    case TT_ERR_TIMEOUT: return "a bounded device wait ran out";
     default: return "unknown status";
   }
 }
@@ -1358,6 +1785,180 @@ int tt_kernel_timer_stop_ex(double *ms, double *flops, int32_t *role, int32_t ca
   if (count) *count = used;
   hatt::timer_release();
   return status;
+}
+
+// ------------------------------------------------------------- batched ---
+
+int tt_batched_plan_create(int32_t count, const tt_t *Y, const tt_t *Z, const tt_opts *opts,
+                           tt_t *X, tt_batch_plan **plan, size_t *workspace_bytes) {
+  if (!plan || !workspace_bytes || count < 1 || !Y || !Z || !opts || !X) return TT_ERR_ARG;
+  *plan = nullptr;
+  std::unique_ptr<tt_batch_plan> P(new tt_batch_plan());
+  P->count = count;
+  P->pairs.resize(count);
+  size_t off = 0;
+  long long flag_ints = 0;
+  for (int j = 0; j < count; ++j) {
+    EnginePair &ep = P->pairs[j];
+    int st = prepare_hatt(&Y[j], &Z[j], &opts[j], true, ep.a);
+    if (st != TT_OK) return st;
+    // the engine runs HaTT-1 in FP64 or with FP32 sketch products, and
+    // without the truncation sweep (sketch rank = output rank)
+    if (ep.a.variant != 1 || ep.a.trunc) return TT_ERR_ARG;
+    if (opts[j].precision != TT_FP64 && opts[j].precision != TT_MIXED_FP32) return TT_ERR_ARG;
+    if (!X[j].cores || !X[j].r || !X[j].n || X[j].d != Y[j].d) return TT_ERR_ARG;
+    for (int k = 0; k < ep.a.d; ++k)
+      if (X[j].n[k] != Y[j].n[k] || !X[j].cores[k]) return TT_ERR_SHAPE;
+    ep.a.Y = Y[j].cores;
+    ep.a.Z = Z[j].cores;
+    ep.a.Xout = X[j].cores;
+    for (int k = 0; k <= ep.a.d; ++k) X[j].r[k] = ep.a.outb[k];
+    ep.ws_off = off;
+    ep.ws_bytes = eng_pair_bytes(ep.a);
+    off += ep.ws_bytes;
+    flag_ints += 4LL * ep.a.d;
+    for (int k = 0; k <= ep.a.d; ++k) P->max_c = std::max<int>(P->max_c, (int)ep.a.ell[k]);
+  }
+  // control words: head, status, per-pair completion counters, QR flags
+  P->flags_bytes = ((2 + (size_t)count + (size_t)flag_ints) * sizeof(int) + 255) & ~(size_t)255;
+  const size_t ctl_off = off;
+  off += P->flags_bytes;
+  // count stages and the largest task count over the tile candidates with a
+  // stand-in base address (pointers are formed, never dereferenced)
+  std::vector<RecOp> ops;
+  size_t nstages = 0, ntasks_max = 0;
+  char *fake = reinterpret_cast<char *>((uintptr_t)1 << 40);
+  int *fq = reinterpret_cast<int *>(fake + ctl_off) + 2 + count;
+  for (int j = 0; j < count; ++j) {
+    EnginePair &ep = P->pairs[j];
+    int st = eng_record_pair(ep, fake + ep.ws_off, fq, j, ops);
+    if (st != TT_OK) return st;
+    fq += 4 * ep.a.d;
+    nstages += ep.stages.size();
+    for (const auto &s : ep.stages) {
+      size_t most = (size_t)s.ntasks;
+      if (s.type == hatt::kStGemm)
+        for (const auto &t : eng_tile_candidates(s)) {
+          hatt::EngineStage c = s;
+          eng_set_tiles(c, t.first, t.second);
+          most = std::max(most, (size_t)c.ntasks);
+        }
+      ntasks_max += most;
+    }
+    ep.stages.clear();
+    ep.group.clear();
+  }
+  if (ntasks_max >= (size_t)INT32_MAX) return TT_ERR_RANK;
+  P->tables_off = (off + 255) & ~(size_t)255;
+  P->ws_bytes = P->tables_off + nstages * sizeof(hatt::EngineStage) +
+                ntasks_max * sizeof(hatt::EngineTask) + 256;
+  *workspace_bytes = P->ws_bytes;
+  *plan = P.release();
+  return TT_OK;
+}
+
+int tt_batched_plan_bind(tt_batch_plan *P, void *workspace, size_t workspace_bytes,
+                         int32_t autotune, void *stream) {
+  if (!P || (autotune != 0 && autotune != 1)) return TT_ERR_ARG;
+  if (!workspace || !aligned(workspace) || workspace_bytes < P->ws_bytes) return TT_ERR_WORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return from_cuda(cudaGetLastError());
+  if (cs != cudaStreamCaptureStatusNone) return TT_ERR_ARG;        // synchronizes: not capturable
+  char *ws = (char *)workspace;
+  const size_t ctl_off = P->pairs.back().ws_off + P->pairs.back().ws_bytes;
+  int *ctl = reinterpret_cast<int *>(ws + ctl_off);
+  P->ws = ws;
+  P->head = ctl;
+  P->status = ctl + 1;
+  P->done = ctl + 2;
+  P->qflags_all = ctl + 2 + P->count;
+  std::vector<RecOp> ops;
+  int *fq = P->qflags_all;
+  for (int j = 0; j < P->count; ++j) {
+    EnginePair &ep = P->pairs[j];
+    int s = eng_record_pair(ep, ws + ep.ws_off, fq, j, ops);
+    if (s != TT_OK) return s;
+    fq += 4 * ep.a.d;
+  }
+  cudaError_t e = cudaMemsetAsync(ctl, 0, P->flags_bytes, st);
+  if (e != cudaSuccess) return from_cuda(e);
+  if (autotune) {
+    int tuned = 0;
+    for (EnginePair &ep : P->pairs) {
+      const int s = eng_autotune(ep.stages, st, &tuned);
+      if (s != TT_OK) return s;
+    }
+  }
+  eng_order(*P);
+  const size_t sb = P->stages.size() * sizeof(hatt::EngineStage);
+  const size_t tb = P->tasks.size() * sizeof(hatt::EngineTask);
+  if (P->tables_off + sb + tb > P->ws_bytes) return TT_ERR_WORKSPACE;
+  e = cudaMemcpyAsync(ws + P->tables_off, P->stages.data(), sb, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ws + P->tables_off + sb, P->tasks.data(), tb, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = hatt::engine_blocks(P->max_c, &P->blocks);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);             // host tables may change later
+  return from_cuda(e);
+}
+
+int tt_batched_run(tt_batch_plan *P, int64_t spin_cap, void *stream) {
+  if (!P || !P->ws || spin_cap < 1) return TT_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemsetAsync(P->head, 0, P->flags_bytes, st);
+  if (e != cudaSuccess) return from_cuda(e);
+  const auto *stages = reinterpret_cast<const hatt::EngineStage *>(P->ws + P->tables_off);
+  const auto *tasks = reinterpret_cast<const hatt::EngineTask *>(
+      P->ws + P->tables_off + P->stages.size() * sizeof(hatt::EngineStage));
+  e = hatt::engine_launch(stages, tasks, (int)P->tasks.size(), P->head, P->done, P->status,
+                          (long long)spin_cap, P->max_c, P->blocks, st);
+  return from_cuda(e);
+}
+
+int tt_batched_status(tt_batch_plan *P, void *stream, int32_t *status) {
+  if (!P || !P->ws || !status) return TT_ERR_ARG;
+  int v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, P->status, sizeof(int), cudaMemcpyDeviceToHost,
+                                  (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return from_cuda(e);
+  *status = (v & hatt::kEngineTimeout) ? TT_ERR_TIMEOUT : TT_OK;
+  return TT_OK;
+}
+
+int tt_batched_plan_info(const tt_batch_plan *P, int64_t *stages, int64_t *tasks, int32_t *blocks) {
+  if (!P) return TT_ERR_ARG;
+  if (stages) *stages = (int64_t)P->stages.size();
+  if (tasks) *tasks = (int64_t)P->tasks.size();
+  if (blocks) *blocks = P->blocks;
+  return TT_OK;
+}
+
+int tt_batched_plan_destroy(tt_batch_plan *P) {
+  delete P;
+  return TT_OK;
+}
+
+int tt_batched_tune_cache(const char *path, int32_t save) {
+  if (!path || (save != 0 && save != 1)) return TT_ERR_ARG;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (save) {
+    FILE *f = std::fopen(path, "w");
+    if (!f) return TT_ERR_ARG;
+    for (const auto &kv : g_tune)
+      std::fprintf(f, "%d %d %d %d %d %d %d\n", kv.first.prec, kv.first.M, kv.first.N, kv.first.K,
+                   kv.first.B, kv.second.first, kv.second.second);
+    std::fclose(f);
+    return TT_OK;
+  }
+  FILE *f = std::fopen(path, "r");
+  if (!f) return TT_ERR_ARG;
+  TuneKey k;
+  int bm = 0, bn = 0;
+  while (std::fscanf(f, "%d %d %d %d %d %d %d", &k.prec, &k.M, &k.N, &k.K, &k.B, &bm, &bn) == 7)
+    if (bm > 0 && bn > 0 && bm <= 128 && bn <= 128 && bm * bn <= 4096) g_tune[k] = {bm, bn};
+  std::fclose(f);
+  return TT_OK;
 }
 
 int tt_philox4x32_10(const uint32_t *ctr, uint32_t key0, uint32_t key1, uint32_t *out,

@@ -1,0 +1,85 @@
+"""Parity at the full size of the smooth d = 50 workload (n = 64, ranks 40,
+sketch rank 90, target rank 80, tol 1e-8) in every sketch precision, against
+the FP64 oracle's result for the same sketch.
+
+The oracle needs about 100 s per format at this size, so its results enter as
+entries at 4000 seeded multi-indices, written by tests/golden/make_cfg3_oracle.py
+(oracle only). The GPU result is sampled at the same indices on the device.
+
+  * FP64: relative difference to the FP64 oracle on the samples <= 1e-12.
+  * FP32 / TF32 / BF16 sketch products (reading C6): the error against the
+    exact product Y * Z stays within reading C7's bound
+    10 * max(error of the FP64 oracle, error of the oracle emulating the
+    format, tol); the difference to the FP64 oracle and to the emulation are
+    checked against the same bound and reported.
+"""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2410_04385_gb300 import workloads as wl
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "cfg3_oracle_samples.npz")
+SKETCH_SEED = 9
+FMT = {0: "fp64", 1: "fp32", 2: "tf32", 3: "bf16"}
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2410_04385_gb300 import binding, build
+    if not os.path.exists(binding.LIB_PATH):
+        build.build()
+    binding.load()
+    return binding
+
+
+@pytest.fixture(scope="module")
+def case():
+    Y, Z, opts = wl.workload_smooth_d50()
+    gold = dict(np.load(GOLDEN))
+    Yg = [torch.from_numpy(c).cuda() for c in Y]
+    Zg = [torch.from_numpy(c).cuda() for c in Z]
+    return Yg, Zg, opts, gold
+
+
+def sampled(cores, idx):
+    """Entries of a TT (CUDA cores) at the multi-indices idx, on the device."""
+    ix = torch.from_numpy(idx.astype(np.int64)).cuda()
+    M = torch.ones((idx.shape[0], 1), dtype=torch.float64, device="cuda")
+    for k, c in enumerate(cores):
+        M = torch.bmm(M.unsqueeze(1), c[:, ix[:, k], :].permute(1, 0, 2)).squeeze(1)
+    return M[:, 0].cpu().numpy()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+def test_full_size_smooth_d50_against_the_fp64_oracle(B, case, prec):
+    Yg, Zg, opts, gold = case
+    X = B.tt_hadamard_recompress(Yg, Zg, seed=SKETCH_SEED, precision=prec, **opts)
+    torch.cuda.synchronize()
+    assert B.device_error() == 0
+    x = sampled(X, gold["idx"])
+    exact = gold["exact"]
+    fmt = FMT[prec]
+    d64 = rel(x, gold["x_fp64"])
+    if prec == 0:
+        assert [int(c.shape[0]) for c in X] + [1] == [int(v) for v in gold["ranks_fp64"]]
+        assert d64 <= 1e-12, d64
+        return
+    tol = opts["tol"]
+    e_gpu = rel(x, exact)
+    e_o64 = rel(gold["x_fp64"], exact)
+    e_emul = rel(gold[f"x_{fmt}"], exact)
+    bound = 10.0 * max(e_o64, e_emul, tol)
+    assert e_gpu <= bound, (fmt, e_gpu, bound)
+    assert d64 <= bound, (fmt, d64, bound)
+    assert rel(x, gold[f"x_{fmt}"]) <= bound
