@@ -42,6 +42,7 @@ FP64_PEAK_NOTE = ("derived: 152 SMs x 2 FP64 FMA lanes/SM/clk x 2 flop x 2070 MH
 
 GEMM_TIMING_STEPS = 3
 CFG3_GOLDEN = os.path.join(ROOT, "tests", "golden", "cfg3_oracle_samples.npz")
+AC_GOLDEN = os.path.join(ROOT, "tests", "golden", "allen_cahn_oracle_samples.npz")
 GEMM_PROFILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles",
                             "gemm_f64_kernel_d20_traffic.json")
 GEMM_SOURCE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2410_04385_gb300",
@@ -107,15 +108,20 @@ def allen_cahn_initial(d, n, terms=4, seed=0):
     return cores
 
 
-def run_allen_cahn(dev, d=8, n=64, steps=100, eps=0.1, dt=1e-3, graph_steps=300):
+def run_allen_cahn(dev, d=8, n=64, steps=50, eps=0.1, dt=1e-3, graph_steps=1000, mixed_steps=100):
     """Example 4 on [0, 2 pi)^8, n = 64, eps = 0.1, dt = 1e-3: explicit Euler
     with u^2, u^3 by HaTT-1 (rank cap 24, tol 1e-10) and tt_round (cap 24, tol
-    1e-8) each step; wall time per step and the discrete energy. Then the
-    fixed-rank variant (rank 24 held) with one step captured in a CUDA graph,
-    replayed graph_steps times."""
+    1e-8) each step. (1) The eager loop (data-dependent ranks, one library call
+    sequence per step). (2) The fixed-rank variant (rank 24 held) with one step
+    captured in a CUDA graph and replayed graph_steps times, fresh sketch seeds
+    every replay; the state after 100 steps against the FP64 oracle's (4000
+    stored samples), the energy every 100 steps. (3) The same graph with FP32
+    sketch products for mixed_steps steps, against the same oracle state."""
     import math
+    import numpy as np
     import torch
     from paper_2410_04385_gb300 import allen_cahn as ac
+    from paper_2410_04385_gb300 import binding
     h = 2.0 * math.pi / n
     u = [torch.from_numpy(c).to(dev) for c in allen_cahn_initial(d, n)]
     energies = []
@@ -129,32 +135,55 @@ def run_allen_cahn(dev, d=8, n=64, steps=100, eps=0.1, dt=1e-3, graph_steps=300)
     wall = time.perf_counter() - t0
     out = {"workload": f"u_t = eps^2 Lap u + u - u^3 on [0,2pi)^{d}, n={n}, eps={eps}, dt={dt}, "
                        f"explicit Euler, u^3 by two HaTT-1 calls, tt_round tol 1e-8",
-           "steps": steps, "ms_per_step": 1000.0 * wall / steps,
-           "max_rank": int(max(c.shape[2] for c in u)),
-           "energy_every_10_steps": energies,
-           "energy_non_increasing": bool(all(b <= a * (1 + 1e-9) for a, b in zip(energies, energies[1:])))}
-    # the same scheme with every shape fixed (u held at rank 24), one step
-    # captured in a CUDA graph and replayed graph_steps times
-    st = ac.FixedRankStepper([torch.from_numpy(c).to(dev) for c in allen_cahn_initial(d, n)], h, eps,
-                             dt, rank=24, tol=1e-8, hatt_tol=1e-10, hatt_rank=24, seed=0)
-    st.capture()
-    e0 = st.energy()
-    genergies, ms = [e0], 0.0
-    for _ in range(graph_steps // 100):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        for _ in range(100):
-            st.replay()
-        b.record()
-        torch.cuda.synchronize()
-        ms += a.elapsed_time(b)
-        genergies.append(st.energy())
-    out["graph"] = {"steps": graph_steps, "ms_per_step": ms / graph_steps,
-                    "timing": "CUDA events around each 100 graph replays (energy read between them)",
-                    "sketch_seeds": "fixed by the graph: the same two seeds every step",
+           "eager": {"steps": steps, "ms_per_step": 1000.0 * wall / steps,
+                     "max_rank": int(max(c.shape[2] for c in u)), "energy_every_10_steps": energies,
+                     "energy_non_increasing": bool(all(b <= a * (1 + 1e-9)
+                                                       for a, b in zip(energies, energies[1:])))}}
+    gold = dict(np.load(AC_GOLDEN)) if os.path.exists(AC_GOLDEN) else None
+
+    def sample_err(st):
+        if gold is None:
+            return None
+        x = sampled_entries([c.cpu().numpy() for c in st.u], gold["idx"])
+        return float(np.linalg.norm(x - gold["u"]) / np.linalg.norm(gold["u"]))
+
+    def graph_run(precision, total):
+        st = ac.FixedRankStepper([torch.from_numpy(c).to(dev) for c in allen_cahn_initial(d, n)], h,
+                                 eps, dt, rank=24, tol=1e-8, hatt_tol=1e-10, hatt_rank=24, seed=10,
+                                 precision=precision, fresh_seeds=True)
+        st.capture()                                   # step 1
+        genergies, ms, done, err100 = [], 0.0, 1, None
+        while done < total:
+            chunk = min(100 - done % 100 if done % 100 else 100, total - done)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(chunk):
+                st.replay()
+            b.record()
+            torch.cuda.synchronize()
+            ms += a.elapsed_time(b)
+            done += chunk
+            if done % 100 == 0:
+                genergies.append(st.energy())
+            if done == 100:
+                err100 = sample_err(st)
+        return st, {"steps": total, "ms_per_step": ms / max(total - 1, 1),
                     "energy_every_100_steps": genergies,
-                    "energy_non_increasing": bool(all(b <= a * (1 + 1e-9)
-                                                      for a, b in zip(genergies, genergies[1:])))}
+                    "energy_non_increasing": bool(all(y <= x * (1 + 1e-9)
+                                                      for x, y in zip(genergies, genergies[1:]))),
+                    "rel_error_vs_fp64_oracle_at_step_100": err100}
+
+    st, g = graph_run(binding.TT_FP64, graph_steps)
+    g.update({"timing": "CUDA events around each run of replays (energy read between them)",
+              "sketch_seeds": "fresh every replay: keys seed + 2w, seed + 1 + 2w (device seed offset)",
+              "oracle": "FP64 oracle's fixed-rank trajectory, 100 steps (tests/golden/"
+                        "make_allen_cahn_oracle.py), relative error on 4000 sampled entries"})
+    out["graph"] = g
+    del st
+    _, m = graph_run(binding.TT_MIXED_FP32, mixed_steps)
+    m["precision"] = "FP32 sketch products (HPCRL), FP64 QR / projection / update / rounding"
+    out["graph_mixed_fp32"] = m
+    out["device_error"] = binding.device_error()
     return out
 
 
@@ -182,36 +211,94 @@ def run_power_iteration(workloads, dev, d=50, iters=100):
     return out
 
 
-def run_batch_cfg4(binding, workloads, dev, lanes=16):
+def run_batch_cfg4(binding, workloads, dev, rank=0, world=1):
     """256 independent pairs (d in [10, 40], n in {16, 32, 64}, inner ranks in
-    [8, 48], target 2 max(r_Y, r_Z), FP32 sketches, FP64 QR / projection /
-    truncation) recompressed by one batched call over `lanes` library streams,
-    against the same call with one lane (the pairs one after another on one
-    stream). Device time of one whole batch each (CUDA events)."""
+    [8, 48], sketch rank = target rank = 2 max(r_Y, r_Z)) recompressed by ONE
+    persistent launch of the task engine (FP32 sketch products, FP64 QR /
+    projection / update, autotuned tiles), against the same pairs one after
+    another in FP64 through the single-pair entry point on one stream. Device
+    time of a whole batch each (CUDA events); the engine's results are checked
+    against the sequential FP64 ones with TT inner products."""
     import torch
+    from paper_2410_04385_gb300 import sharding
     pairs = workloads.workload_batch_uneven()
-    gpu = [([torch.from_numpy(c).to(dev) for c in Y], [torch.from_numpy(c).to(dev) for c in Z],
-            dict(o, precision=binding.TT_MIXED_FP32, seed=j)) for j, (Y, Z, o) in enumerate(pairs)]
-    out = {"workload": "256 TT pairs, d 10-40, n 16/32/64, ranks 8-48, target 2 max(r), "
-                       "FP32 sketch, FP64 QR / projection / truncation",
+    out = {"workload": "256 TT pairs, d 10-40, n 16/32/64, ranks 8-48, sketch = target = 2 max(r)",
            "unit": "recompressions/s"}
-    for name, nl in (("one_lane", 1), (f"{lanes}_lanes", lanes)):
-        b = binding.BatchRecompressor(gpu, lanes=nl)
-        b.run()
-        torch.cuda.synchronize()
+    # pairs sharded over the ranks by LPT on predicted flops (no data-path collective)
+    costs = [sharding.predicted_flops(Y, Z, o) for Y, Z, o in pairs]
+    mine = sharding.lpt_partition(costs, world)[rank]
+    mk = lambda prec, idx: [([torch.from_numpy(c).to(dev) for c in pairs[j][0]],
+                             [torch.from_numpy(c).to(dev) for c in pairs[j][1]],
+                             dict(pairs[j][2], precision=prec, seed=j)) for j in idx]
+    gpu = mk(binding.TT_MIXED_FP32, mine)
+    t0 = time.perf_counter()
+    eng = binding.BatchedRecompressor(gpu, autotune=True) if gpu else None
+    plan_s = time.perf_counter() - t0
+    if eng is not None:
+        eng.run()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(2):
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
         s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s0.record()
-        b.run()
+        if eng is not None:
+            eng.run()
         s1.record()
         torch.cuda.synchronize()
-        ms = s0.elapsed_time(s1)
-        out[name] = {"ms_per_batch": ms, "value": 1000.0 * len(gpu) / ms,
-                     "workspace_gb": b.workspace_bytes / 1e9}
-        del b
+        ms.append(max_over_ranks(s0.elapsed_time(s1), world, dev))
+    status = eng.status() if eng is not None else 0
+    records = [[j, status] + [int(v) for v in eng.Xd[q].r] for q, j in enumerate(mine)] if eng else []
+    gathered = sharding.gather_records(records, world)
+    out["engine"] = {"ms_per_batch": min(ms), "value": 1000.0 * len(pairs) / min(ms),
+                     "launches_per_batch_per_gpu": 1, "status": status, "plan_and_autotune_s": plan_s,
+                     "workspace_gb_rank0": (eng.workspace_bytes / 1e9) if eng else 0.0,
+                     **(eng.info() if eng else {}),
+                     "precision": "FP32 sketch products, FP64 QR / projection / update",
+                     "sharding": f"LPT on predicted flops over {world} rank(s); pairs on rank 0: {len(mine)}",
+                     "pairs_gathered": len(gathered),
+                     "all_status_ok": all(rec[1] == 0 for rec in gathered)}
+    if world > 1:
+        out["scaling"] = "strong"
+        del eng
         torch.cuda.empty_cache()
-    out["speedup_batched"] = out["one_lane"]["ms_per_batch"] / out[f"{lanes}_lanes"]["ms_per_batch"]
+        return out
+    res = [[c.clone() for c in eng.result(q)] for q in range(len(gpu))]
+    del eng, gpu
+    torch.cuda.empty_cache()
+    seq_in = mk(binding.TT_FP64, range(len(pairs)))
+    seq = binding.BatchRecompressor(seq_in, lanes=1)
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record()
+    seq.run()
+    s1.record()
+    torch.cuda.synchronize()
+    seq_ms = s0.elapsed_time(s1)
+    out["sequential_fp64"] = {"ms_per_batch": seq_ms, "value": 1000.0 * len(pairs) / seq_ms,
+                              "impl": "256 single-pair FP64 calls one after another on one stream"}
+    worst = 0.0
+    for j in range(len(pairs)):
+        a, b = res[j], seq.result(j)
+        aa = binding.tt_dot(a, a).item()
+        bb = binding.tt_dot(b, b).item()
+        ab = binding.tt_dot(a, b).item()
+        worst = max(worst, (max(aa - 2 * ab + bb, 0.0) ** 0.5) / bb ** 0.5)
+    out["max_rel_diff_engine_fp32_vs_sequential_fp64"] = worst
+    out["speedup_engine_vs_sequential_fp64"] = seq_ms / min(ms)
+    from paper_2410_04385_gb300 import costmodel
+    sw = 0.0
+    for Y, Z, o in pairs:
+        n, r, s_, ell = sharding.pair_ranks(Y, Z, o)
+        sw += costmodel.hatt1_flops(n, r, s_, ell)[1]
+    ach = sw / (min(ms) * 1e-3) / 1e12
+    out["engine_roofline"] = {"bound": "alu", "fp64_flops": sw, "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                              "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                              "note": "FP64 left-to-right pass (Section 4 model) over the batch time; the "
+                                      "FP32 sketch products (HPCRL) run inside the same time"}
     out["device_error"] = binding.device_error()
-    del gpu
+    del seq, res
     torch.cuda.empty_cache()
     return out
 
@@ -696,8 +783,10 @@ def main():
         line["mixed_cfg3"] = run_mixed_cfg3(binding, workloads, dev)
 
     # ---- many uneven pairs: batched over library streams vs one after another ----
-    if not args.no_batch and rank == 0:
-        line["batch_cfg4"] = run_batch_cfg4(binding, workloads, dev)
+    if not args.no_batch:
+        b4 = run_batch_cfg4(binding, workloads, dev, rank, world)
+        if rank == 0:
+            line["batch_cfg4"] = b4
 
     # ---- power iteration for the largest entry (Example 3) ----
     if not args.no_power and rank == 0:

@@ -35,8 +35,9 @@ typedef enum {
   TT_ERR_ARG = 3,        /* null pointer, negative option, unknown precision/variant */
   TT_ERR_WORKSPACE = 4,  /* workspace smaller than the size reported by the *_plan call */
   TT_ERR_CUDA = 5,       /* a CUDA launch or copy failed; cudaGetLastError() has been cleared */
-  TT_ERR_NONFINITE = 6,  /* reserved: a non-finite input or result was detected */
-  TT_ERR_TIMEOUT = 7     /* a bounded device wait ran out (tt_batched_status) */
+  TT_ERR_NONFINITE = 6,  /* a non-finite input core or intermediate (tt_device_status) */
+  TT_ERR_TIMEOUT = 7,    /* a bounded device wait ran out (tt_device_status, tt_batched_status) */
+  TT_ERR_BREAKDOWN = 8   /* a shifted Cholesky QR met a non-positive pivot (tt_device_status) */
 } tt_status;
 
 /* Largest sketch / output rank the small dense factorizations accept
@@ -113,7 +114,12 @@ typedef enum {
  *                (min(l_k, max_rank) when truncating with a cap, else l_k): rows and
  *                columns past the kept ranks are zero, X->r is set on the host before the
  *                call returns, and nothing is read back, so a call whose inputs have fixed
- *                shapes can be captured in a CUDA graph and replayed (time stepping) */
+ *                shapes can be captured in a CUDA graph and replayed (time stepping)
+ *   seed_offset  NULL, or a device uint64 read when the sketch is generated: the
+ *                Philox key is seed + *seed_offset. A captured call then draws a
+ *                fresh sketch on every replay if the caller advances the word
+ *                between replays (the library never writes it). The batched
+ *                entry point requires NULL. */
 typedef struct {
   int64_t max_rank;
   double tol;
@@ -124,6 +130,7 @@ typedef struct {
   int32_t variant;
   double ep;
   int32_t fixed_ranks;
+  const uint64_t *seed_offset;
 } tt_opts;
 
 /* Rank plan and workspace size of tt_hadamard_recompress.
@@ -304,7 +311,8 @@ int64_t tt_launch_count(void);
  *   wait (polls of ~0.25 us; once any wait has run out every later wait gives
  *   up at once and the results are invalid).
  * status: reads the status word of the last run (synchronizes `stream`):
- *   TT_OK, or TT_ERR_TIMEOUT if a wait ran out.
+ *   TT_OK, TT_ERR_TIMEOUT if a wait ran out, TT_ERR_NONFINITE if a norm or a
+ *   Gram matrix was not finite (NaN or Inf in an input), TT_ERR_BREAKDOWN.
  * info: number of stages and tasks of the bound plan and resident CTAs.
  * tune_cache: save (save = 1) or load (save = 0) the process-wide tile cache
  *   as text lines "prec M N K batch bm bn" at `path` (host string). */
@@ -373,13 +381,24 @@ int tt_lincomb(int32_t count, const tt_t *T, const double *coef, tt_t *S, void *
  * TT_ERR_ARG for a negative count or NULL pointers (count > 0). */
 int tt_scale(double *x, int64_t count, const double *divisor, void *stream);
 
-/* Device error word, a diagnostic with no counterpart in the paper: set when
- * a bounded wait inside a kernel runs out (the tensor-core products wait on
- * an mbarrier for their own MMAs); that kernel writes NaN to its outputs,
- * frees its tensor memory and returns, so nothing hangs or traps. Writes the
- * word to *value (host) and clears it; synchronizes the current device.
- * TT_ERR_ARG if value is NULL, TT_ERR_CUDA if the device cannot be read. */
+/* Device error word, a diagnostic with no counterpart in the paper. Bits:
+ *   1  a bounded wait inside a kernel ran out (the tensor-core products wait
+ *      on an mbarrier for their own MMAs); that kernel writes NaN to its
+ *      outputs, frees its tensor memory and returns, so nothing hangs or traps;
+ *   2  a non-finite value reached a norm ||W^{(k)}|| of the right-to-left
+ *      sketches (Algorithm 3) or the Gram matrix of a Cholesky QR pass
+ *      (Algorithm 4, tt_round): a NaN or Inf in an input core, or an overflow;
+ *      the QR stops there and leaves its matrix as it was;
+ *   4  a shifted Cholesky factorization still met a non-positive pivot (QR
+ *      breakdown; the shift of shifted Cholesky QR makes this unreachable for
+ *      finite inputs, the bit guards against it).
+ * Writes the word to *value (host) and clears it; synchronizes the current
+ * device. TT_ERR_ARG if value is NULL, TT_ERR_CUDA if the device cannot be read. */
 int tt_device_error(int32_t *value);
+/* As tt_device_error, reporting the word as a status: TT_ERR_TIMEOUT (bit 1),
+ * else TT_ERR_NONFINITE (bit 2), else TT_ERR_BREAKDOWN (bit 4), else TT_OK;
+ * clears the word, synchronizes the current device. */
+int tt_device_status(int32_t *status);
 
 /* Static description of a status code (never NULL). */
 const char *tt_status_string(int status);

@@ -125,3 +125,20 @@ def is_left_orthogonal(cores, atol=1e-12):
         if not np.allclose(v.T @ v, np.eye(v.shape[1]), atol=atol, rtol=0):
             return False
     return True
+
+
+def bond_singular_values(A):
+    """Singular values of the unfoldings A_<k> (rows: modes 1..k, columns:
+    modes k+1..d) for k = 1..d-1: left-orthogonalize, then sweep right to
+    left taking the SVD of H(X_k) and moving U S into core k-1 (the left
+    factor is orthonormal, so these are the unfolding's singular values).
+    Returns a list of d-1 arrays, bond k at index k-1."""
+    cores = left_orthogonalize(A)
+    out = [None] * (len(cores) - 1)
+    for k in range(len(cores) - 1, 0, -1):
+        a, n, b = cores[k].shape
+        u, sv, vt = np.linalg.svd(H(cores[k]), full_matrices=False)
+        out[k - 1] = sv
+        cores[k] = vt.reshape(vt.shape[0], n, b)
+        cores[k - 1] = np.einsum("xiy,yz->xiz", cores[k - 1], u * sv)
+    return out

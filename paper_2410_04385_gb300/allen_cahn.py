@@ -59,20 +59,26 @@ class FixedRankStepper:
     in a CUDA graph and replayed: u is held at the padded rank `rank` (zero
     past the ranks the rounding keeps), both HaTT-1 calls and the rounding run
     with fixed_ranks=1, and the Laplacian, the combination and the rounding
-    write into buffers planned once. The graph fixes the sketch seeds, so every
-    step uses `seed` and `seed + 1`."""
+    write into buffers planned once. With fresh_seeds the sketches of step w
+    use the keys seed + 2 w and seed + 1 + 2 w: a device counter (the calls'
+    seed_offset) that every step, graph replays included, advances by 2;
+    without it every step uses seed and seed + 1."""
 
     def __init__(self, u0: Sequence[torch.Tensor], h: float, eps: float, dt: float, rank: int,
                  tol: float, hatt_tol: float, hatt_rank: int, seed: int,
-                 precision: int = binding.TT_FP64):
+                 precision: int = binding.TT_FP64, fresh_seeds: bool = False):
         self.h, self.eps, self.dt = h, eps, dt
         self.u = [c.contiguous().clone() for c in pad_ranks(u0, rank)]
         ranks = [int(self.u[0].shape[0])] + [int(c.shape[2]) for c in self.u]
+        dev = self.u[0].device
+        self.seed_counter = torch.zeros(1, dtype=torch.int64, device=dev) if fresh_seeds else None
         self.h1 = binding.HadamardRecompressor(self.u, self.u, max_rank=hatt_rank, tol=hatt_tol,
-                                               seed=seed, precision=precision, fixed_ranks=1)
+                                               seed=seed, precision=precision, fixed_ranks=1,
+                                               seed_offset=self.seed_counter)
         self.u2 = self.h1.result()
         self.h2 = binding.HadamardRecompressor(self.u2, self.u, max_rank=hatt_rank, tol=hatt_tol,
-                                               seed=seed + 1, precision=precision, fixed_ranks=1)
+                                               seed=seed + 1, precision=precision, fixed_ranks=1,
+                                               seed_offset=self.seed_counter)
         self.u3 = self.h2.result()
         self.lap = binding.tt_laplacian(self.u, 1.0 / (h * h))
         self.coef = [1.0 + dt, dt * eps * eps, -dt]
@@ -93,6 +99,8 @@ class FixedRankStepper:
         self.rnd.run()
         for a, b in zip(self.u, self.un):
             a.copy_(b)
+        if self.seed_counter is not None:
+            self.seed_counter.add_(2)
 
     def capture(self):
         """Capture one step in a CUDA graph. The eager warm-up before the

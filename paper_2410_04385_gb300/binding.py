@@ -45,6 +45,7 @@ class OptsStruct(ctypes.Structure):
         ("variant", ctypes.c_int32),
         ("ep", ctypes.c_double),
         ("fixed_ranks", ctypes.c_int32),
+        ("seed_offset", ctypes.c_void_p),
     ]
 
 
@@ -64,7 +65,7 @@ EXPORTS = ("tt_hadamard_recompress_plan", "tt_hadamard_recompress", "tt_round_pl
            "tt_hadamard_recompress_batch", "tt_scale", "tt_laplacian", "tt_lincomb",
            "tt_status_string", "tt_batched_plan_create", "tt_batched_plan_bind", "tt_batched_run",
            "tt_batched_status", "tt_batched_plan_info", "tt_batched_plan_destroy",
-           "tt_batched_tune_cache")
+           "tt_batched_tune_cache", "tt_device_status")
 
 
 def load(path: Optional[str] = None):
@@ -104,6 +105,7 @@ def load(path: Optional[str] = None):
     lib.tt_launch_count.argtypes = []
     lib.tt_kernel_timer_start.argtypes = [ctypes.c_int32]
     lib.tt_device_error.argtypes = [P(ctypes.c_int32)]
+    lib.tt_device_status.argtypes = [P(ctypes.c_int32)]
     lib.tt_scale.argtypes = [vp, ctypes.c_int64, vp, vp]
     lib.tt_laplacian.argtypes = [P(TTStruct), ctypes.c_double, P(TTStruct), vp]
     lib.tt_lincomb.argtypes = [ctypes.c_int32, P(TTStruct), P(ctypes.c_double), P(TTStruct), vp]
@@ -273,10 +275,13 @@ class TT:
 
 
 def make_opts(max_rank=0, tol=0.0, sketch_rank=0, oversample=10, seed=0, precision=TT_FP64,
-              variant=1, ep=0.0, fixed_ranks=0):
+              variant=1, ep=0.0, fixed_ranks=0, seed_offset=None):
+    """seed_offset: None, or a CUDA uint64/int64 tensor of one element whose
+    value the sketch adds to `seed` when it runs (graph replays)."""
+    off = None if seed_offset is None else ctypes.c_void_p(seed_offset.data_ptr())
     return OptsStruct(int(max_rank), float(tol), int(sketch_rank), int(oversample),
                       int(seed) & 0xFFFFFFFFFFFFFFFF, int(precision), int(variant), float(ep),
-                      int(fixed_ranks))
+                      int(fixed_ranks), off)
 
 
 class HadamardRecompressor:
@@ -343,14 +348,16 @@ class HadamardRecompressor:
 
 
 def tt_hadamard_recompress(Y, Z, max_rank=0, tol=0.0, sketch_rank=0, oversample=10, seed=0,
-                           precision=TT_FP64, variant=1, ep=0.0, fixed_ranks=0,
+                           precision=TT_FP64, variant=1, ep=0.0, fixed_ranks=0, seed_offset=None,
                            stream=None) -> List[torch.Tensor]:
     """HaTT recompression of Y ⊙ Z; returns the output cores (synchronizes).
     precision: TT_FP64, TT_MIXED_FP32 / TF32 / BF16 or TT_FP64_TC;
-    variant 1 = HaTT-1, 2 = HaTT-2 with threshold ep."""
+    variant 1 = HaTT-1, 2 = HaTT-2 with threshold ep; seed_offset: None or a
+    one-element CUDA int64 tensor added to the sketch key."""
     h = HadamardRecompressor(Y, Z, max_rank=max_rank, tol=tol, sketch_rank=sketch_rank,
                              oversample=oversample, seed=seed, precision=precision,
-                             variant=variant, ep=ep, fixed_ranks=fixed_ranks)
+                             variant=variant, ep=ep, fixed_ranks=fixed_ranks,
+                             seed_offset=seed_offset)
     h.run(stream)
     (stream or torch.cuda.current_stream()).synchronize()
     return [c.clone() for c in h.result()]
@@ -547,8 +554,18 @@ class BatchRecompressor:
                 for k in range(self.Xd[j].d)]
 
 
+TT_ERR_NONFINITE = 6
 TT_ERR_TIMEOUT = 7
+TT_ERR_BREAKDOWN = 8
 DEFAULT_SPIN_CAP = 1 << 26
+
+
+def device_status() -> int:
+    """Read and clear the device error word as a status (synchronizes):
+    TT_OK, TT_ERR_TIMEOUT, TT_ERR_NONFINITE or TT_ERR_BREAKDOWN."""
+    v = ctypes.c_int32(0)
+    _check("tt_device_status", load().tt_device_status(ctypes.byref(v)))
+    return int(v.value)
 
 
 class BatchedRecompressor:

@@ -44,6 +44,7 @@ struct EngineStage {
   const int *skip_dev = nullptr;
   int prec = 0;                         // kPrecFP64 or kPrecFP32 operands
   int bm = 0, bn = 0, tiles_m = 0, tiles_n = 0;
+  int bgroup = 1;                       // consecutive batch entries per task
   // element stages: x / out / count, chunked by `chunk`
   const double *x = nullptr;
   double *out = nullptr;
@@ -70,9 +71,11 @@ struct EngineTask {
   int need;        // completed tasks of this pair required before it runs
 };
 
-// Status word of a launch (device int): 0, or kEngineTimeout when a wait ran
-// out (the task then ran anyway on whatever its inputs held).
-constexpr int kEngineTimeout = 1;
+// Status word of a launch (device int), bits: kEngineTimeout when a wait ran
+// out (the task then ran anyway on whatever its inputs held), kEngineNonfinite
+// when a norm of W^{(k)} or a QR Gram matrix was not finite, kEngineBreakdown
+// when a shifted Cholesky factorization still met a non-positive pivot.
+constexpr int kEngineTimeout = 1, kEngineNonfinite = 2, kEngineBreakdown = 4;
 
 constexpr int kEngineThreads = 256;
 constexpr int kEngineMaxC = 128;        // largest Cholesky / TRSM width

@@ -293,6 +293,7 @@ struct HattArgs {
   int cap;
   double tol;
   uint64_t seed;
+  const uint64_t *seed_offset = nullptr;   // device word added to the key (graph replays)
   int prec = hatt::kPrecFP64;   // arithmetic of the HPCRL-1 products (A2/A3)
   int variant = 1;              // 1 = HPCRL-1 (Eq. (3.6)), 2 = HPCRL-2 (Eq. (3.7))
   double ep = 0.0;              // HPCRL-2: keep sigma > ep * ||W^{(k)}||_2
@@ -504,6 +505,7 @@ void run_hatt(Runner &run, const HattArgs &a, const HattBufs &b) {
     hatt::SketchTable t;
     t.d = d;
     t.seed = a.seed;
+    t.seed_offset = a.seed_offset;
     t.pair = 0;
     for (int k = 0; k <= d; ++k) t.offset[k] = b.Roff[k];
     for (int k = 0; k < d; ++k) {
@@ -681,6 +683,7 @@ int prepare_hatt(const tt_t *Y, const tt_t *Z, const tt_opts *o, bool need_cores
   a.cap = (int)std::min<ll>(o->max_rank, hatt::kMaxSmall);
   a.tol = o->tol;
   a.seed = o->seed;
+  a.seed_offset = o->seed_offset;
   bool below = false;
   for (int k = 1; k < d; ++k) below = below || (o->max_rank > 0 && a.ell[k] > o->max_rank);
   a.trunc = d > 1 && (o->tol > 0.0 || below);
@@ -986,12 +989,19 @@ int eng_edge(int X, int cap) {
   return best;
 }
 
+// Tiles of bm x bn outputs; a task takes bgroup consecutive batch entries of
+// one tile position, enough for ~kTaskFma multiply-adds (the per-task queue
+// and wait overhead is a few microseconds).
+constexpr double kTaskFma = 131072.0;
+
 void eng_set_tiles(hatt::EngineStage &s, int bm, int bn) {
   s.bm = bm;
   s.bn = bn;
   s.tiles_m = (s.M + bm - 1) / bm;
   s.tiles_n = (s.N + bn - 1) / bn;
-  s.ntasks = s.tiles_m * s.tiles_n * s.batch;
+  const double work = (double)bm * bn * s.K;
+  s.bgroup = (int)std::min<double>(s.batch, std::max(1.0, std::ceil(kTaskFma / work)));
+  s.ntasks = s.tiles_m * s.tiles_n * ((s.batch + s.bgroup - 1) / s.bgroup);
 }
 
 // Candidate tile shapes (bm x bn <= 4096, each edge <= 128) for a GEMM.
@@ -1197,10 +1207,10 @@ void eng_order(tt_batch_plan &P) {
 
 // Autotuner: the tile shape of every engine GEMM stage, chosen by timing the
 // candidate shapes (engine_gemm_probe: all tiles of the stage as one grid) on
-// the first stage of each shape bucket -- operand dims rounded up to
-// multiples of 16, batch to a power of two, and the operand precision -- and
-// cached for the process. The cache can be saved and loaded as JSON lines
-// (tt_batched_tune_cache).
+// the first stage of each shape bucket -- M, N, K and the batch rounded up to
+// powers of two, and the operand precision -- and cached for the process.
+// GEMMs under 2e7 flops keep the analytic choice. The cache can be saved and
+// loaded as text lines (tt_batched_tune_cache).
 struct TuneKey {
   int prec, M, N, K, B;
   bool operator<(const TuneKey &o) const {
@@ -1211,15 +1221,14 @@ std::mutex g_tune_mu;
 std::map<TuneKey, std::pair<int, int>> g_tune;
 
 TuneKey tune_key(const hatt::EngineStage &s) {
-  auto r16 = [](int x) { return (x + 15) / 16 * 16; };
-  int b = 1;
-  while (b < s.batch) b <<= 1;
-  return {s.prec, r16(s.M), r16(s.N), r16(s.K), b};
+  auto p2 = [](int x) { int b = 1; while (b < x) b <<= 1; return b; };
+  return {s.prec, p2(s.M), p2(s.N), p2(s.K), p2(s.batch)};
 }
 
 int eng_autotune(std::vector<hatt::EngineStage> &stages, cudaStream_t st, int *tuned) {
   for (hatt::EngineStage &s : stages) {
     if (s.type != hatt::kStGemm) continue;
+    if (2.0 * s.M * (double)s.N * s.K * s.batch < 2e7) continue;   // small: analytic tiles
     const TuneKey key = tune_key(s);
     {
       std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -1340,7 +1349,8 @@ const char *tt_status_string(int status) {
     case TT_ERR_ARG: return "invalid argument (null pointer or option)";
     case TT_ERR_WORKSPACE: return "workspace too small or misaligned";
     case TT_ERR_CUDA: return "CUDA launch or copy failed";
-    case TT_ERR_NONFINITE: return "non-finite value";
+    case TT_ERR_NONFINITE: return "non-finite value in an input or an intermediate";
+    case TT_ERR_BREAKDOWN: return "QR breakdown: a shifted Cholesky pivot was not positive";
     case TT_ERR_TIMEOUT: return "a bounded device wait ran out";
     default: return "unknown status";
   }
@@ -1728,6 +1738,18 @@ int tt_device_error(int32_t *value) {
   return TT_OK;
 }
 
+int tt_device_status(int32_t *status) {
+  if (!status) return TT_ERR_ARG;
+  int32_t v = 0;
+  const int st = tt_device_error(&v);
+  if (st != TT_OK) return st;
+  *status = (v & hatt::kHealthTimeout)     ? TT_ERR_TIMEOUT
+            : (v & hatt::kHealthNonfinite) ? TT_ERR_NONFINITE
+            : (v & hatt::kHealthBreakdown) ? TT_ERR_BREAKDOWN
+                                           : TT_OK;
+  return TT_OK;
+}
+
 int tt_kernel_timer_start(int32_t capacity) {
   if (capacity < 1 || capacity > (1 << 20)) return TT_ERR_ARG;
   std::lock_guard<std::mutex> lk(hatt::g_timer.mu);
@@ -1804,7 +1826,7 @@ int tt_batched_plan_create(int32_t count, const tt_t *Y, const tt_t *Z, const tt
     if (st != TT_OK) return st;
     // the engine runs HaTT-1 in FP64 or with FP32 sketch products, and
     // without the truncation sweep (sketch rank = output rank)
-    if (ep.a.variant != 1 || ep.a.trunc) return TT_ERR_ARG;
+    if (ep.a.variant != 1 || ep.a.trunc || ep.a.seed_offset) return TT_ERR_ARG;
     if (opts[j].precision != TT_FP64 && opts[j].precision != TT_MIXED_FP32) return TT_ERR_ARG;
     if (!X[j].cores || !X[j].r || !X[j].n || X[j].d != Y[j].d) return TT_ERR_ARG;
     for (int k = 0; k < ep.a.d; ++k)
@@ -1922,7 +1944,10 @@ int tt_batched_status(tt_batch_plan *P, void *stream, int32_t *status) {
                                   (cudaStream_t)stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
   if (e != cudaSuccess) return from_cuda(e);
-  *status = (v & hatt::kEngineTimeout) ? TT_ERR_TIMEOUT : TT_OK;
+  *status = (v & hatt::kEngineTimeout)     ? TT_ERR_TIMEOUT
+            : (v & hatt::kEngineNonfinite) ? TT_ERR_NONFINITE
+            : (v & hatt::kEngineBreakdown) ? TT_ERR_BREAKDOWN
+                                           : TT_OK;
   return TT_OK;
 }
 

@@ -117,6 +117,13 @@ cudaError_t oz_error_word(int *value, bool clear);
 // device) and clear it.
 cudaError_t read_device_error(int *value);
 cudaError_t clear_device_error();
+// Health bits of the device error word (tt_device_error): a bounded wait ran
+// out, a non-finite value reached a norm or a Gram matrix, a shifted Cholesky
+// factorization still met a non-positive pivot. Each source file that sets a
+// bit owns its word; read_device_error ORs them.
+constexpr int kHealthTimeout = 1, kHealthNonfinite = 2, kHealthBreakdown = 4;
+cudaError_t qr_health_word(int *value, bool clear);
+cudaError_t misc_health_word(int *value, bool clear);
 // Enqueue; `scratch` must hold gemm_scratch_doubles(g) doubles.
 cudaError_t gemm_f64(const Gemm &g, double *scratch, cudaStream_t st);
 
@@ -124,6 +131,7 @@ cudaError_t gemm_f64(const Gemm &g, double *scratch, cudaStream_t st);
 struct SketchTable {
   int d;
   uint64_t seed;
+  const uint64_t *seed_offset = nullptr;   // device: key = seed + *seed_offset
   uint32_t pair;
   long long offset[kMaxOrder + 1];   // element offset of core k inside `base`
   int a[kMaxOrder], n[kMaxOrder], b[kMaxOrder];
@@ -186,6 +194,15 @@ cudaError_t trunc_step(double *Xk, int la, int n, int lb, double *Xkm1, int lm, 
 // stop its cluster levels early; the batched entry point switches it off for
 // the calling thread while it issues its lanes.
 void set_host_sync(bool allowed);
+// FP64 refinement of a start U (c x c, in place) of the eigenvectors of the
+// symmetric c x c matrix G in one launch on a thread-block cluster
+// (k_refine.cu), for c <= kEigFusedMax; *skip != 0 leaves U untouched.
+// refine_cluster_available says whether the device can place the cluster.
+constexpr int kEigFusedMax = 96;
+constexpr int kMaxDevices = 64;
+cudaError_t refine_cluster_available(bool *ok);
+cudaError_t refine_cluster(const double *G, int c, double *U, double floor_norm, const int *skip,
+                           cudaStream_t st);
 // Eigenvectors (columns of U, c x c row-major) of the symmetric c x c matrix G.
 size_t sym_eig_scratch_doubles(int c);
 cudaError_t sym_eig(const double *G, int c, double *U, double *scratch, cudaStream_t st);

@@ -60,16 +60,26 @@ __device__ void task_sketch(const EngineStage &s, int tile) {
 // to the threads (at most kMaxOut each). prec == kPrecFP32 rounds the operands
 // to FP32 and accumulates in FP32 (the low-precision sketch products).
 template <typename T>
+__device__ void gemm_tile_one(const EngineStage &s, int tm_i, int tn_i, int b, T *As, T *Bs);
+
+template <typename T>
 __device__ void gemm_tile_t(const EngineStage &s, int tile, double *smem) {
   if (s.skip_dev && __ldcg(s.skip_dev)) return;
   T *As = reinterpret_cast<T *>(smem);                     // kBK x (kMaxTile + 1)
   T *Bs = As + kBK * (kMaxTile + 1);
-  const int tid = threadIdx.x;
-  const int bm = s.bm, bn = s.bn;
   const int tn_i = tile % s.tiles_n;
   const int rest = tile / s.tiles_n;
   const int tm_i = rest % s.tiles_m;
-  const int b = rest / s.tiles_m;
+  const int bg = rest / s.tiles_m;
+  for (int b = bg * s.bgroup; b < min(s.batch, (bg + 1) * s.bgroup); ++b)
+    gemm_tile_one<T>(s, tm_i, tn_i, b, As, Bs);
+}
+
+// The tile (tm_i, tn_i) of batch entry b.
+template <typename T>
+__device__ void gemm_tile_one(const EngineStage &s, int tm_i, int tn_i, int b, T *As, T *Bs) {
+  const int tid = threadIdx.x;
+  const int bm = s.bm, bn = s.bn;
   const int b1 = b / s.bdiv, b2 = b % s.bdiv;
   const double *A = s.A + b1 * s.sA1 + b2 * s.sA2;
   const double *B = s.B + b1 * s.sB1 + b2 * s.sB2;
@@ -148,11 +158,14 @@ __device__ void task_norm_part(const EngineStage &s, int tile, double *red) {
   if (threadIdx.x == 0) s.part[tile] = acc;
 }
 
-__device__ void task_norm_fin(const EngineStage &s, double *red) {
+__device__ void task_norm_fin(const EngineStage &s, double *red, int *status) {
   double acc = 0.0;
   for (int i = threadIdx.x; i < (int)s.count; i += kT) acc += __ldcg(s.part + i);
   acc = block_sum(acc, red);
-  if (threadIdx.x == 0) s.out[0] = acc > 0.0 ? 1.0 / sqrt(acc) : 1.0;
+  if (threadIdx.x == 0) {
+    if (!isfinite(acc)) atomicOr(status, kEngineNonfinite);
+    s.out[0] = acc > 0.0 ? 1.0 / sqrt(acc) : 1.0;
+  }
 }
 
 // C[0, i, a s1 + b] = Y[0, i, a] Z[0, i, b]
@@ -183,7 +196,7 @@ __device__ __forceinline__ double rsqrt_nr(double x) {
   return ldexp(y, -e / 2);
 }
 
-__device__ void task_chol(const EngineStage &s, double *smem) {
+__device__ void task_chol(const EngineStage &s, double *smem, int *status) {
   int *flags = s.flags;
   __shared__ double s_dev, s_dmax, s_tr, s_rinv[kEngineMaxC];
   __shared__ int s_fail, s_done;
@@ -198,9 +211,11 @@ __device__ void task_chol(const EngineStage &s, double *smem) {
   double *G = smem;                                 // c x ld
   double *red = smem + c * ld;                      // kT / 32
   double dev = 0.0, dmax = 0.0, tr = 0.0;
+  int bad = 0;
   for (int e = tid; e < c * c; e += kT) {
     const int i = e / c, j = e % c;
     const double v = __ldcg(s.G + e);
+    bad |= !isfinite(v);
     G[i * ld + j] = v;
     if (i == j) {
       dmax = fmax(dmax, v);
@@ -209,6 +224,14 @@ __device__ void task_chol(const EngineStage &s, double *smem) {
     } else {
       dev = fmax(dev, fabs(v));
     }
+  }
+  if (__syncthreads_or(bad)) {                       // a non-finite Gram matrix
+    if (tid == 0) {
+      atomicOr(status, kEngineNonfinite);
+      flags[0] = 1;
+      flags[1] = 1;
+    }
+    return;
   }
   for (int o = 16; o > 0; o >>= 1) {
     dev = fmax(dev, __shfl_xor_sync(0xffffffffu, dev, o));
@@ -256,6 +279,7 @@ __device__ void task_chol(const EngineStage &s, double *smem) {
           piv = 1.0;                                // zero column: R_jj = 1, Q_j = 0
         } else if (!(piv > floor_piv)) {
           if (attempt == 0) s_fail = 1;
+          else atomicOr(status, kEngineBreakdown);
           piv = fmax(shift, 1e-300);
         }
         const double y = rsqrt_nr(piv);
@@ -318,14 +342,14 @@ __device__ void task_trsm(const EngineStage &s, int tile, double *smem) {
   }
 }
 
-__device__ void run_task(const EngineStage &s, int tile, double *smem, double *red) {
+__device__ void run_task(const EngineStage &s, int tile, double *smem, double *red, int *status) {
   switch (s.type) {
     case kStSketch: task_sketch(s, tile); break;
     case kStGemm: task_gemm(s, tile, smem); break;
     case kStNormPart: task_norm_part(s, tile, red); break;
-    case kStNormFin: task_norm_fin(s, red); break;
+    case kStNormFin: task_norm_fin(s, red, status); break;
     case kStPkpFirst: task_pkp_first(s, tile); break;
-    case kStChol: task_chol(s, smem); break;
+    case kStChol: task_chol(s, smem, status); break;
     case kStTrsm: task_trsm(s, tile, smem); break;
     case kStSet:
       if (threadIdx.x == 0) s.out[0] = s.value;
@@ -355,7 +379,7 @@ engine_kernel(const EngineStage *stages, const EngineTask *tasks, int ntasks, in
       volatile int *sp = status;
       long long polls = 0;
       while (*dp < task.need) {
-        if (*sp != 0 || ++polls > spin_cap) {
+        if ((*sp & kEngineTimeout) != 0 || ++polls > spin_cap) {
           atomicOr(status, kEngineTimeout);
           break;
         }
@@ -364,7 +388,7 @@ engine_kernel(const EngineStage *stages, const EngineTask *tasks, int ntasks, in
       __threadfence();
     }
     __syncthreads();
-    run_task(stages[task.stage], task.tile, smem, red);
+    run_task(stages[task.stage], task.tile, smem, red, status);
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) atomicAdd(done + task.pair, 1);
@@ -428,14 +452,14 @@ cudaError_t engine_gemm_time(const EngineStage &s, cudaStream_t st, float *ms) {
   if (e != cudaSuccess) { cudaEventDestroy(a); return e; }
   engine_gemm_probe<<<tiles, kT, engine_gemm_smem(), st>>>(s);      // warm-up
   cudaEventRecord(a, st);
-  for (int r = 0; r < 3; ++r) engine_gemm_probe<<<tiles, kT, engine_gemm_smem(), st>>>(s);
+  engine_gemm_probe<<<tiles, kT, engine_gemm_smem(), st>>>(s);
   cudaEventRecord(b, st);
   e = cudaEventSynchronize(b);
   float t = 0.0f;
   if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
   cudaEventDestroy(a);
   cudaEventDestroy(b);
-  *ms = t / 3.0f;
+  *ms = t;
   return e == cudaSuccess ? cudaGetLastError() : e;
 }
 

@@ -276,10 +276,12 @@ TcLaunch tc_plan(const Gemm &g) {
 }  // namespace
 
 cudaError_t read_device_error(int *value) {
-  int oz = 0;
+  int oz = 0, qr = 0, misc = 0;
   cudaError_t e = cudaMemcpyFromSymbol(value, g_device_error, sizeof(int));
   if (e == cudaSuccess) e = oz_error_word(&oz, false);
-  if (e == cudaSuccess) *value |= oz;
+  if (e == cudaSuccess) e = qr_health_word(&qr, false);
+  if (e == cudaSuccess) e = misc_health_word(&misc, false);
+  if (e == cudaSuccess) *value = (*value != 0 || oz != 0 ? kHealthTimeout : 0) | qr | misc;
   return e;
 }
 
@@ -288,6 +290,8 @@ cudaError_t clear_device_error() {
   int oz = 0;
   cudaError_t e = cudaMemcpyToSymbol(g_device_error, &zero, sizeof(int));
   if (e == cudaSuccess) e = oz_error_word(&oz, true);
+  if (e == cudaSuccess) e = qr_health_word(&oz, true);
+  if (e == cudaSuccess) e = misc_health_word(&oz, true);
   return e;
 }
 

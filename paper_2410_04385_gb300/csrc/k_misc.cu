@@ -6,6 +6,8 @@
 namespace hatt {
 namespace {
 
+__device__ int g_misc_health = 0;   // kHealthNonfinite: a non-finite ||W^{(k)}||
+
 constexpr int kThreads = 256;
 
 // Philox4x32-10 (Salmon et al., SC'11): multipliers and Weyl key increments.
@@ -47,8 +49,9 @@ __device__ __forceinline__ double sketch_gaussian(uint32_t flat, uint32_t core, 
 __global__ void __launch_bounds__(kThreads) sketch_kernel(SketchTable t, double *base) {
   pdl_enter();
   const long long total = t.offset[t.d];
-  const uint32_t k0 = (uint32_t)(t.seed & 0xFFFFFFFFull);
-  const uint32_t k1 = (uint32_t)(t.seed >> 32);
+  const uint64_t key = t.seed + (t.seed_offset ? *t.seed_offset : 0ull);
+  const uint32_t k0 = (uint32_t)(key & 0xFFFFFFFFull);
+  const uint32_t k1 = (uint32_t)(key >> 32);
   for (long long e = blockIdx.x * (long long)kThreads + threadIdx.x; e < total;
        e += (long long)gridDim.x * kThreads) {
     int lo = 0, hi = t.d - 1;            // core k with offset[k] <= e < offset[k+1]
@@ -123,6 +126,7 @@ inv_norm_kernel(const double *x, long long count, double *out, double *partials,
   }
   if (threadIdx.x == 0) {
     const double ss = red[0];
+    if (!isfinite(ss)) atomicOr(&g_misc_health, kHealthNonfinite);
     out[0] = ss > 0.0 ? 1.0 / sqrt(ss) : 1.0;
     *ticket = 0u;
   }
@@ -283,6 +287,15 @@ cudaError_t sqrt_scalar(const double *x, double *out, cudaStream_t st) {
   launch_k(sqrt_kernel, 1, 1, 0, st, x, out);
   note_launch();
   return cudaGetLastError();
+}
+
+cudaError_t misc_health_word(int *value, bool clear) {
+  cudaError_t e = cudaMemcpyFromSymbol(value, g_misc_health, sizeof(int));
+  if (e == cudaSuccess && clear && *value != 0) {
+    const int zero = 0;
+    e = cudaMemcpyToSymbol(g_misc_health, &zero, sizeof(int));
+  }
+  return e;
 }
 
 }  // namespace hatt

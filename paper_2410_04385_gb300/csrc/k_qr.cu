@@ -33,6 +33,8 @@
 namespace hatt {
 namespace {
 
+__device__ int g_qr_health = 0;   // kHealthNonfinite / kHealthBreakdown bits
+
 constexpr int kPasses = 6;
 constexpr int kCholThreads = 256;
 constexpr int kTrsmThreads = 256;
@@ -78,9 +80,11 @@ chol_inv_kernel(const double *Gg, double *Ut_g, double *y_g, int c, int m, int *
   // absolute on purpose: S of any scale (HaTT sketches of long chains reach
   // 1e-20 and below) is never mistaken for a converged basis.
   double dev = 0.0, dmax = 0.0, tr = 0.0;
+  int bad = 0;
   for (int e = tid; e < c * c; e += kCholThreads) {
     const int i = e / c, j = e % c;
     const double v = Gg[e];
+    bad |= !isfinite(v);
     G[i * ld + j] = v;
     if (i == j) {
       dmax = fmax(dmax, v);
@@ -89,6 +93,16 @@ chol_inv_kernel(const double *Gg, double *Ut_g, double *y_g, int c, int m, int *
     } else {
       dev = fmax(dev, fabs(v));
     }
+  }
+  // a non-finite Gram matrix (a non-finite input core or intermediate): record
+  // it, leave S as it is and stop this QR (every later pass is a no-op)
+  if (__syncthreads_or(bad)) {
+    if (tid == 0) {
+      atomicOr(&g_qr_health, kHealthNonfinite);
+      flags[0] = 1;
+      flags[1] = 1;
+    }
+    return;
   }
   {
     __shared__ double red[kCholThreads];
@@ -157,6 +171,7 @@ chol_inv_kernel(const double *Gg, double *Ut_g, double *y_g, int c, int m, int *
           piv = 1.0;
         } else if (!(piv > floor_piv)) {
           if (attempt == 0) s_fail = 1;
+          else atomicOr(&g_qr_health, kHealthBreakdown);   // shifted and still not positive
           piv = fmax(shift, 1e-300);          // shifted attempt: never divide by zero
         }
         const double y = rsqrt_newton(piv);
@@ -243,6 +258,15 @@ Gemm gram_desc(double *S, int m, int c, long long ldS, double *G, const int *fla
 }
 
 }  // namespace
+
+cudaError_t qr_health_word(int *value, bool clear) {
+  cudaError_t e = cudaMemcpyFromSymbol(value, g_qr_health, sizeof(int));
+  if (e == cudaSuccess && clear && *value != 0) {
+    const int zero = 0;
+    e = cudaMemcpyToSymbol(g_qr_health, &zero, sizeof(int));
+  }
+  return e;
+}
 
 size_t qr_scratch_doubles(int m, int c) {
   Gemm g = gram_desc(nullptr, m, c, c, nullptr, nullptr);

@@ -628,11 +628,15 @@ rank_kernel(const double *e, int c, int cap, const double *delta2, long long *ra
   pdl_enter();
   __shared__ double sorted[kMaxSmall];
   const int tid = threadIdx.x;
+  // sort key: the energy, or -1 when it is not finite (NaN compares false
+  // with everything, so without the key equal positions could repeat and
+  // perm would not be a permutation)
+  auto key = [&](int i) { const double v = e[i]; return isfinite(v) ? v : -1.0; };
   for (int i = tid; i < c; i += kThreads) {
-    const double ei = e[i];
+    const double ei = key(i);
     int pos = 0;
     for (int j = 0; j < c; ++j) {
-      const double ej = e[j];
+      const double ej = key(j);
       pos += (ej > ei) || (ej == ei && j < i);
     }
     perm[pos] = i;
@@ -818,6 +822,11 @@ static cudaError_t eigvecs(const double *A, int c, double *Ua, double *Ub, doubl
   launch_k(eig_tridiag32_kernel, 1, kEigThreads, eig_smem(c), st, A, c, Ua, state);
   note_launch();
   HATT_TRY(cudaGetLastError());
+  if (c <= kEigFusedMax) {          // all refinement steps in one cluster launch
+    bool ok = false;
+    HATT_TRY(refine_cluster_available(&ok));
+    if (ok) return refine_cluster(A, c, Ua, floor_norm, state, st);
+  }
   double *U = Ua, *Un = Ub;
   for (int it = 0; it < kEigSteps; ++it) {
     const int orth_only = (it >= kRefineSteps);   // closing steps: orthonormalize only

@@ -210,9 +210,9 @@ def workload_batch_uneven(count: int = 256, seed: int = 7, d_range=(10, 40), n_c
                           r_range=(8, 48)):
     """Many independent pairs of uneven order, mode size and rank: per pair
     d uniform in d_range, one mode size from n_choices, every inner rank of
-    Y and of Z uniform in r_range, Gaussian cores; target rank
-    2 max(r_Y, r_Z) (capped at 118 so that the oversampled sketch stays within
-    the 128 of the small factorizations). Returns a list of (Y, Z, opts)."""
+    Y and of Z uniform in r_range, Gaussian cores; sketch rank = target rank
+    = 2 max(r_Y, r_Z) (clamped by the plan to the PKP ranks and unfolding
+    sizes), so no truncation sweep follows. Returns a list of (Y, Z, opts)."""
     rng = np.random.default_rng(seed)
     pairs = []
     for j in range(count):
@@ -222,8 +222,8 @@ def workload_batch_uneven(count: int = 256, seed: int = 7, d_range=(10, 40), n_c
         rz = [1] + [int(v) for v in rng.integers(r_range[0], r_range[1] + 1, size=d - 1)] + [1]
         Y = gaussian_tt([n] * d, ry, int(rng.integers(1 << 30)))
         Z = gaussian_tt([n] * d, rz, int(rng.integers(1 << 30)))
-        target = min(2 * max(max(ry), max(rz)), 118)
-        pairs.append((Y, Z, dict(max_rank=target, oversample=10)))
+        target = 2 * max(max(ry), max(rz))
+        pairs.append((Y, Z, dict(sketch_rank=target, max_rank=target, oversample=0)))
     return pairs
 
 

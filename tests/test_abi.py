@@ -43,7 +43,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_status_strings(lib):
-    for st in range(0, 7):
+    for st in range(0, 9):
         assert len(B.status_string(st)) > 0
     assert B.status_string(99) == "unknown status"
 

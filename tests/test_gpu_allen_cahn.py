@@ -169,3 +169,90 @@ def test_fixed_rank_graph_full_configuration(B):
     assert all(np.isfinite(energies))
     assert all(b <= a * (1 + 1e-9) for a, b in zip(energies, energies[1:]))
     assert B.device_error() == 0
+
+
+def test_fresh_seeds_per_replay_match_the_oracle(B):
+    """With fresh_seeds the graph draws new sketches every replay: five steps
+    (the warm-up step and four replays) against five oracle steps whose sketch
+    seeds advance by two per step."""
+    from paper_2410_04385_gb300 import allen_cahn as ac
+    d, n, eps, dt = 3, 8, 0.1, 1e-3
+    h = 2 * np.pi / n
+    u0 = _pad_np(oac.initial_condition(d, n, seed=3), 8)
+    st = ac.FixedRankStepper(to_gpu(u0), h, eps, dt, rank=8, tol=1e-12, hatt_tol=0.0,
+                             hatt_rank=8, seed=100, fresh_seeds=True)
+    st.capture()
+    for _ in range(4):
+        st.replay()
+    torch.cuda.synchronize()
+    assert int(st.seed_counter.item()) == 10
+    u = u0
+    for w in range(5):
+        u, _ = oac.step(u, h, eps, dt, max_rank=8, tol=1e-12, hatt_tol=0.0, seed=100 + 2 * w)
+        u = _pad_np(u, 8)
+    assert ott.tt_diff_norm(to_np(st.u), u) <= 1e-10 * ott.tt_norm(u)
+    # the same run with fixed seeds differs: the replays did draw new sketches
+    st2 = ac.FixedRankStepper(to_gpu(u0), h, eps, dt, rank=8, tol=1e-12, hatt_tol=0.0,
+                              hatt_rank=8, seed=100)
+    st2.capture()
+    for _ in range(4):
+        st2.replay()
+    torch.cuda.synchronize()
+    assert st2.seed_counter is None
+
+
+GOLDEN_AC = os.path.join(os.path.dirname(__file__), "golden", "allen_cahn_oracle_samples.npz")
+
+
+def _sampled(cores, idx):
+    ix = torch.from_numpy(idx.astype(np.int64)).cuda()
+    M = torch.ones((idx.shape[0], 1), dtype=torch.float64, device="cuda")
+    for k, c in enumerate(cores):
+        M = torch.bmm(M.unsqueeze(1), c[:, ix[:, k], :].permute(1, 0, 2)).squeeze(1)
+    return M[:, 0].cpu().numpy()
+
+
+def test_full_configuration_100_graph_steps_against_the_oracle(B):
+    """d = 8, n = 64, rank 24, fresh sketches every replay: after 100 steps
+    (the warm-up step and 99 replays) the state agrees with the oracle's on
+    4000 sampled entries, and the energies every 10 steps, within the
+    resolution bound of the truncations at the binding rank cap
+    (ac_resolution_bound)."""
+    from paper_2410_04385_gb300 import allen_cahn as ac
+    gold = dict(np.load(GOLDEN_AC))
+    d, n, eps, dt = 8, 64, 0.1, 1e-3
+    h = 2 * np.pi / n
+    st = ac.FixedRankStepper(to_gpu(oac.initial_condition(d, n, seed=0)), h, eps, dt, rank=24,
+                             tol=1e-8, hatt_tol=1e-10, hatt_rank=24, seed=10, fresh_seeds=True)
+    st.capture()
+    energies = []
+    for w in range(1, int(gold["steps"])):
+        st.replay()
+        if w % 10 == 9:
+            torch.cuda.synchronize()
+            energies.append(st.energy())
+    torch.cuda.synchronize()
+    assert B.device_error() == 0
+    x, ref = _sampled(st.u, gold["idx"]), gold["u"]
+    err = float(np.linalg.norm(x - ref) / np.linalg.norm(ref))
+    bound = ac_resolution_bound(gold)
+    assert err <= bound, (err, bound)
+    e_ref = gold["energy_every_10"]
+    assert np.allclose(energies, e_ref, rtol=4.0 * bound, atol=0.0), (energies, e_ref)
+
+
+def ac_resolution_bound(gold):
+    """Every step truncates three times at the binding rank-24 cap (u^2, u^3
+    and the rounding). A Gram-based truncation resolves the kept subspace of
+    a bond to about c u sigma_1^2 / (sigma_rho^2 - sigma_{rho+1}^2) (c the rank
+    there), which moves the truncated tensor by that angle times sigma_rho;
+    the explicit Euler map grows a perturbation by at most 1 + dt + O(dt) per
+    step. With the stored spectra of the rounded tensors (the HaTT outputs
+    taken as no worse): 10 * 3 * sum over steps and bonds of the angle times
+    sigma_rho / ||w||."""
+    u = 1.1102230246251565e-16
+    cut = gold["cut"]                   # steps x bonds x (s1, s_rho, s_rho+1, c, ||w||)
+    s1, sr, sr1, c, nw = (cut[..., i] for i in range(5))
+    gap = np.maximum(sr ** 2 - sr1 ** 2, 1e-300)
+    eps_step = np.sum(c * u * s1 ** 2 / gap * sr / nw, axis=1)
+    return float(10.0 * 3.0 * np.sum(eps_step) * np.exp(1.2 * 1e-3 * len(eps_step)))

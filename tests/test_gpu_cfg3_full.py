@@ -6,7 +6,19 @@ The oracle needs about 100 s per format at this size, so its results enter as
 entries at 4000 seeded multi-indices, written by tests/golden/make_cfg3_oracle.py
 (oracle only). The GPU result is sampled at the same indices on the device.
 
-  * FP64: relative difference to the FP64 oracle on the samples <= 1e-12.
+  * FP64 without the truncation sweep (sketch rank 90 kept), the HaTT path
+    itself: relative difference to the oracle on the samples <= 1e-12, or 10
+    times the difference between the oracle's own two codings of HPCRL-1 on
+    the same sketch, whichever is larger (the rounding sensitivity of this
+    ill-conditioned sketch; see the test).
+  * FP64 with the truncation to rank 80: the truncation (not in the paper)
+    finds the kept singular subspace from the Gram matrix of each core, which
+    resolves it to about c u sigma_1^2 / (sigma_rho^2 - sigma_{rho+1}^2) per
+    bond (c the sketch rank there); with the bond singular values the oracle
+    stored, the difference to the oracle's SVD-based truncation must stay
+    within 10 times sum_k that angle times sigma_rho / ||X||. (At this cut,
+    sigma_80 / sigma_1 ~ 1e-4 and neighbouring singular values lie within a
+    factor 1.02-1.3 of each other, so the bound is ~1e-8, not 1e-12.)
   * FP32 / TF32 / BF16 sketch products (reading C6): the error against the
     exact product Y * Z stays within reading C7's bound
     10 * max(error of the FP64 oracle, error of the oracle emulating the
@@ -73,7 +85,22 @@ def test_full_size_smooth_d50_against_the_fp64_oracle(B, case, prec):
     d64 = rel(x, gold["x_fp64"])
     if prec == 0:
         assert [int(c.shape[0]) for c in X] + [1] == [int(v) for v in gold["ranks_fp64"]]
-        assert d64 <= 1e-12, d64
+        u = 1.1102230246251565e-16
+        s1, cut, c = gold["sv_first"], gold["sv_cut"], gold["ell_bond"]
+        gap = np.maximum(cut[:, 0] ** 2 - cut[:, 1] ** 2, 1e-300)
+        bound = 10.0 * float(np.sum(c * u * s1 ** 2 / gap * cut[:, 0])) / float(gold["norm_notrunc"])
+        assert d64 <= bound, (d64, bound)
+        Xu = B.tt_hadamard_recompress(Yg, Zg, seed=SKETCH_SEED, sketch_rank=opts["sketch_rank"])
+        torch.cuda.synchronize()
+        xu = sampled(Xu, gold["idx"])
+        assert [int(c.shape[0]) for c in Xu] + [1] == [int(v) for v in gold["ranks_fp64_notrunc"]]
+        # the sketch matrices of this smooth product are ill-conditioned (the
+        # unfolding spectra decay to ~1e-5 of sigma_1 within the sketch rank),
+        # so the range finder's output moves with the rounding of W itself: the
+        # oracle's two codings of the same sketch differ by `sens`; the GPU is
+        # held to 1e-12 or 10 sens, whichever is larger
+        sens = rel(gold["x_fp64_notrunc_paper"], gold["x_fp64_notrunc"])
+        assert rel(xu, gold["x_fp64_notrunc"]) <= max(1e-12, 10.0 * sens), sens
         return
     tol = opts["tol"]
     e_gpu = rel(x, exact)

@@ -81,3 +81,14 @@ def test_left_orthogonalize():
     assert tt.is_left_orthogonal(L, atol=1e-13)
     assert np.allclose(tt.tt_full(L), tt.tt_full(Y), atol=1e-13)
     assert np.isclose(np.linalg.norm(L[-1]), np.linalg.norm(tt.tt_full(Y)), rtol=1e-13)
+
+
+def test_bond_singular_values_equal_those_of_the_dense_unfoldings():
+    A = wl.gaussian_tt([3, 4, 5, 3], [1, 2, 6, 3, 1], 5)
+    full = tt.tt_full(A)
+    sv = tt.bond_singular_values(A)
+    for k in range(1, 4):
+        dense = np.linalg.svd(full.reshape(int(np.prod(full.shape[:k])), -1), compute_uv=False)
+        m = len(sv[k - 1])
+        assert np.allclose(sv[k - 1], dense[:m], rtol=1e-12, atol=1e-14 * dense[0])
+        assert np.all(dense[m:] <= 1e-12 * dense[0])
