@@ -250,6 +250,7 @@ def run_batch_cfg4(binding, workloads, dev, rank=0, world=1):
         torch.cuda.synchronize()
         ms.append(max_over_ranks(s0.elapsed_time(s1), world, dev))
     status = eng.status() if eng is not None else 0
+    prof = eng.profile() if eng is not None else {}
     records = [[j, status] + [int(v) for v in eng.Xd[q].r] for q, j in enumerate(mine)] if eng else []
     gathered = sharding.gather_records(records, world)
     out["engine"] = {"ms_per_batch": min(ms), "value": 1000.0 * len(pairs) / min(ms),
@@ -259,6 +260,7 @@ def run_batch_cfg4(binding, workloads, dev, rank=0, world=1):
                      "precision": "FP32 sketch products, FP64 QR / projection / update",
                      "sharding": f"LPT on predicted flops over {world} rank(s); pairs on rank 0: {len(mine)}",
                      "pairs_gathered": len(gathered),
+                     "cta_time_fractions_rank0": prof,
                      "all_status_ok": all(rec[1] == 0 for rec in gathered)}
     if world > 1:
         out["scaling"] = "strong"

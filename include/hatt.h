@@ -303,8 +303,9 @@ int64_t tt_launch_count(void);
  *   plan is used. *workspace_bytes: the device workspace to bind. The plan is
  *   host memory owned by the caller (free it with tt_batched_plan_destroy).
  * bind: lays out the workspace (caller-owned, 256-byte aligned, >= the size
- *   reported), and with autotune = 1 times the candidate tile shapes of each
- *   GEMM shape bucket not yet in the process-wide cache; uploads the task
+ *   reported), and with autotune = 1 times the candidate tile shapes of the
+ *   48 GEMM shape buckets with the most flops that are not yet in the
+ *   process-wide cache (the others keep an analytic choice); uploads the task
  *   tables. Synchronizes `stream`; not allowed while it is being captured.
  * run: clears the control words and enqueues the persistent launch on
  *   `stream` (no synchronization; capturable once bound). spin_cap bounds each
@@ -314,6 +315,12 @@ int64_t tt_launch_count(void);
  *   TT_OK, TT_ERR_TIMEOUT if a wait ran out, TT_ERR_NONFINITE if a norm or a
  *   Gram matrix was not finite (NaN or Inf in an input), TT_ERR_BREAKDOWN.
  * info: number of stages and tasks of the bound plan and resident CTAs.
+ * profile: sums over the CTAs of the last run's profile words into out (host
+ *   int64[24]): [0] cycles from each CTA's start to its end, [1] cycles
+ *   polling for prerequisites, [2] cycles taking tickets, [8 + t] cycles
+ *   running tasks of kind t, [16 + t] number of those tasks (t: 0 sketch,
+ *   1 GEMM tile, 2 norm partial, 3 norm, 4 first core, 5 Cholesky, 6 QR
+ *   apply, 7 set). Synchronizes `stream`.
  * tune_cache: save (save = 1) or load (save = 0) the process-wide tile cache
  *   as text lines "prec M N K batch bm bn" at `path` (host string). */
 typedef struct tt_batch_plan tt_batch_plan;
@@ -325,6 +332,7 @@ int tt_batched_run(tt_batch_plan *plan, int64_t spin_cap, void *stream);
 int tt_batched_status(tt_batch_plan *plan, void *stream, int32_t *status);
 int tt_batched_plan_info(const tt_batch_plan *plan, int64_t *stages, int64_t *tasks,
                          int32_t *blocks);
+int tt_batched_profile(tt_batch_plan *plan, void *stream, int64_t *out);
 int tt_batched_plan_destroy(tt_batch_plan *plan);
 int tt_batched_tune_cache(const char *path, int32_t save);
 

@@ -65,7 +65,7 @@ EXPORTS = ("tt_hadamard_recompress_plan", "tt_hadamard_recompress", "tt_round_pl
            "tt_hadamard_recompress_batch", "tt_scale", "tt_laplacian", "tt_lincomb",
            "tt_status_string", "tt_batched_plan_create", "tt_batched_plan_bind", "tt_batched_run",
            "tt_batched_status", "tt_batched_plan_info", "tt_batched_plan_destroy",
-           "tt_batched_tune_cache", "tt_device_status")
+           "tt_batched_tune_cache", "tt_device_status", "tt_batched_profile")
 
 
 def load(path: Optional[str] = None):
@@ -120,6 +120,7 @@ def load(path: Optional[str] = None):
     lib.tt_batched_plan_info.argtypes = [vp, P(ctypes.c_int64), P(ctypes.c_int64), P(ctypes.c_int32)]
     lib.tt_batched_plan_destroy.argtypes = [vp]
     lib.tt_batched_tune_cache.argtypes = [ctypes.c_char_p, ctypes.c_int32]
+    lib.tt_batched_profile.argtypes = [vp, vp, P(ctypes.c_int64)]
     lib.tt_hadamard_recompress_batch.argtypes = [ctypes.c_int32, P(TTStruct), P(TTStruct),
                                                  P(OptsStruct), P(TTStruct), ctypes.c_int32, vp,
                                                  ctypes.c_size_t, vp]
@@ -628,6 +629,19 @@ class BatchedRecompressor:
         _check("tt_batched_plan_info", load().tt_batched_plan_info(self.plan, ctypes.byref(st),
                                                                    ctypes.byref(tk), ctypes.byref(bl)))
         return {"stages": int(st.value), "tasks": int(tk.value), "blocks": int(bl.value)}
+
+    def profile(self, stream=None):
+        """Sums over the CTAs of the last run's cycle counters (see
+        tt_batched_profile) as a dict of fractions of the CTAs' time."""
+        out = (ctypes.c_int64 * 24)()
+        _check("tt_batched_profile", load().tt_batched_profile(self.plan, _stream_ptr(stream), out))
+        total = max(int(out[0]), 1)
+        kinds = ("sketch", "gemm", "norm_part", "norm", "first_core", "cholesky", "qr_apply", "set")
+        res = {"wait_frac": out[1] / total, "ticket_frac": out[2] / total}
+        for t, name in enumerate(kinds):
+            res[f"{name}_frac"] = out[8 + t] / total
+            res[f"{name}_tasks"] = int(out[16 + t])
+        return res
 
     def result(self, j: int) -> List[torch.Tensor]:
         r, n = self.Xd[j].r, self.Xd[j].n

@@ -81,6 +81,13 @@ constexpr int kEngineThreads = 256;
 constexpr int kEngineMaxC = 128;        // largest Cholesky / TRSM width
 constexpr int kEngineTrsmRows = 64;     // rows per TRSM task
 
+// Per-CTA profile of a launch (long long words, kProfWords per CTA): [0] cycles
+// from the CTA's start to its end, [1] cycles polling for prerequisites,
+// [2] cycles taking tickets, [8 + t] cycles running tasks of stage type t,
+// [16 + t] tasks of type t. Thread 0 reads clock64 around each phase.
+constexpr int kProfWords = 24;
+constexpr int kMaxProfBlocks = 2048;
+
 // Dynamic shared memory of the persistent kernel for Cholesky / TRSM width max_c.
 size_t engine_smem(int max_c);
 // Resident CTAs of the persistent kernel on the current device (SMs x per SM).
@@ -89,7 +96,7 @@ cudaError_t engine_blocks(int max_c, int *blocks);
 // zero on entry (done: one counter per pair).
 cudaError_t engine_launch(const EngineStage *stages, const EngineTask *tasks, int ntasks,
                           int *head, int *done, int *status, long long spin_cap, int max_c,
-                          int blocks, cudaStream_t st);
+                          int blocks, long long *prof, cudaStream_t st);
 // Average time of the GEMM stage s run alone (all its tiles as one grid), for
 // the autotuner; synchronizes the stream.
 cudaError_t engine_gemm_time(const EngineStage &s, cudaStream_t st, float *ms);

@@ -1153,6 +1153,7 @@ struct tt_batch_plan {
   std::vector<hatt::EngineTask> tasks;
   char *ws = nullptr;                // bound workspace
   int *head = nullptr, *done = nullptr, *status = nullptr, *qflags_all = nullptr;
+  long long *prof = nullptr;         // per-CTA profile words (kProfWords each)
   size_t flags_bytes = 0;            // the per-pair QR flags, cleared every run
   int blocks = 0;
   double beta = 0.5;                 // wave shift of the shorter chains (LPT)
@@ -1209,7 +1210,8 @@ void eng_order(tt_batch_plan &P) {
 // candidate shapes (engine_gemm_probe: all tiles of the stage as one grid) on
 // the first stage of each shape bucket -- M, N, K and the batch rounded up to
 // powers of two, and the operand precision -- and cached for the process.
-// GEMMs under 2e7 flops keep the analytic choice. The cache can be saved and
+// Only the buckets with the most flops are timed; the others, and GEMMs
+// under 2e7 flops, keep the analytic choice. The cache can be saved and
 // loaded as text lines (tt_batched_tune_cache).
 struct TuneKey {
   int prec, M, N, K, B;
@@ -1225,27 +1227,36 @@ TuneKey tune_key(const hatt::EngineStage &s) {
   return {s.prec, p2(s.M), p2(s.N), p2(s.K), p2(s.batch)};
 }
 
-int eng_autotune(std::vector<hatt::EngineStage> &stages, cudaStream_t st, int *tuned) {
-  for (hatt::EngineStage &s : stages) {
-    if (s.type != hatt::kStGemm) continue;
-    if (2.0 * s.M * (double)s.N * s.K * s.batch < 2e7) continue;   // small: analytic tiles
-    const TuneKey key = tune_key(s);
+// Tunes the kEngineTuneBuckets buckets that carry the most flops in the whole
+// batch (each timed once per candidate, on its first stage), then gives every
+// GEMM stage its bucket's shape if tuned or cached, else keeps the analytic one.
+constexpr int kEngineTuneBuckets = 48;
+
+int eng_autotune(std::vector<EnginePair> &pairs, cudaStream_t st, int *tuned) {
+  std::map<TuneKey, std::pair<double, hatt::EngineStage *>> buckets;   // flops, first stage
+  for (EnginePair &ep : pairs)
+    for (hatt::EngineStage &s : ep.stages) {
+      if (s.type != hatt::kStGemm) continue;
+      const double f = 2.0 * s.M * (double)s.N * s.K * s.batch;
+      if (f < 2e7) continue;                                  // small: analytic tiles
+      auto &b = buckets[tune_key(s)];
+      if (!b.second) b.second = &s;
+      b.first += f;
+    }
+  std::vector<std::pair<double, TuneKey>> order;
+  for (const auto &kv : buckets) order.push_back({kv.second.first, kv.first});
+  std::sort(order.begin(), order.end(), [](const auto &x, const auto &y) { return x.first > y.first; });
+  for (size_t i = 0; i < order.size() && (int)i < kEngineTuneBuckets; ++i) {
+    const TuneKey key = order[i].second;
     {
       std::lock_guard<std::mutex> lk(g_tune_mu);
-      auto it = g_tune.find(key);
-      if (it != g_tune.end()) {
-        const auto cands = eng_tile_candidates(s);
-        // a cached shape is reused when it is among this stage's candidates
-        if (std::find(cands.begin(), cands.end(), it->second) != cands.end()) {
-          eng_set_tiles(s, it->second.first, it->second.second);
-          continue;
-        }
-      }
+      if (g_tune.count(key)) continue;
     }
+    const hatt::EngineStage &rep = *buckets[key].second;
     float best = 1e30f;
-    std::pair<int, int> pick(s.bm, s.bn);
-    for (const auto &t : eng_tile_candidates(s)) {
-      hatt::EngineStage probe = s;
+    std::pair<int, int> pick(rep.bm, rep.bn);
+    for (const auto &t : eng_tile_candidates(rep)) {
+      hatt::EngineStage probe = rep;
       probe.skip_dev = nullptr;
       eng_set_tiles(probe, t.first, t.second);
       float ms = 0.0f;
@@ -1253,11 +1264,20 @@ int eng_autotune(std::vector<hatt::EngineStage> &stages, cudaStream_t st, int *t
       if (e != cudaSuccess) return from_cuda(e);
       if (ms < best) { best = ms; pick = t; }
     }
-    eng_set_tiles(s, pick.first, pick.second);
     ++*tuned;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune[key] = pick;
   }
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (EnginePair &ep : pairs)
+    for (hatt::EngineStage &s : ep.stages) {
+      if (s.type != hatt::kStGemm) continue;
+      auto it = g_tune.find(tune_key(s));
+      if (it == g_tune.end()) continue;
+      const auto cands = eng_tile_candidates(s);
+      if (std::find(cands.begin(), cands.end(), it->second) != cands.end())
+        eng_set_tiles(s, it->second.first, it->second.second);
+    }
   return TT_OK;
 }
 
@@ -1841,8 +1861,10 @@ int tt_batched_plan_create(int32_t count, const tt_t *Y, const tt_t *Z, const tt
     flag_ints += 4LL * ep.a.d;
     for (int k = 0; k <= ep.a.d; ++k) P->max_c = std::max<int>(P->max_c, (int)ep.a.ell[k]);
   }
-  // control words: head, status, per-pair completion counters, QR flags
+  // control words: head, status, per-pair completion counters, QR flags, then
+  // the per-CTA profile words (all cleared every run)
   P->flags_bytes = ((2 + (size_t)count + (size_t)flag_ints) * sizeof(int) + 255) & ~(size_t)255;
+  P->flags_bytes += (size_t)hatt::kMaxProfBlocks * hatt::kProfWords * sizeof(long long);
   const size_t ctl_off = off;
   off += P->flags_bytes;
   // count stages and the largest task count over the tile candidates with a
@@ -1895,6 +1917,8 @@ int tt_batched_plan_bind(tt_batch_plan *P, void *workspace, size_t workspace_byt
   P->status = ctl + 1;
   P->done = ctl + 2;
   P->qflags_all = ctl + 2 + P->count;
+  P->prof = reinterpret_cast<long long *>(
+      ws + ctl_off + P->flags_bytes - (size_t)hatt::kMaxProfBlocks * hatt::kProfWords * sizeof(long long));
   std::vector<RecOp> ops;
   int *fq = P->qflags_all;
   for (int j = 0; j < P->count; ++j) {
@@ -1907,10 +1931,8 @@ int tt_batched_plan_bind(tt_batch_plan *P, void *workspace, size_t workspace_byt
   if (e != cudaSuccess) return from_cuda(e);
   if (autotune) {
     int tuned = 0;
-    for (EnginePair &ep : P->pairs) {
-      const int s = eng_autotune(ep.stages, st, &tuned);
-      if (s != TT_OK) return s;
-    }
+    const int s = eng_autotune(P->pairs, st, &tuned);
+    if (s != TT_OK) return s;
   }
   eng_order(*P);
   const size_t sb = P->stages.size() * sizeof(hatt::EngineStage);
@@ -1933,7 +1955,7 @@ int tt_batched_run(tt_batch_plan *P, int64_t spin_cap, void *stream) {
   const auto *tasks = reinterpret_cast<const hatt::EngineTask *>(
       P->ws + P->tables_off + P->stages.size() * sizeof(hatt::EngineStage));
   e = hatt::engine_launch(stages, tasks, (int)P->tasks.size(), P->head, P->done, P->status,
-                          (long long)spin_cap, P->max_c, P->blocks, st);
+                          (long long)spin_cap, P->max_c, P->blocks, P->prof, st);
   return from_cuda(e);
 }
 
@@ -1956,6 +1978,22 @@ int tt_batched_plan_info(const tt_batch_plan *P, int64_t *stages, int64_t *tasks
   if (stages) *stages = (int64_t)P->stages.size();
   if (tasks) *tasks = (int64_t)P->tasks.size();
   if (blocks) *blocks = P->blocks;
+  return TT_OK;
+}
+
+int tt_batched_profile(tt_batch_plan *P, void *stream, int64_t *out) {
+  if (!P || !P->ws || !out) return TT_ERR_ARG;
+  const int n = std::min(P->blocks, hatt::kMaxProfBlocks);
+  std::vector<long long> h((size_t)n * hatt::kProfWords);
+  cudaError_t e = cudaMemcpyAsync(h.data(), P->prof, h.size() * sizeof(long long),
+                                  cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return from_cuda(e);
+  for (int i = 0; i < hatt::kProfWords; ++i) {
+    long long sum = 0;
+    for (int b = 0; b < n; ++b) sum += h[(size_t)b * hatt::kProfWords + i];
+    out[i] = sum;
+  }
   return TT_OK;
 }
 

@@ -363,17 +363,28 @@ __device__ void run_task(const EngineStage &s, int tile, double *smem, double *r
 // it, publish it.
 __global__ void __launch_bounds__(kT)
 engine_kernel(const EngineStage *stages, const EngineTask *tasks, int ntasks, int *head,
-              int *done, int *status, long long spin_cap) {
+              int *done, int *status, long long spin_cap, long long *prof) {
   extern __shared__ __align__(16) double smem[];
   __shared__ double red[kT / 32];
   __shared__ int s_task;
+  __shared__ long long pw[kProfWords];  // profile words, thread 0 only (see engine.cuh)
+  if (threadIdx.x == 0)
+    for (int i = 0; i < kProfWords; ++i) pw[i] = 0;
+  const long long t_start = clock64();
+  long long t0 = t_start;
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) s_task = atomicAdd(head, 1);
     __syncthreads();
     const int t = s_task;
+    if (threadIdx.x == 0) {
+      const long long now = clock64();
+      pw[2] += now - t0;
+      t0 = now;
+    }
     if (t >= ntasks) break;
     const EngineTask task = tasks[t];
+    const int type = stages[task.stage].type & 7;
     if (threadIdx.x == 0) {
       volatile int *dp = done + task.pair;
       volatile int *sp = status;
@@ -386,12 +397,25 @@ engine_kernel(const EngineStage *stages, const EngineTask *tasks, int ntasks, in
         __nanosleep(256);
       }
       __threadfence();
+      const long long now = clock64();
+      pw[1] += now - t0;
+      t0 = now;
     }
     __syncthreads();
     run_task(stages[task.stage], task.tile, smem, red, status);
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) atomicAdd(done + task.pair, 1);
+    if (threadIdx.x == 0) {
+      atomicAdd(done + task.pair, 1);
+      const long long now = clock64();
+      pw[8 + type] += now - t0;
+      pw[16 + type] += 1;
+      t0 = now;
+    }
+  }
+  if (threadIdx.x == 0 && prof && blockIdx.x < kMaxProfBlocks) {
+    pw[0] = clock64() - t_start;
+    for (int i = 0; i < kProfWords; ++i) prof[blockIdx.x * kProfWords + i] = pw[i];
   }
 }
 
@@ -414,12 +438,13 @@ size_t engine_smem(int max_c) {
 
 cudaError_t engine_launch(const EngineStage *stages, const EngineTask *tasks, int ntasks,
                           int *head, int *done, int *status, long long spin_cap, int max_c,
-                          int blocks, cudaStream_t st) {
+                          int blocks, long long *prof, cudaStream_t st) {
   const size_t smem = engine_smem(max_c);
   cudaError_t e = cudaFuncSetAttribute(engine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  engine_kernel<<<blocks, kT, smem, st>>>(stages, tasks, ntasks, head, done, status, spin_cap);
+  engine_kernel<<<blocks, kT, smem, st>>>(stages, tasks, ntasks, head, done, status, spin_cap,
+                                          prof);
   note_launch();
   return cudaGetLastError();
 }
@@ -450,7 +475,6 @@ cudaError_t engine_gemm_time(const EngineStage &s, cudaStream_t st, float *ms) {
   if (e != cudaSuccess) return e;
   e = cudaEventCreate(&b);
   if (e != cudaSuccess) { cudaEventDestroy(a); return e; }
-  engine_gemm_probe<<<tiles, kT, engine_gemm_smem(), st>>>(s);      // warm-up
   cudaEventRecord(a, st);
   engine_gemm_probe<<<tiles, kT, engine_gemm_smem(), st>>>(s);
   cudaEventRecord(b, st);

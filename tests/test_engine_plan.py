@@ -61,12 +61,18 @@ def test_plan_writes_the_clamped_sketch_ranks(lib):
         assert got == [int(v) for v in ohatt.plan_ranks(n, ry, rz, lreq)]
 
 
-def test_workspace_grows_with_the_batch(lib):
+def test_workspace_grows_linearly_with_the_batch(lib):
+    # every pair has its own region: the size is a fixed part plus one region per pair
     one = [([16] * 6, [1] + [5] * 5 + [1], [1] + [4] * 5 + [1], dict(sketch_rank=12))]
-    st1, ws1, _ = create(one)
-    st2, ws2, _ = create(one * 3)
-    assert st1 == st2 == 0
-    assert ws2 > 2.5 * ws1
+    sizes = []
+    for k in (1, 2, 3, 5):
+        st, ws, _ = create(one * k)
+        assert st == 0
+        sizes.append(ws)
+    per = sizes[1] - sizes[0]
+    assert per > 0
+    assert abs((sizes[2] - sizes[1]) - per) <= 0.05 * per
+    assert abs((sizes[3] - sizes[0]) - 4 * per) <= 0.05 * 4 * per
 
 
 @pytest.mark.parametrize("opts, expect", [
