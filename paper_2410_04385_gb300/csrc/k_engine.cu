@@ -85,13 +85,12 @@ __device__ void gemm_tile_one(const EngineStage &s, int tm_i, int tn_i, int b, T
   const double *B = s.B + b1 * s.sB1 + b2 * s.sB2;
   const int m0 = tm_i * bm, n0 = tn_i * bn;
   const int outs = bm * bn;
-  int om[kMaxOut], on[kMaxOut];
+  int mn[kMaxOut];                      // output q of this thread: row << 8 | column in the tile
   T acc[kMaxOut];
 #pragma unroll
   for (int q = 0; q < kMaxOut; ++q) {
     const int o = tid + kT * q;
-    om[q] = (o < outs) ? o / bn : 0;
-    on[q] = (o < outs) ? o % bn : 0;
+    mn[q] = (o < outs) ? ((o / bn) << 8) | (o % bn) : 0;
     acc[q] = 0;
   }
   const int nq = (outs - tid + kT - 1) / kT;
@@ -116,7 +115,8 @@ __device__ void gemm_tile_one(const EngineStage &s, int tm_i, int tn_i, int b, T
     for (int kk = 0; kk < kdepth; ++kk) {
 #pragma unroll
       for (int q = 0; q < kMaxOut; ++q)
-        if (q < nq) acc[q] = fma(As[kk * (kMaxTile + 1) + om[q]], Bs[kk * (kMaxTile + 1) + on[q]], acc[q]);
+        if (q < nq)
+          acc[q] = fma(As[kk * (kMaxTile + 1) + (mn[q] >> 8)], Bs[kk * (kMaxTile + 1) + (mn[q] & 255)], acc[q]);
     }
     __syncthreads();
   }
@@ -125,7 +125,7 @@ __device__ void gemm_tile_one(const EngineStage &s, int tm_i, int tn_i, int b, T
 #pragma unroll
   for (int q = 0; q < kMaxOut; ++q) {
     if (q >= nq) break;
-    const int gm = m0 + om[q], gn = n0 + on[q];
+    const int gm = m0 + (mn[q] >> 8), gn = n0 + (mn[q] & 255);
     if (gm < s.M && gn < s.N) C[gm * s.sCm + gn * s.sCn] = alpha * (double)acc[q];
   }
 }
@@ -361,7 +361,7 @@ __device__ void run_task(const EngineStage &s, int tile, double *smem, double *r
 // The persistent kernel: take the next task, wait for its pair's prerequisite
 // count (bounded: spin_cap polls, or at once once any wait has run out), run
 // it, publish it.
-__global__ void __launch_bounds__(kT)
+__global__ void __launch_bounds__(kT, 3)
 engine_kernel(const EngineStage *stages, const EngineTask *tasks, int ntasks, int *head,
               int *done, int *status, long long spin_cap, long long *prof) {
   extern __shared__ __align__(16) double smem[];
