@@ -75,6 +75,27 @@ __device__ void gemm_tile_t(const EngineStage &s, int tile, double *smem) {
     gemm_tile_one<T>(s, tm_i, tn_i, b, As, Bs);
 }
 
+// acc[q] += sum over a k slice of As[k][row q] Bs[k][column q] for the first
+// NQ output slots; nqw is warp-uniform (the slots of the warp's lane 0), so no
+// warp issues a DFMA for a slot none of its lanes owns -- a predicated-off
+// DFMA holds the FP64 unit as long as a full one. Lanes with fewer slots
+// multiply valid entries (index 0) into accumulators that are never stored.
+template <int NQ, typename T>
+__device__ __forceinline__ void mac_slots(int nqw, int kdepth, const T *As, const T *Bs,
+                                          const int (&mn)[kMaxOut], T (&acc)[kMaxOut]) {
+  if (nqw <= 0) return;
+  if (nqw == NQ) {
+    for (int kk = 0; kk < kdepth; ++kk) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q)
+        acc[q] = fma(As[kk * (kMaxTile + 1) + (mn[q] >> 8)], Bs[kk * (kMaxTile + 1) + (mn[q] & 255)],
+                     acc[q]);
+    }
+    return;
+  }
+  if constexpr (NQ < kMaxOut) mac_slots<NQ + 1, T>(nqw, kdepth, As, Bs, mn, acc);
+}
+
 // The tile (tm_i, tn_i) of batch entry b.
 template <typename T>
 __device__ void gemm_tile_one(const EngineStage &s, int tm_i, int tn_i, int b, T *As, T *Bs) {
@@ -94,6 +115,7 @@ __device__ void gemm_tile_one(const EngineStage &s, int tm_i, int tn_i, int b, T
     acc[q] = 0;
   }
   const int nq = (outs - tid + kT - 1) / kT;
+  const int nqw = __shfl_sync(0xffffffffu, nq, 0);   // lane 0 owns the most outputs of its warp
   const bool a_kfast = (s.sAk == 1), b_nfast = (s.sBn == 1);
   for (int kt = 0; kt < s.K; kt += kBK) {
     for (int e = tid; e < bm * kBK; e += kT) {
@@ -111,13 +133,7 @@ __device__ void gemm_tile_one(const EngineStage &s, int tm_i, int tn_i, int b, T
       Bs[kk * (kMaxTile + 1) + nn] = (T)v;
     }
     __syncthreads();
-    const int kdepth = min(kBK, s.K - kt);
-    for (int kk = 0; kk < kdepth; ++kk) {
-#pragma unroll
-      for (int q = 0; q < kMaxOut; ++q)
-        if (q < nq)
-          acc[q] = fma(As[kk * (kMaxTile + 1) + (mn[q] >> 8)], Bs[kk * (kMaxTile + 1) + (mn[q] & 255)], acc[q]);
-    }
+    mac_slots<1>(nqw, min(kBK, s.K - kt), As, Bs, mn, acc);
     __syncthreads();
   }
   const double alpha = s.alpha_dev ? __ldcg(s.alpha_dev) : 1.0;

@@ -4,12 +4,17 @@
 // per clock, against ~73 TFLOP/s of FP32. A warp-wide DFMA therefore occupies
 // the SM's FP64 unit for ~16 clocks while the two shared-memory operand loads
 // it needs take ~3 wavefronts: an FP64 contraction is bound by DFMA issue, and
-// register blocking buys nothing. What costs time is every padded output lane
-// and every idle SM. So:
+// register blocking buys nothing. What costs time is every DFMA a warp issues
+// for an output slot that some of its lanes do not have -- a predicated-off
+// DFMA holds the FP64 unit as long as a full one (ncu: a 625-output tile dealt
+// as four slots per thread kept the pipe busy for 32 warp-DFMAs per k step
+// where 20 carry outputs) -- and every idle SM. So:
 //   * a block computes a bm x bn output tile of any shape (bm, bn <= 128,
-//     bm*bn <= 4096), its outputs dealt linearly to 256 threads; tiles are
-//     chosen to divide M and N (e.g. 80 x 50 for a 1600 x 50 product), so
-//     almost no lane computes padding;
+//     bm*bn <= 4096), its outputs dealt linearly to 256 threads; each warp
+//     runs the multiply-add loop for exactly the number of slots its lane 0
+//     owns (a warp-uniform switch, no predicated-off slots), and tiles are
+//     chosen by a cost model that counts those warp-DFMAs, so almost no DFMA
+//     is spent on padding;
 //   * K is split until the grid has about four blocks per SM (wave
 //     quantization < 25%); the block that finishes an output tile last (a
 //     per-tile counter) sums its split-K partials in split order 0..ksplit-1,
@@ -44,6 +49,40 @@ __device__ __forceinline__ float round_operand(double x, int prec) {
   if (prec == kPrecTF32) u = (u + 0x1000u) & 0xFFFFE000u;
   else if (prec == kPrecBF16) u = (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
   return __uint_as_float(u);
+}
+
+// acc[q] += sum over the k slice of As[k][om[q]] Bs[k][on[q]] for the first NQ
+// output slots. Lanes that own fewer slots than NQ multiply valid shared-memory
+// entries (their indices are 0) into accumulators that are never stored.
+template <int NQ, int OUT, typename T>
+__device__ __forceinline__ void mac_n(int kdepth, const T (*As)[kMaxTile + 1],
+                                      const T (*Bs)[kMaxTile + 1], const int (&om)[OUT],
+                                      const int (&on)[OUT], T (&acc)[OUT]) {
+  if (kdepth == kBK) {
+#pragma unroll 4
+    for (int kk = 0; kk < kBK; ++kk) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) acc[q] = fma(As[kk][om[q]], Bs[kk][on[q]], acc[q]);
+    }
+  } else {
+    for (int kk = 0; kk < kdepth; ++kk) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) acc[q] = fma(As[kk][om[q]], Bs[kk][on[q]], acc[q]);
+    }
+  }
+}
+
+// Dispatch on the warp-uniform slot count nqw in [0, OUT].
+template <int NQ, int OUT, typename T>
+__device__ __forceinline__ void mac_slots(int nqw, int kdepth, const T (*As)[kMaxTile + 1],
+                                          const T (*Bs)[kMaxTile + 1], const int (&om)[OUT],
+                                          const int (&on)[OUT], T (&acc)[OUT]) {
+  if (nqw <= 0) return;
+  if (nqw == NQ) {
+    mac_n<NQ, OUT, T>(kdepth, As, Bs, om, on, acc);
+    return;
+  }
+  if constexpr (NQ < OUT) mac_slots<NQ + 1, OUT, T>(nqw, kdepth, As, Bs, om, on, acc);
 }
 
 // LOWP = false: FP64 operands and accumulators. LOWP = true: operands rounded
@@ -85,6 +124,8 @@ gemm_f64_kernel(Gemm g, int bm, int bn, int tiles_n, int tiles_m, int ksplit, in
     acc[q] = 0.0;
   }
   const int nq = (outs - tid + kThreads - 1) / kThreads;   // outputs this thread owns
+  // lane 0 owns the most outputs of its warp (nq does not increase with tid)
+  const int nqw = __shfl_sync(0xffffffffu, nq, 0);
 
   const bool a_kfast = (g.sAk == 1);
   const bool b_nfast = (g.sBn == 1);
@@ -105,21 +146,7 @@ gemm_f64_kernel(Gemm g, int bm, int bn, int tiles_n, int tiles_m, int ksplit, in
     }
     __syncthreads();
     // exact depth: a ragged last k-tile issues no DFMAs on zero padding
-    const int kdepth = min(kBK, kend - kt);
-    if (kdepth == kBK) {
-#pragma unroll 4
-      for (int kk = 0; kk < kBK; ++kk) {
-#pragma unroll
-        for (int q = 0; q < OUT; ++q)
-          if (q < nq) acc[q] = fma(As[kk][om[q]], Bs[kk][on[q]], acc[q]);
-      }
-    } else {
-      for (int kk = 0; kk < kdepth; ++kk) {
-#pragma unroll
-        for (int q = 0; q < OUT; ++q)
-          if (q < nq) acc[q] = fma(As[kk][om[q]], Bs[kk][on[q]], acc[q]);
-      }
-    }
+    mac_slots<1, OUT>(nqw, min(kBK, kend - kt), As, Bs, om, on, acc);
     __syncthreads();
   }
 
@@ -190,36 +217,76 @@ int tile_edge(int X, int cap) {
   return best;
 }
 
+// Warp-DFMA clocks per k step of one block: each warp issues one DFMA per
+// output slot its lane 0 owns, and a warp-DFMA holds the SM's FP64 unit
+// (two lanes per clock) for 16 clocks.
+double block_dfma_clocks(long long outs) {
+  double warp_slots = 0.0;
+  for (int w = 0; w < kThreads / 32; ++w)
+    warp_slots += (double)std::max<long long>(0, ceil_div(outs - 32LL * w, kThreads));
+  return 16.0 * warp_slots;
+}
+
+int out_slots(long long outs) {
+  const long long need = ceil_div(outs, kThreads);
+  return need <= 1 ? 1 : need <= 2 ? 2 : need <= 4 ? 4 : need <= 8 ? 8 : need <= 12 ? 12 : 16;
+}
+
 // Analytic launch model (clocks of the busiest SM) used to pick the tile and
 // the K split:
-//   FP64: a block's padded DFMAs at two lanes per clock, times the number of
-//         blocks the busiest SM receives (wave quantization over 152 SMs);
+//   FP64: the warp-DFMAs of a block (block_dfma_clocks per k step) times the
+//         number of blocks the busiest SM receives (wave quantization over
+//         152 SMs);
 //   latency: ~450 clocks per 16-deep k-tile (staging + two barriers), hidden
-//         up to 4 blocks per SM;
+//         by the blocks resident on an SM (fewer when a thread holds more
+//         accumulators);
 //   split-K: the last block of each tile re-reads the tile's ksplit partial
 //         sums from L2 (~64 bytes per clock per SM) before it writes C; the
 //         busiest SM does ceil(tiles / 152) such reductions.
 double model_clocks(const Gemm &g, int bm, int bn, long long ksplit) {
   const long long tiles = ceil_div(g.M, bm) * ceil_div(g.N, bn) * (long long)g.batch;
   const long long kchunk = ceil_div(ceil_div(g.K, ksplit), kBK) * kBK;
-  const long long blocks = tiles * ceil_div(g.K, kchunk);
+  const long long nsplit = ceil_div(g.K, kchunk);
+  const long long blocks = tiles * nsplit;
   const long long per_sm = ceil_div(blocks, 152);
-  const double dfma = (double)bm * bn * std::min<long long>(kchunk, g.K);
-  const double ktiles = (double)ceil_div(std::min<long long>(kchunk, g.K), kBK);
-  double t = per_sm * (dfma / 2.0) + ceil_div(per_sm, 4) * ktiles * 450.0 + 1500.0;
-  if (ksplit > 1)
-    t += (double)ceil_div(tiles, 152) * (600.0 + (double)ksplit * bm * bn * 8.0 / 64.0);
+  const long long kdepth = std::min<long long>(kchunk, g.K);
+  const long long outs = (long long)bm * bn;
+  const int out = out_slots(outs);
+  const int resident = out <= 4 ? 4 : out <= 8 ? 3 : 2;
+  const double ktiles = (double)ceil_div(kdepth, kBK);
+  double t = per_sm * (double)kdepth * block_dfma_clocks(outs) +
+             ceil_div(per_sm, resident) * ktiles * 450.0 + 1500.0;
+  if (nsplit > 1)
+    t += (double)ceil_div(tiles, 152) * (600.0 + (double)nsplit * outs * 8.0 / 64.0);
   return t;
 }
 
-Launch plan_search(const Gemm &g) {
+// Candidate tile edges for a dimension X: every divisor of X up to
+// kMaxTile, and the least-padding edge below each power-of-two cap.
+int edge_candidates(int X, int *out) {
+  int n = 0;
+  for (int t = 1; t <= std::min(X, kMaxTile); ++t)
+    if (X % t == 0) out[n++] = t;
   static const int caps[5] = {128, 64, 32, 16, 8};
+  for (int cap : caps) {
+    const int t = tile_edge(X, cap);
+    bool have = false;
+    for (int i = 0; i < n; ++i) have |= (out[i] == t);
+    if (!have) out[n++] = t;
+  }
+  return n;
+}
+
+Launch plan_search(const Gemm &g) {
   double best = 1e300;
   Launch L{};
-  for (int cn : caps) {
-    const int bn = tile_edge(g.N, cn);
-    for (int cm : caps) {
-      const int bm = tile_edge(g.M, std::min(cm, kThreads * kMaxOut / bn));
+  int em[kMaxTile + 8], en[kMaxTile + 8];
+  const int nm = edge_candidates(g.M, em), nn = edge_candidates(g.N, en);
+  for (int j = 0; j < nn; ++j) {
+    const int bn = en[j];
+    for (int i = 0; i < nm; ++i) {
+      const int bm = em[i];
+      if ((long long)bm * bn > (long long)kThreads * kMaxOut) continue;
       const long long tiles = ceil_div(g.M, bm) * ceil_div(g.N, bn) * (long long)g.batch;
       const long long kmax = ceil_div(g.K, kBK);
       long long cands[12];
@@ -227,22 +294,21 @@ Launch plan_search(const Gemm &g) {
       for (long long s = 1; s <= kmax && nc < 10; s *= 2) cands[nc++] = s;
       cands[nc++] = std::min(kmax, std::max<long long>(1, ceil_div(kTargetBlocks, tiles)));
       cands[nc++] = std::min(kmax, std::max<long long>(1, ceil_div(152, tiles)));
-      for (int i = 0; i < nc; ++i) {
-        if (cands[i] > 1 && tiles > kTileCounters) continue;   // one counter per tile
-        const double t = model_clocks(g, bm, bn, cands[i]);
+      for (int c = 0; c < nc; ++c) {
+        if (cands[c] > 1 && tiles > kTileCounters) continue;   // one counter per tile
+        const double t = model_clocks(g, bm, bn, cands[c]);
         if (t < best) {
           best = t;
           L.bm = bm;
           L.bn = bn;
-          L.ksplit = (int)cands[i];
+          L.ksplit = (int)cands[c];
         }
       }
     }
   }
   L.tiles_m = (int)ceil_div(g.M, L.bm);
   L.tiles_n = (int)ceil_div(g.N, L.bn);
-  const int need = (int)ceil_div((long long)L.bm * L.bn, kThreads);
-  L.out = need <= 1 ? 1 : need <= 2 ? 2 : need <= 4 ? 4 : need <= 8 ? 8 : need <= 12 ? 12 : 16;
+  L.out = out_slots((long long)L.bm * L.bn);
   const long long kchunk = ceil_div(ceil_div(g.K, L.ksplit), kBK) * kBK;
   L.kchunk = (int)std::max<long long>(kchunk, kBK);
   L.ksplit = (int)ceil_div(g.K, L.kchunk);
