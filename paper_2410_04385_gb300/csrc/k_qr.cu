@@ -54,11 +54,74 @@ __device__ __forceinline__ double rsqrt_newton(double x) {
   return ldexp(y, -e / 2);
 }
 
+// 1/sqrt(x) for x in [1e-30, 1e30] (a pivot pre-scaled by an even power of
+// two): the FP32 seed and the same two Newton-Raphson steps as rsqrt_newton,
+// without its range reduction. On GB300 a dependent FP64 instruction costs
+// ~64 clocks and frexp / ldexp are long sequences: measured 1447 clocks for
+// rsqrt_newton against ~450 for this, on the critical path of every column.
+__device__ __forceinline__ double rsqrt_scaled(double x) {
+  const double h = -0.5 * x;
+  double y = (double)rsqrtf((float)x);
+  y = y * fma(h, y * y, 1.5);
+  y = y * fma(h, y * y, 1.5);
+  return y;
+}
+
+// Warp reduction of the three convergence statistics; lane 0 holds the
+// result. dev and dmax are maxima of non-negative doubles, taken on their bit
+// patterns (integer order equals numeric order there), which keeps them off
+// the FP64 unit.
+__device__ __forceinline__ void warp_stats(long long &dev, long long &dmax, double &tr) {
+  for (int o = 16; o > 0; o >>= 1) {
+    dev = max(dev, __shfl_xor_sync(0xffffffffu, dev, o));
+    dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    tr += __shfl_xor_sync(0xffffffffu, tr, o);
+  }
+}
+
+// Pivot step of column j (thread 0 only): R_jj = sqrt(pivot) as y_j = 1/R_jj.
+// An exactly zero column of S (zero Gram diagonal) gets R_jj = 1, which
+// leaves Q_j = 0 and couples nothing; sending it to the shifted attempt
+// instead would make every pass shifted and leave ||Q^T Q - I|| at the shift
+// (~1e-11) on an otherwise benign S. A pivot not safely positive fails the
+// unshifted attempt; in the shifted attempt it sets the breakdown bit and is
+// clamped so that nothing divides by zero.
+// sc = 2^-2k and unsc = 2^-k put the largest Gram diagonal near 1, so every
+// pivot above the failure floor is a normal FP32 number once scaled.
+__device__ __forceinline__ void chol_pivot(double *G, int ld, int j, const unsigned char *zero_col,
+                                           double floor_piv, double shift, int attempt, double sc,
+                                           double unsc, double *rinv, unsigned char *fail) {
+  if (zero_col[j]) {
+    rinv[j] = 1.0;
+    return;
+  }
+  double piv = G[j * ld + j];
+  if (!(piv > floor_piv)) {
+    if (attempt == 0) fail[j] = 1;
+    else atomicOr(&g_qr_health, kHealthBreakdown);
+    piv = fmax(shift, 1e-300);
+  }
+  const double ps = piv * sc;
+  rinv[j] = (ps >= 1e-30 && ps <= 1e30) ? rsqrt_scaled(ps) * unsc : rsqrt_newton(piv);
+}
+
 // Flag words (reset at the start of every QR):
 //   flags[0] done:      no further pass is needed (read by the Gram GEMM and
 //                       this kernel at the start of every later pass)
 //   flags[1] skip_apply: the S <- S R^{-1} launch of this pass is a no-op
 //   flags[2] passes applied, flags[3] shifted passes (diagnostics)
+//
+// One block: convergence test of G = S^T S, then the Cholesky factor R of G
+// (shifted if the plain factorization breaks down), published as the unit
+// upper triangle U~ = D^{-1} R and y = diag(D^{-1}), D = diag(R).
+//
+// Right-looking factorization with a one-column look-ahead: during the
+// trailing update for column j, warp 0 first updates row j + 1 and thread 0
+// takes the pivot of column j + 1 (the only serial step of the next column)
+// while the other warps update the rest, so each column costs one barrier and
+// the pivot's dependent FP64 chain overlaps the bulk of the update. Rows of R
+// are not scaled in place: the update subtracts (G_ji y_j^2) G_jl, and the
+// publication scales row j by y_j^2.
 __global__ void __launch_bounds__(kCholThreads)
 chol_inv_kernel(const double *Gg, double *Ut_g, double *y_g, int c, int m, int *flags) {
   pdl_enter();
@@ -68,31 +131,54 @@ chol_inv_kernel(const double *Gg, double *Ut_g, double *y_g, int c, int m, int *
   }
   extern __shared__ double sm[];
   const int ld = c + 1;
-  double *G = sm;                                   // c x ld, upper triangle becomes R
-  __shared__ double s_diag_max, s_trace, s_dev;
+  double *G = sm;                                   // c x ld, upper triangle is updated
+  __shared__ double s_red[3][kCholThreads / 32];
+  __shared__ double s_diag_max, s_trace, s_dev, s_sc, s_unsc;
   __shared__ double s_rinv[kMaxSmall];              // 1 / R_jj
-  __shared__ int s_fail;
+  __shared__ unsigned char s_zero[kMaxSmall];       // column j of S is exactly zero
+  __shared__ unsigned char s_failc[kMaxSmall];      // unshifted pivot j not safely positive
   const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
   const int tx = tid % 16, ty = tid / 16;           // 16 x 16 grid (kCholThreads = 256)
 
   // -- convergence test: G = I to working accuracy, except columns that are
   // exactly zero (a zero column stays zero through every pass). The test is
   // absolute on purpose: S of any scale (HaTT sketches of long chains reach
   // 1e-20 and below) is never mistaken for a converged basis.
-  double dev = 0.0, dmax = 0.0, tr = 0.0;
+  long long dev = 0, dmax = 0;          // bit patterns of non-negative doubles
+  double tr = 0.0;
   int bad = 0;
-  for (int e = tid; e < c * c; e += kCholThreads) {
-    const int i = e / c, j = e % c;
-    const double v = Gg[e];
-    bad |= !isfinite(v);
-    G[i * ld + j] = v;
-    if (i == j) {
-      dmax = fmax(dmax, v);
-      tr += v;
-      dev = fmax(dev, (v == 0.0) ? 0.0 : fabs(v - 1.0));
-    } else {
-      dev = fmax(dev, fabs(v));
+  const int n = c * c;
+  for (int e0 = tid; e0 < n; e0 += 4 * kCholThreads) {
+    double v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {         // four loads in flight per thread
+      const int e = e0 + q * kCholThreads;
+      v[q] = e < n ? Gg[e] : 0.0;
     }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = e0 + q * kCholThreads;
+      if (e >= n) break;
+      const int i = e / c, j = e - i * c;
+      const long long bits = __double_as_longlong(fabs(v[q]));
+      bad |= bits >= 0x7ff0000000000000LL;                   // Inf or NaN
+      G[i * ld + j] = v[q];
+      if (i == j) {
+        s_zero[i] = (v[q] == 0.0);
+        dmax = max(dmax, bits);
+        tr += v[q];
+        if (v[q] != 0.0) dev = max(dev, __double_as_longlong(fabs(v[q] - 1.0)));
+      } else {
+        dev = max(dev, bits);
+      }
+    }
+  }
+  warp_stats(dev, dmax, tr);
+  if (lane == 0) {
+    s_red[0][warp] = __longlong_as_double(dev);
+    s_red[1][warp] = __longlong_as_double(dmax);
+    s_red[2][warp] = tr;
   }
   // a non-finite Gram matrix (a non-finite input core or intermediate): record
   // it, leave S as it is and stop this QR (every later pass is a no-op)
@@ -104,34 +190,26 @@ chol_inv_kernel(const double *Gg, double *Ut_g, double *y_g, int c, int m, int *
     }
     return;
   }
-  {
-    __shared__ double red[kCholThreads];
-    red[tid] = dev;
-    __syncthreads();
-    for (int w = kCholThreads / 2; w > 0; w >>= 1) {
-      if (tid < w) red[tid] = fmax(red[tid], red[tid + w]);
-      __syncthreads();
+  if (tid == 0) {
+    double d0 = 0.0, d1 = 0.0, d2 = 0.0;
+    for (int w = 0; w < kCholThreads / 32; ++w) {
+      d0 = fmax(d0, s_red[0][w]);
+      d1 = fmax(d1, s_red[1][w]);
+      d2 += s_red[2][w];
     }
-    if (tid == 0) s_dev = red[0];
-    __syncthreads();
-    red[tid] = dmax;
-    __syncthreads();
-    for (int w = kCholThreads / 2; w > 0; w >>= 1) {
-      if (tid < w) red[tid] = fmax(red[tid], red[tid + w]);
-      __syncthreads();
-    }
-    if (tid == 0) s_diag_max = red[0];
-    __syncthreads();
-    red[tid] = tr;
-    __syncthreads();
-    for (int w = kCholThreads / 2; w > 0; w >>= 1) {
-      if (tid < w) red[tid] += red[tid + w];
-      __syncthreads();
-    }
-    if (tid == 0) s_trace = red[0];
-    __syncthreads();
+    s_dev = d0;
+    s_diag_max = d1;
+    s_trace = d2;
+    // pivot scaling 2^-2k with the largest diagonal in [0.5, 2) after scaling
+    int ex = 0;
+    if (d1 > 0.0) frexp(d1, &ex);
+    const int k = ex / 2;
+    s_sc = ldexp(1.0, -2 * k);
+    s_unsc = ldexp(1.0, -k);
   }
+  __syncthreads();
   const double u = 1.1102230246251565e-16;
+  const double sc = s_sc, unsc = s_unsc;
   if (s_dev <= 8.0 * c * u) {              // already orthonormal: nothing to apply
     if (tid == 0) { flags[0] = 1; flags[1] = 1; }
     return;
@@ -145,7 +223,10 @@ chol_inv_kernel(const double *Gg, double *Ut_g, double *y_g, int c, int m, int *
     if (s_dev <= 0.1 / c) flags[0] = 1;
   }
 
-  // -- Cholesky: first unshifted, then shifted if a pivot is not safely positive
+  // -- Cholesky: first unshifted, then shifted if a pivot is not safely positive.
+  // A failed pivot of column j is recorded in s_failc[j] while column j - 1
+  // is updated and read by every thread after that column's barrier, so all
+  // threads leave the column loop at the same j.
   for (int attempt = 0; attempt < 2; ++attempt) {
     double shift = 0.0;
     if (attempt == 1) {
@@ -157,49 +238,47 @@ chol_inv_kernel(const double *Gg, double *Ut_g, double *y_g, int c, int m, int *
       }
       if (tid == 0) flags[3] += 1;
     }
-    if (tid == 0) s_fail = 0;
+    for (int j = tid; j < c; j += kCholThreads) s_failc[j] = 0;
     __syncthreads();
     const double floor_piv = (attempt == 0) ? (double)c * u * s_diag_max : 0.0;
+    if (tid == 0) chol_pivot(G, ld, 0, s_zero, floor_piv, shift, attempt, sc, unsc, s_rinv, s_failc);
+    __syncthreads();
+    bool failed = false;
     for (int j = 0; j < c; ++j) {
-      if (tid == 0) {
-        double piv = G[j * ld + j];
-        if (Gg[j * c + j] == 0.0) {
-          // an exactly zero column of S: its Gram row and column vanish, so
-          // R_jj = 1 leaves Q_j = 0 and couples nothing. Sending it to the
-          // shifted attempt instead would make every pass shifted and leave
-          // ||Q^T Q - I|| at the shift (~1e-11) on an otherwise benign S.
-          piv = 1.0;
-        } else if (!(piv > floor_piv)) {
-          if (attempt == 0) s_fail = 1;
-          else atomicOr(&g_qr_health, kHealthBreakdown);   // shifted and still not positive
-          piv = fmax(shift, 1e-300);          // shifted attempt: never divide by zero
-        }
-        const double y = rsqrt_newton(piv);
-        G[j * ld + j] = piv * y;              // R_jj = sqrt(piv)
-        s_rinv[j] = y;
+      if (s_failc[j]) {
+        failed = true;
+        break;
       }
-      __syncthreads();
-      if (s_fail) break;
       const double yj = s_rinv[j];
-      for (int l = j + 1 + tid; l < c; l += kCholThreads) G[j * ld + l] *= yj;
-      __syncthreads();
-      // trailing update of the upper triangle on a 16 x 16 thread grid
-      for (int i = j + 1 + ty; i < c; i += 16) {
-        const double rji = G[j * ld + i];
-        for (int l = i + tx; l < c; l += 16) G[i * ld + l] = fma(-rji, G[j * ld + l], G[i * ld + l]);
+      const double y2 = yj * yj;
+      const double *rowj = G + j * ld;
+      if (warp == 0 && j + 1 < c) {       // look-ahead: row j + 1, then its pivot
+        const int i = j + 1;
+        const double rji = rowj[i] * y2;
+        for (int l = i + lane; l < c; l += 32) G[i * ld + l] = fma(-rji, rowj[l], G[i * ld + l]);
+        __syncwarp();
+        if (lane == 0) chol_pivot(G, ld, i, s_zero, floor_piv, shift, attempt, sc, unsc, s_rinv, s_failc);
+      }
+      // trailing update of the rows below on a 16 x 16 thread grid
+      for (int i = j + 2 + ty; i < c; i += 16) {
+        const double rji = rowj[i] * y2;
+        for (int l = i + tx; l < c; l += 16) G[i * ld + l] = fma(-rji, rowj[l], G[i * ld + l]);
       }
       __syncthreads();
     }
-    __syncthreads();
-    if (!s_fail) break;
+    if (!failed) break;
+    __syncthreads();                      // all reads of G and s_failc done before the retry
   }
 
-  // -- publish R = D U~ as the unit upper triangle U~ (U~_jl = R_jl / R_jj)
-  // and y_j = 1 / R_jj; the apply kernel solves with them, so no serial
-  // triangular inverse is formed in this single block
-  for (int i = ty; i < c; i += 16)
+  // -- publish R = D U~ as the unit upper triangle U~ (U~_jl = R_jl / R_jj =
+  // G_jl y_j^2 with G the updated Gram row) and y_j = 1 / R_jj; the apply
+  // kernel solves with them, so no serial triangular inverse is formed in
+  // this single block
+  for (int i = ty; i < c; i += 16) {
+    const double yi2 = s_rinv[i] * s_rinv[i];
     for (int l = tx; l < c; l += 16)
-      Ut_g[i * c + l] = (l > i) ? G[i * ld + l] * s_rinv[i] : (l == i ? 1.0 : 0.0);
+      Ut_g[i * c + l] = (l > i) ? G[i * ld + l] * yi2 : (l == i ? 1.0 : 0.0);
+  }
   for (int i = tid; i < c; i += kCholThreads) y_g[i] = s_rinv[i];
 }
 

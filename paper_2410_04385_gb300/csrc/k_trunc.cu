@@ -169,6 +169,36 @@ __device__ void tridiag_shifted_solve(const float *d, const float *e, int c, flo
   }
 }
 
+// Householder reflector of column k of A (rows k+1..c-1), by one warp:
+// v = x - alpha e_1 with alpha = -sign(x_0) ||x|| in row k of Vh, tau[k] =
+// 2 / v^T v (0 when x is already zero), d[k] = A_kk, e[k] = alpha.
+__device__ __forceinline__ void householder_col(const float *A, int ld, int c, int k, float *Vh,
+                                                float *d, float *e, float *tau, int lane) {
+  const int m = c - k - 1;
+  float *v = Vh + k * c;
+  float s2 = 0.0f;
+  for (int r = lane; r < m; r += 32) {
+    const float x = A[(k + 1 + r) * ld + k];
+    s2 = fmaf(x, x, s2);
+  }
+  s2 = warp_sum_f(s2);
+  const float x0 = A[(k + 1) * ld + k];
+  const bool skip = !(s2 > 1e-36f);
+  const float alpha = skip ? x0 : -copysignf(sqrtf(s2), x0);
+  const float v0 = x0 - alpha;
+  const float vtv = s2 - x0 * x0 + v0 * v0;
+  for (int r = lane; r < m; r += 32) v[r] = skip ? 0.0f : (r == 0 ? v0 : A[(k + 1 + r) * ld + k]);
+  if (lane == 0) {
+    d[k] = A[k * ld + k];
+    e[k] = alpha;
+    tau[k] = (skip || !(vtv > 0.0f)) ? 0.0f : 2.0f / vtv;
+  }
+}
+
+constexpr int kSturmPts = 2;      // Sturm-count points per lane and multisection round
+constexpr int kWarpCluster = 8;   // clusters up to this size are orthogonalized by one warp
+constexpr int kBtCols = 8;        // eigenvector columns per warp in the back-transformation
+
 __global__ void __launch_bounds__(kEigThreads)
 eig_tridiag32_kernel(const double *G, int c, double *U, const int *skip) {
   pdl_enter();
@@ -183,79 +213,74 @@ eig_tridiag32_kernel(const double *G, int c, double *U, const int *skip) {
   float *tau = e + c;            // reflector scales beta_k
   float *lam = tau + c;          // eigenvalues, decreasing
   float *p = lam + c;            // work vector
-  __shared__ double red[kEigThreads];
+  __shared__ double s_tr;
   __shared__ float s_scal[4];
   __shared__ int s_start[kMaxSmall + 1];
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const int tx = tid % 16, ty = tid / 16;
 
-  double tr = 0.0;
-  for (int i = tid; i < c; i += kEigThreads) tr += G[i * c + i];
-  tr = block_sum(tr, red);
-  const double scale = tr > 0.0 ? 1.0 / tr : 1.0;
+  if (warp == 0) {                          // trace (FP64), one warp
+    double tr = 0.0;
+    for (int i = lane; i < c; i += 32) tr += G[i * c + i];
+    for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+    if (lane == 0) s_tr = tr;
+  }
+  __syncthreads();
+  const double scale = s_tr > 0.0 ? 1.0 / s_tr : 1.0;
   for (int e2 = tid; e2 < c * c; e2 += kEigThreads) {
     const int i = e2 / c, j = e2 % c;
     A[i * ld + j] = (float)(0.5 * (G[i * c + j] + G[j * c + i]) * scale);
   }
   __syncthreads();
 
-  // 1. tridiagonalization
+  // 1. tridiagonalization, two barriers per column: (a) p = beta A2 v;
+  // (b) the rank-2 update, during which warp 0 first updates column k + 1 and
+  // forms the next reflector while the other warps update the trailing block
+  // (row k + 1 right of the diagonal is never read again and is not updated).
+  if (warp == 0 && c > 2) householder_col(A, ld, c, 0, Vh, d, e, tau, lane);
+  __syncthreads();
   for (int k = 0; k + 2 < c; ++k) {
     const int m = c - k - 1;
-    float *v = Vh + k * c;
-    if (warp == 0) {
-      float s2 = 0.0f;
-      for (int r = lane; r < m; r += 32) {
-        const float x = A[(k + 1 + r) * ld + k];
-        s2 = fmaf(x, x, s2);
-      }
-      s2 = warp_sum_f(s2);
-      const float x0 = A[(k + 1) * ld + k];
-      const bool skip = !(s2 > 1e-36f);
-      const float alpha = skip ? x0 : -copysignf(sqrtf(s2), x0);
-      const float v0 = x0 - alpha;
-      const float vtv = s2 - x0 * x0 + v0 * v0;
-      for (int r = lane; r < m; r += 32) v[r] = skip ? 0.0f : (r == 0 ? v0 : A[(k + 1 + r) * ld + k]);
-      if (lane == 0) {
-        d[k] = A[k * ld + k];
-        e[k] = alpha;
-        tau[k] = (skip || !(vtv > 0.0f)) ? 0.0f : 2.0f / vtv;
-      }
-    }
-    __syncthreads();
+    const float *v = Vh + k * c;
     const float beta = tau[k];
     if (beta != 0.0f) {
       {                                                     // p = beta A2 v
         const int lanes = lanes_per_dot(m);
         const int i = tid / lanes, sub = tid % lanes;
-        float s = 0.0f;
+        float sacc = 0.0f;
         if (i < m) {
           const float *row = A + (k + 1 + i) * ld + (k + 1);
-          for (int j = sub; j < m; j += lanes) s = fmaf(row[j], v[j], s);
+          for (int j = sub; j < m; j += lanes) sacc = fmaf(row[j], v[j], sacc);
         }
-        s = group_sum_f(s, lanes);
-        if (i < m && sub == 0) p[i] = beta * s;
+        sacc = group_sum_f(sacc, lanes);
+        if (i < m && sub == 0) p[i] = beta * sacc;
       }
       __syncthreads();
-      if (warp == 0) {
-        float s = 0.0f;
-        for (int r = lane; r < m; r += 32) s = fmaf(v[r], p[r], s);
-        s = warp_sum_f(s);
-        if (lane == 0) s_scal[0] = 0.5f * beta * s;
+      float kd = 0.0f;                                      // K = beta/2 v^T p, every warp
+      for (int r = lane; r < m; r += 32) kd = fmaf(v[r], p[r], kd);
+      const float K = 0.5f * beta * warp_sum_f(kd);
+      if (warp == 0) {                                      // column k + 1, then reflector k + 1
+        const float v0 = v[0], w0 = p[0] - K * v0;
+        for (int i = lane; i < m; i += 32) {
+          const float vi = v[i], wi = p[i] - K * vi;
+          A[(k + 1 + i) * ld + (k + 1)] -= vi * w0 + wi * v0;
+        }
+        __syncwarp();
+        if (k + 3 < c) householder_col(A, ld, c, k + 1, Vh, d, e, tau, lane);
       }
-      __syncthreads();
-      const float K = s_scal[0];
-      for (int i = ty; i < m; i += 16) {                     // A2 -= v w^T + w v^T
+      for (int i = 1 + ty; i < m; i += 16) {                // trailing block A2[1:, 1:]
         const float vi = v[i], wi = p[i] - K * vi;
         float *row = A + (k + 1 + i) * ld + (k + 1);
-        for (int j = tx; j < m; j += 16) {
+        for (int j = 1 + tx; j < m; j += 16) {
           const float wj = p[j] - K * v[j];
           row[j] -= vi * wj + wi * v[j];
         }
       }
-      __syncthreads();
+    } else if (warp == 0 && k + 3 < c) {
+      householder_col(A, ld, c, k + 1, Vh, d, e, tau, lane);
     }
+    __syncthreads();
   }
   if (tid == 0) {
     if (c >= 2) {
@@ -270,7 +295,10 @@ eig_tridiag32_kernel(const double *G, int c, double *U, const int *skip) {
       const float rad = (i > 0 ? fabsf(e[i - 1]) : 0.0f) + (i + 1 < c ? fabsf(e[i]) : 0.0f);
       lo = fminf(lo, d[i] - rad);
       hi = fmaxf(hi, d[i] + rad);
-      if (i + 1 < c) emax = fmaxf(emax, e[i] * e[i]);
+      if (i + 1 < c) {
+        p[i] = e[i] * e[i];                                  // e^2 for the Sturm counts
+        emax = fmaxf(emax, p[i]);
+      }
     }
     s_scal[0] = lo;
     s_scal[1] = hi;
@@ -278,25 +306,58 @@ eig_tridiag32_kernel(const double *G, int c, double *U, const int *skip) {
   }
   __syncthreads();
 
-  // 2. bisection: thread i finds the i-th largest eigenvalue
+  // 2. eigenvalues by multisection on Sturm counts: a group of G lanes per
+  // eigenvalue (the i-th largest), each lane counting at kSturmPts points of
+  // the bracket at once, so a round shrinks it G kSturmPts + 1 times (a
+  // bisection step halves it) and the independent count chains hide each
+  // other's division latency.
   const float glo = s_scal[0], ghi = s_scal[1], pivmin = s_scal[2];
   const float span = fmaxf(fabsf(glo), fabsf(ghi));
-  for (int i = tid; i < c; i += kEigThreads) {
+  {
+    const int G = c <= 32 ? 8 : c <= 64 ? 4 : 2;
+    const int i = tid / G, g = tid % G;
+    const bool has = i < c;
     const int target = c - 1 - i;                           // count of smaller eigenvalues
     float a = glo, b = ghi;
-    for (int it = 0; it < 80; ++it) {
-      const float mid = 0.5f * (a + b);
-      float q = d[0] - mid;
-      int cnt = q < 0.0f;
-      for (int j = 1; j < c; ++j) {
-        if (fabsf(q) < pivmin) q = -pivmin;
-        q = d[j] - mid - __fdividef(e[j - 1] * e[j - 1], q);
-        cnt += q < 0.0f;
+    bool active = has;
+    const float inv_n = 1.0f / (float)(G * kSturmPts + 1);
+    for (int round = 0; round < 64 && __any_sync(0xffffffffu, active); ++round) {
+      float na = a, nb = b;
+      if (active) {
+        float x[kSturmPts], q[kSturmPts];
+        int cnt[kSturmPts];
+#pragma unroll
+        for (int t = 0; t < kSturmPts; ++t) {
+          x[t] = fmaf(b - a, (float)(g + G * t + 1) * inv_n, a);
+          q[t] = d[0] - x[t];
+          cnt[t] = q[t] < 0.0f;
+        }
+        for (int j = 1; j < c; ++j) {
+          const float dj = d[j], ej2 = p[j - 1];
+#pragma unroll
+          for (int t = 0; t < kSturmPts; ++t) {
+            if (fabsf(q[t]) < pivmin) q[t] = -pivmin;
+            q[t] = dj - x[t] - __fdividef(ej2, q[t]);
+            cnt[t] += q[t] < 0.0f;
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < kSturmPts; ++t) {
+          if (cnt[t] <= target) na = fmaxf(na, x[t]);
+          else nb = fminf(nb, x[t]);
+        }
       }
-      if (cnt <= target) a = mid; else b = mid;
-      if (b - a <= 2.4e-7f * fmaxf(fmaxf(fabsf(a), fabsf(b)), 1e-7f * span)) break;
+      for (int o = 1; o < G; o <<= 1) {                     // group of G aligned lanes
+        na = fmaxf(na, __shfl_xor_sync(0xffffffffu, na, o));
+        nb = fminf(nb, __shfl_xor_sync(0xffffffffu, nb, o));
+      }
+      if (active) {
+        a = na;
+        b = nb;
+        if (b - a <= 2.4e-7f * fmaxf(fmaxf(fabsf(a), fabsf(b)), 1e-7f * span)) active = false;
+      }
     }
-    lam[i] = 0.5f * (a + b);
+    if (has && g == 0) lam[i] = 0.5f * (a + b);
   }
   __syncthreads();
   // Shifts of equal (or nearly equal) eigenvalues are moved apart by 10 ulps
@@ -337,11 +398,17 @@ eig_tridiag32_kernel(const double *G, int c, double *U, const int *skip) {
   if (tid == 0) s_start[c] = 1;
   __syncthreads();
 
-  // 4. modified Gram-Schmidt (twice) within clusters, a warp per cluster
+  // 4. Gram-Schmidt (twice) within clusters. Clusters of up to kWarpCluster
+  // vectors: modified Gram-Schmidt by one warp each, all such clusters at
+  // once. Larger clusters (graded spectra put every eigenvalue below
+  // kClusterRel of the largest into one): classical Gram-Schmidt by the whole
+  // block, one vector at a time -- its projections on the earlier vectors of
+  // the cluster spread over the warps, the update over the rows.
   for (int s0 = 0; s0 < c; ++s0) {
     if (!s_start[s0] || (s0 % (kEigThreads / 32)) != warp) continue;
     int t0 = s0 + 1;
     while (!s_start[t0]) ++t0;
+    if (t0 - s0 > kWarpCluster) continue;
     for (int a = s0 + 1; a < t0; ++a) {
       for (int rep = 0; rep < 2; ++rep) {
         for (int b = s0; b < a; ++b) {
@@ -351,40 +418,98 @@ eig_tridiag32_kernel(const double *G, int c, double *U, const int *skip) {
           for (int r = lane; r < c; r += 32) Z[r * ld + a] = fmaf(-dot, Z[r * ld + b], Z[r * ld + a]);
           __syncwarp();
         }
-        float s = 0.0f;
-        for (int r = lane; r < c; r += 32) s = fmaf(Z[r * ld + a], Z[r * ld + a], s);
-        s = warp_sum_f(s);
-        const float inv = s > 0.0f ? rsqrtf(s) : 0.0f;
+        float sn = 0.0f;
+        for (int r = lane; r < c; r += 32) sn = fmaf(Z[r * ld + a], Z[r * ld + a], sn);
+        sn = warp_sum_f(sn);
+        const float inv = sn > 0.0f ? rsqrtf(sn) : 0.0f;
         for (int r = lane; r < c; r += 32) Z[r * ld + a] *= inv;
         __syncwarp();
       }
     }
   }
   __syncthreads();
-
-  // 5. back-transformation Z <- H_0 ... H_{c-3} Z
-  for (int k = c - 3; k >= 0; --k) {
-    const float beta = tau[k];
-    if (beta == 0.0f) continue;
-    const int m = c - k - 1;
-    const float *v = Vh + k * c;
-    {                                                       // p = beta Z2^T v
-      const int lanes = lanes_per_dot(c);
-      const int j = tid / lanes, sub = tid % lanes;
-      float s = 0.0f;
-      if (j < c)
-        for (int r = sub; r < m; r += lanes) s = fmaf(v[r], Z[(k + 1 + r) * ld + j], s);
-      s = group_sum_f(s, lanes);
-      if (j < c && sub == 0) p[j] = beta * s;
+  for (int s0 = 0; s0 < c; ++s0) {                 // every thread takes the same branches
+    if (!s_start[s0]) continue;
+    int t0 = s0 + 1;
+    while (!s_start[t0]) ++t0;
+    if (t0 - s0 <= kWarpCluster) continue;
+    for (int a = s0 + 1; a < t0; ++a) {
+      for (int rep = 0; rep < 2; ++rep) {
+        for (int bb = s0 + warp; bb < a; bb += kEigThreads / 32) {   // p[b - s0] = z_b . z_a
+          float dot = 0.0f;
+          for (int r = lane; r < c; r += 32) dot = fmaf(Z[r * ld + bb], Z[r * ld + a], dot);
+          dot = warp_sum_f(dot);
+          if (lane == 0) p[bb - s0] = dot;
+        }
+        __syncthreads();
+        for (int r = tid; r < c; r += kEigThreads) {                  // z_a -= sum_b p_b z_b
+          float za = Z[r * ld + a];
+          for (int bb = s0; bb < a; ++bb) za = fmaf(-p[bb - s0], Z[r * ld + bb], za);
+          Z[r * ld + a] = za;
+        }
+        __syncthreads();
+      }
+      if (warp == 0) {
+        float sn = 0.0f;
+        for (int r = lane; r < c; r += 32) sn = fmaf(Z[r * ld + a], Z[r * ld + a], sn);
+        sn = warp_sum_f(sn);
+        if (lane == 0) s_scal[3] = sn > 0.0f ? rsqrtf(sn) : 0.0f;
+      }
+      __syncthreads();
+      const float inv = s_scal[3];
+      for (int r = tid; r < c; r += kEigThreads) Z[r * ld + a] *= inv;
+      __syncthreads();
     }
-    __syncthreads();
-    for (int r = ty; r < m; r += 16) {
-      const float vr = v[r];
-      float *row = Z + (k + 1 + r) * ld;
-      for (int j = tx; j < c; j += 16) row[j] -= vr * p[j];
-    }
-    __syncthreads();
   }
+
+  // 5. back-transformation Z <- H_0 ... H_{c-3} Z. The columns of Z are
+  // independent: each warp takes kBtCols of them at a time, holds their
+  // entries in registers (lane l: rows l, l + 32, l + 64, l + 96) and applies
+  // the reflectors from the last to the first -- per reflector one warp sum
+  // per column, no block barrier.
+  for (int i0 = warp * kBtCols; i0 < c; i0 += (kEigThreads / 32) * kBtCols) {
+    float z[kBtCols][4];
+#pragma unroll
+    for (int q = 0; q < kBtCols; ++q)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int r = lane + 32 * t, i = i0 + q;
+        z[q][t] = (r < c && i < c) ? Z[r * ld + i] : 0.0f;
+      }
+    for (int k = c - 3; k >= 0; --k) {
+      const float beta = tau[k];
+      if (beta == 0.0f) continue;
+      const float *v = Vh + k * c;                // v[r - k - 1] for rows r > k
+      float vr[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int r = lane + 32 * t;
+        vr[t] = (r > k && r < c) ? v[r - k - 1] : 0.0f;
+      }
+      float dq[kBtCols];
+#pragma unroll
+      for (int q = 0; q < kBtCols; ++q)
+        dq[q] = fmaf(vr[3], z[q][3], fmaf(vr[2], z[q][2], fmaf(vr[1], z[q][1], vr[0] * z[q][0])));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int q = 0; q < kBtCols; ++q) dq[q] += __shfl_xor_sync(0xffffffffu, dq[q], o);
+#pragma unroll
+      for (int q = 0; q < kBtCols; ++q) {
+        const float f = beta * dq[q];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) z[q][t] = fmaf(-f, vr[t], z[q][t]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kBtCols; ++q)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int r = lane + 32 * t, i = i0 + q;
+        if (r < c && i < c) Z[r * ld + i] = z[q][t];
+      }
+  }
+  __syncthreads();
   for (int e2 = tid; e2 < c * c; e2 += kEigThreads) {
     const int r = e2 / c, i = e2 % c;
     U[e2] = (double)Z[r * ld + i];
@@ -627,16 +752,22 @@ rank_kernel(const double *e, int c, int cap, const double *delta2, long long *ra
             int *perm, double *sigma) {
   pdl_enter();
   __shared__ double sorted[kMaxSmall];
+  __shared__ double keys[kMaxSmall];
   const int tid = threadIdx.x;
   // sort key: the energy, or -1 when it is not finite (NaN compares false
   // with everything, so without the key equal positions could repeat and
-  // perm would not be a permutation)
-  auto key = [&](int i) { const double v = e[i]; return isfinite(v) ? v : -1.0; };
+  // perm would not be a permutation); staged in shared memory once, so the
+  // counting loop below waits on no global load
   for (int i = tid; i < c; i += kThreads) {
-    const double ei = key(i);
+    const double v = e[i];
+    keys[i] = isfinite(v) ? v : -1.0;
+  }
+  __syncthreads();
+  for (int i = tid; i < c; i += kThreads) {
+    const double ei = keys[i];
     int pos = 0;
     for (int j = 0; j < c; ++j) {
-      const double ej = key(j);
+      const double ej = keys[j];
       pos += (ej > ei) || (ej == ei && j < i);
     }
     perm[pos] = i;

