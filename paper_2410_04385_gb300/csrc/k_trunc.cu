@@ -213,12 +213,13 @@ eig_tridiag32_kernel(const double *G, int c, double *U, const int *skip) {
   float *tau = e + c;            // reflector scales beta_k
   float *lam = tau + c;          // eigenvalues, decreasing
   float *p = lam + c;            // work vector
+  float *p2 = p + c;             // work vector (second buffer of p)
+  float *wv = p2 + c;            // work vector (w of the rank-2 update)
   __shared__ double s_tr;
   __shared__ float s_scal[4];
   __shared__ int s_start[kMaxSmall + 1];
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
-  const int tx = tid % 16, ty = tid / 16;
 
   if (warp == 0) {                          // trace (FP64), one warp
     double tr = 0.0;
@@ -234,53 +235,71 @@ eig_tridiag32_kernel(const double *G, int c, double *U, const int *skip) {
   }
   __syncthreads();
 
-  // 1. tridiagonalization, two barriers per column: (a) p = beta A2 v;
-  // (b) the rank-2 update, during which warp 0 first updates column k + 1 and
-  // forms the next reflector while the other warps update the trailing block
-  // (row k + 1 right of the diagonal is never read again and is not updated).
-  if (warp == 0 && c > 2) householder_col(A, ld, c, 0, Vh, d, e, tau, lane);
-  __syncthreads();
-  for (int k = 0; k + 2 < c; ++k) {
-    const int m = c - k - 1;
-    const float *v = Vh + k * c;
-    const float beta = tau[k];
-    if (beta != 0.0f) {
-      {                                                     // p = beta A2 v
-        const int lanes = lanes_per_dot(m);
-        const int i = tid / lanes, sub = tid % lanes;
-        float sacc = 0.0f;
-        if (i < m) {
-          const float *row = A + (k + 1 + i) * ld + (k + 1);
-          for (int j = sub; j < m; j += lanes) sacc = fmaf(row[j], v[j], sacc);
-        }
-        sacc = group_sum_f(sacc, lanes);
-        if (i < m && sub == 0) p[i] = beta * sacc;
+  // 1. tridiagonalization, two barriers per column. With p_k = beta_k A2 v_k
+  // known, K = beta_k/2 v_k^T p_k and w = p_k - K v_k; warp 0 updates column
+  // k + 1 (column 0 of A2) and forms reflector k + 1 while the other warps
+  // wait at the first barrier; then one pass over the trailing block both
+  // applies A2 -= v w^T + w v^T and accumulates p_{k+1} = beta_{k+1} A2' v_{k+1}
+  // (each element is read and written once per column). Row k + 1 right of
+  // the diagonal is never read again and is not updated.
+  {
+    float *pc = p, *pn = p2;
+    if (warp == 0 && c > 2) householder_col(A, ld, c, 0, Vh, d, e, tau, lane);
+    __syncthreads();
+    if (c > 2) {                                            // p_0 = beta_0 A2 v_0
+      const int m = c - 1;
+      const float *v = Vh;
+      const int lanes = lanes_per_dot(m);
+      const int i = tid / lanes, sub = tid % lanes;
+      float sacc = 0.0f;
+      if (i < m) {
+        const float *row = A + (1 + i) * ld + 1;
+        for (int j = sub; j < m; j += lanes) sacc = fmaf(row[j], v[j], sacc);
       }
-      __syncthreads();
+      sacc = group_sum_f(sacc, lanes);
+      if (i < m && sub == 0) pc[i] = tau[0] * sacc;
+    }
+    __syncthreads();
+    for (int k = 0; k + 2 < c; ++k) {
+      const int m = c - k - 1;
+      const float *v = Vh + k * c;
+      const float beta = tau[k];
       float kd = 0.0f;                                      // K = beta/2 v^T p, every warp
-      for (int r = lane; r < m; r += 32) kd = fmaf(v[r], p[r], kd);
+      for (int r = lane; r < m; r += 32) kd = fmaf(v[r], pc[r], kd);
       const float K = 0.5f * beta * warp_sum_f(kd);
+      for (int r = tid; r < m; r += kEigThreads) wv[r] = pc[r] - K * v[r];
       if (warp == 0) {                                      // column k + 1, then reflector k + 1
-        const float v0 = v[0], w0 = p[0] - K * v0;
+        const float v0 = v[0], w0 = pc[0] - K * v0;
         for (int i = lane; i < m; i += 32) {
-          const float vi = v[i], wi = p[i] - K * vi;
+          const float vi = v[i], wi = pc[i] - K * vi;
           A[(k + 1 + i) * ld + (k + 1)] -= vi * w0 + wi * v0;
         }
         __syncwarp();
         if (k + 3 < c) householder_col(A, ld, c, k + 1, Vh, d, e, tau, lane);
       }
-      for (int i = 1 + ty; i < m; i += 16) {                // trailing block A2[1:, 1:]
-        const float vi = v[i], wi = p[i] - K * vi;
-        float *row = A + (k + 1 + i) * ld + (k + 1);
-        for (int j = 1 + tx; j < m; j += 16) {
-          const float wj = p[j] - K * v[j];
-          row[j] -= vi * wj + wi * v[j];
+      __syncthreads();
+      // trailing block A2[1:, 1:] (= the next A2), row i - 1 of it per lane group
+      const bool next = (k + 3 < c);
+      const float bnext = next ? tau[k + 1] : 0.0f;
+      const float *vn = Vh + (k + 1) * c;                   // v_{k+1}, length m - 1
+      const int mm = m - 1;
+      const int lanes = lanes_per_dot(mm);
+      const int r = tid / lanes, sub = tid % lanes;
+      float sacc = 0.0f;
+      if (r < mm) {
+        const float vi = v[r + 1], wi = wv[r + 1];
+        float *row = A + (k + 2 + r) * ld + (k + 2);
+        for (int j = sub; j < mm; j += lanes) {
+          const float a2 = row[j] - (vi * wv[j + 1] + wi * v[j + 1]);
+          row[j] = a2;
+          if (next) sacc = fmaf(a2, vn[j], sacc);
         }
       }
-    } else if (warp == 0 && k + 3 < c) {
-      householder_col(A, ld, c, k + 1, Vh, d, e, tau, lane);
+      sacc = group_sum_f(sacc, lanes);
+      if (next && r < mm && sub == 0) pn[r] = bnext * sacc;
+      __syncthreads();
+      float *t = pc; pc = pn; pn = t;
     }
-    __syncthreads();
   }
   if (tid == 0) {
     if (c >= 2) {
@@ -861,7 +880,7 @@ __global__ void set_ranks_kernel(RankTable t, long long *ranks) {
   for (int i = threadIdx.x; i < t.count; i += blockDim.x) ranks[i] = t.r[i];
 }
 
-size_t eig_smem(int c) { return ((size_t)2 * c * (c + 1) + (size_t)c * c + 5 * (size_t)c) * sizeof(float); }
+size_t eig_smem(int c) { return ((size_t)2 * c * (c + 1) + (size_t)c * c + 7 * (size_t)c) * sizeof(float); }
 
 struct Layout {
   double *G, *U0, *U1, *UtU, *T, *S, *E, *H, *V0, *V1, *B1, *e, *sigma, *K, *tmp, *gs, *scale;
