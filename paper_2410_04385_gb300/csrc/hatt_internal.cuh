@@ -47,6 +47,30 @@ __device__ __forceinline__ void pdl_enter() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// Forward substitution of one row x (lane t holds columns t, t+32, t+64,
+// t+96) against the unit upper triangle U~ in shared memory: step l
+// broadcasts the finished x_l and the lanes update their later columns. The
+// slots a step touches are chosen by warp-uniform loop bounds, never by
+// per-lane predicates alone: a predicated-off DFMA holds the FP64 unit like a
+// full one, and guarding all four slots at every step cost 2.4x (c = 50) to
+// 4x (c = 32) the DFMAs the solve needs.
+template <int NS>
+__device__ __forceinline__ void trsm_row(double (&x)[4], const double *Us, int c, int lane) {
+#pragma unroll
+  for (int s0 = 0; s0 < NS; ++s0) {
+    const int lend = min(c, 32 * (s0 + 1));
+    for (int l = 32 * s0; l < lend; ++l) {
+      const double xl = __shfl_sync(0xffffffffu, x[s0], l & 31);
+      const double *u = Us + l * c;
+#pragma unroll
+      for (int s = s0; s < NS; ++s) {
+        const int col = lane + 32 * s;
+        if (col > l && col < c) x[s] = fma(-xl, u[col], x[s]);
+      }
+    }
+  }
+}
+
 // Process-wide count of kernels enqueued by this library (each launch site
 // calls note_launch once).
 void note_launch();

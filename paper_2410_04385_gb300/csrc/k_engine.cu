@@ -335,26 +335,23 @@ __device__ void task_trsm(const EngineStage &s, int tile, double *smem) {
   __syncthreads();
   const int lane = threadIdx.x & 31, warps = kT / 32;
   const int r0 = tile * kEngineTrsmRows, r1 = min(s.m, r0 + kEngineTrsmRows);
+  const int ns = (c + 31) / 32;          // column slots in use (c <= kEngineMaxC)
   for (int r = r0 + (threadIdx.x >> 5); r < r1; r += warps) {
     double *row = s.S + (long long)r * c;
-    double x0 = lane < c ? __ldcg(row + lane) : 0.0;
-    double x1 = lane + 32 < c ? __ldcg(row + lane + 32) : 0.0;
-    double x2 = lane + 64 < c ? __ldcg(row + lane + 64) : 0.0;
-    double x3 = lane + 96 < c ? __ldcg(row + lane + 96) : 0.0;
-    for (int l = 0; l < c; ++l) {
-      const int slot = l >> 5;
-      const double own = slot == 0 ? x0 : slot == 1 ? x1 : slot == 2 ? x2 : x3;
-      const double xl = __shfl_sync(0xffffffffu, own, l & 31);
-      const double *ur = Us + l * c;
-      if (lane > l && lane < c) x0 = fma(-xl, ur[lane], x0);
-      if (lane + 32 > l && lane + 32 < c) x1 = fma(-xl, ur[lane + 32], x1);
-      if (c > 64 && lane + 64 > l && lane + 64 < c) x2 = fma(-xl, ur[lane + 64], x2);
-      if (c > 96 && lane + 96 > l && lane + 96 < c) x3 = fma(-xl, ur[lane + 96], x3);
+    double x[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) x[q] = (q < ns && lane + 32 * q < c) ? __ldcg(row + lane + 32 * q) : 0.0;
+    switch (ns) {                        // warp-uniform slot loops (see trsm_row)
+      case 1: trsm_row<1>(x, Us, c, lane); break;
+      case 2: trsm_row<2>(x, Us, c, lane); break;
+      case 3: trsm_row<3>(x, Us, c, lane); break;
+      default: trsm_row<4>(x, Us, c, lane); break;
     }
-    if (lane < c) row[lane] = x0 * ys[lane];
-    if (lane + 32 < c) row[lane + 32] = x1 * ys[lane + 32];
-    if (lane + 64 < c) row[lane + 64] = x2 * ys[lane + 64];
-    if (lane + 96 < c) row[lane + 96] = x3 * ys[lane + 96];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int col = lane + 32 * q;
+      if (q < ns && col < c) row[col] = x[q] * ys[col];
+    }
   }
 }
 

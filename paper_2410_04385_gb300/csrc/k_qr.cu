@@ -282,9 +282,7 @@ chol_inv_kernel(const double *Gg, double *Ut_g, double *y_g, int c, int m, int *
   for (int i = tid; i < c; i += kCholThreads) y_g[i] = s_rinv[i];
 }
 
-// Q = S R^{-1} = (S U~^{-1}) D^{-1}, one warp per row, in place. Lane t holds
-// columns t, t+32, t+64, t+96 of the row; step l broadcasts the finished x_l
-// and every lane updates its later columns (x_j -= x_l U~_lj). The unit
+// Q = S R^{-1} = (S U~^{-1}) D^{-1}, one warp per row, in place. The unit
 // diagonal keeps divisions out of the chain; the final scaling by y = D^{-1}
 // is one multiply per entry.
 __global__ void __launch_bounds__(kTrsmThreads)
@@ -300,26 +298,23 @@ trsm_rows_kernel(double *S, int m, int c, long long ldS, const double *Ut, const
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int warps = kTrsmThreads / 32;
+  const int ns = (c + 31) / 32;          // column slots in use (c <= 128)
   for (int r = blockIdx.x * warps + (threadIdx.x >> 5); r < m; r += gridDim.x * warps) {
     double *row = S + (long long)r * ldS;
-    double x0 = lane < c ? row[lane] : 0.0;
-    double x1 = lane + 32 < c ? row[lane + 32] : 0.0;
-    double x2 = lane + 64 < c ? row[lane + 64] : 0.0;
-    double x3 = lane + 96 < c ? row[lane + 96] : 0.0;
-    for (int l = 0; l < c; ++l) {
-      const int slot = l >> 5;
-      const double own = slot == 0 ? x0 : slot == 1 ? x1 : slot == 2 ? x2 : x3;
-      const double xl = __shfl_sync(0xffffffffu, own, l & 31);
-      const double *u = Us + l * c;
-      if (lane > l && lane < c) x0 = fma(-xl, u[lane], x0);
-      if (lane + 32 > l && lane + 32 < c) x1 = fma(-xl, u[lane + 32], x1);
-      if (c > 64 && lane + 64 > l && lane + 64 < c) x2 = fma(-xl, u[lane + 64], x2);
-      if (c > 96 && lane + 96 > l && lane + 96 < c) x3 = fma(-xl, u[lane + 96], x3);
+    double x[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) x[s] = (s < ns && lane + 32 * s < c) ? row[lane + 32 * s] : 0.0;
+    switch (ns) {
+      case 1: trsm_row<1>(x, Us, c, lane); break;
+      case 2: trsm_row<2>(x, Us, c, lane); break;
+      case 3: trsm_row<3>(x, Us, c, lane); break;
+      default: trsm_row<4>(x, Us, c, lane); break;
     }
-    if (lane < c) row[lane] = x0 * ys[lane];
-    if (lane + 32 < c) row[lane + 32] = x1 * ys[lane + 32];
-    if (lane + 64 < c) row[lane + 64] = x2 * ys[lane + 64];
-    if (lane + 96 < c) row[lane + 96] = x3 * ys[lane + 96];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int col = lane + 32 * s;
+      if (s < ns && col < c) row[col] = x[s] * ys[col];
+    }
   }
 }
 
