@@ -289,11 +289,23 @@ eig_tridiag32_kernel(const double *G, int c, double *U, const int *skip) {
       if (r < mm) {
         const float vi = v[r + 1], wi = wv[r + 1];
         float *row = A + (k + 2 + r) * ld + (k + 2);
-        for (int j = sub; j < mm; j += lanes) {
+        float sacc2 = 0.0f;
+        int j = sub;
+        for (; j + lanes < mm; j += 2 * lanes) {             // two independent elements per trip
+          const float a2 = row[j] - (vi * wv[j + 1] + wi * v[j + 1]);
+          const float b2 = row[j + lanes] - (vi * wv[j + lanes + 1] + wi * v[j + lanes + 1]);
+          row[j] = a2;
+          row[j + lanes] = b2;
+          sacc = fmaf(a2, vn[j], sacc);
+          sacc2 = fmaf(b2, vn[j + lanes], sacc2);
+        }
+        if (j < mm) {
           const float a2 = row[j] - (vi * wv[j + 1] + wi * v[j + 1]);
           row[j] = a2;
-          if (next) sacc = fmaf(a2, vn[j], sacc);
+          sacc = fmaf(a2, vn[j], sacc);
         }
+        sacc += sacc2;
+        if (!next) sacc = 0.0f;
       }
       sacc = group_sum_f(sacc, lanes);
       if (next && r < mm && sub == 0) pn[r] = bnext * sacc;
