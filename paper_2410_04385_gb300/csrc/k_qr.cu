@@ -149,6 +149,10 @@ chol_inv_kernel(const double *Gg, double *Ut_g, double *y_g, int c, int m, int *
   double tr = 0.0;
   int bad = 0;
   const int n = c * c;
+  // entry e = i c + j of thread tid: (i, j) advanced by (di, dj) per step of
+  // kCholThreads entries, with a carry, instead of a division per entry
+  const int di = kCholThreads / c, dj = kCholThreads - (kCholThreads / c) * c;
+  int ii = tid / c, jj = tid - (tid / c) * c;
   for (int e0 = tid; e0 < n; e0 += 4 * kCholThreads) {
     double v[4];
 #pragma unroll
@@ -160,7 +164,13 @@ chol_inv_kernel(const double *Gg, double *Ut_g, double *y_g, int c, int m, int *
     for (int q = 0; q < 4; ++q) {
       const int e = e0 + q * kCholThreads;
       if (e >= n) break;
-      const int i = e / c, j = e - i * c;
+      const int i = ii, j = jj;
+      ii += di;
+      jj += dj;
+      if (jj >= c) {
+        jj -= c;
+        ++ii;
+      }
       const long long bits = __double_as_longlong(fabs(v[q]));
       bad |= bits >= 0x7ff0000000000000LL;                   // Inf or NaN
       G[i * ld + j] = v[q];
@@ -259,10 +269,14 @@ chol_inv_kernel(const double *Gg, double *Ut_g, double *y_g, int c, int m, int *
         __syncwarp();
         if (lane == 0) chol_pivot(G, ld, i, s_zero, floor_piv, shift, attempt, sc, unsc, s_rinv, s_failc);
       }
-      // trailing update of the rows below on a 16 x 16 thread grid
-      for (int i = j + 2 + ty; i < c; i += 16) {
-        const double rji = rowj[i] * y2;
-        for (int l = i + tx; l < c; l += 16) G[i * ld + l] = fma(-rji, rowj[l], G[i * ld + l]);
+      // trailing update of the rows below by warps 1..7 on a 14 x 16 grid:
+      // warp 0 carries the pivot chain and takes no share of it
+      if (warp > 0) {
+        const int bt = tid - 32, bx = bt % 16, by = bt / 16;
+        for (int i = j + 2 + by; i < c; i += 14) {
+          const double rji = rowj[i] * y2;
+          for (int l = i + bx; l < c; l += 16) G[i * ld + l] = fma(-rji, rowj[l], G[i * ld + l]);
+        }
       }
       __syncthreads();
     }
