@@ -89,13 +89,14 @@ __device__ __forceinline__ float warp_sum_f(float v) {
   return v;
 }
 
-// Lanes per dot product when n dot products of one block share kEigThreads
-// threads: the largest power of two <= 32 with lanes * n <= kEigThreads.
-__device__ __forceinline__ int lanes_per_dot(int n) {
+// Lanes per dot product when n dot products share `threads` threads: the
+// largest power of two <= 32 with lanes * n <= threads.
+__device__ __forceinline__ int lanes_per_dot_n(int n, int threads) {
   int t = 32;
-  while (t > 1 && t * n > kEigThreads) t >>= 1;
+  while (t > 1 && t * n > threads) t >>= 1;
   return t;
 }
+__device__ __forceinline__ int lanes_per_dot(int n) { return lanes_per_dot_n(n, kEigThreads); }
 
 // Sum over aligned groups of `lanes` lanes (a power of two dividing 32); every
 // lane of the warp must call it.
@@ -199,6 +200,59 @@ constexpr int kSturmPts = 2;      // Sturm-count points per lane and multisectio
 constexpr int kWarpCluster = 8;   // clusters up to this size are orthogonalized by one warp
 constexpr int kBtCols = 8;        // eigenvector columns per warp in the back-transformation
 
+// Back-transformation of columns i0 .. i0 + kBtCols - 1 of Z by the stored
+// reflectors, one warp: lane l holds rows l + 32 t (t < TR, TR = 2 covers
+// c <= 64), the reflectors applied from the last to the first with one warp
+// sum per column each.
+template <int TR>
+__device__ __noinline__ void back_transform_cols(float *Z, int ld, const float *Vh,
+                                                 const float *tau, int c, int i0, int lane) {
+  float z[kBtCols][TR];
+#pragma unroll
+  for (int q = 0; q < kBtCols; ++q)
+#pragma unroll
+    for (int t = 0; t < TR; ++t) {
+      const int r = lane + 32 * t, i = i0 + q;
+      z[q][t] = (r < c && i < c) ? Z[r * ld + i] : 0.0f;
+    }
+  for (int k = c - 3; k >= 0; --k) {
+    const float beta = tau[k];
+    if (beta == 0.0f) continue;
+    const float *v = Vh + k * c;                  // v[r - k - 1] for rows r > k
+    float vr[TR];
+#pragma unroll
+    for (int t = 0; t < TR; ++t) {
+      const int r = lane + 32 * t;
+      vr[t] = (r > k && r < c) ? v[r - k - 1] : 0.0f;
+    }
+    float dq[kBtCols];
+#pragma unroll
+    for (int q = 0; q < kBtCols; ++q) {
+      float acc = vr[0] * z[q][0];
+#pragma unroll
+      for (int t = 1; t < TR; ++t) acc = fmaf(vr[t], z[q][t], acc);
+      dq[q] = acc;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int q = 0; q < kBtCols; ++q) dq[q] += __shfl_xor_sync(0xffffffffu, dq[q], o);
+#pragma unroll
+    for (int q = 0; q < kBtCols; ++q) {
+      const float f = beta * dq[q];
+#pragma unroll
+      for (int t = 0; t < TR; ++t) z[q][t] = fmaf(-f, vr[t], z[q][t]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kBtCols; ++q)
+#pragma unroll
+    for (int t = 0; t < TR; ++t) {
+      const int r = lane + 32 * t, i = i0 + q;
+      if (r < c && i < c) Z[r * ld + i] = z[q][t];
+    }
+}
+
 __global__ void __launch_bounds__(kEigThreads)
 eig_tridiag32_kernel(const double *G, int c, double *U, const int *skip) {
   pdl_enter();
@@ -214,7 +268,6 @@ eig_tridiag32_kernel(const double *G, int c, double *U, const int *skip) {
   float *lam = tau + c;          // eigenvalues, decreasing
   float *p = lam + c;            // work vector
   float *p2 = p + c;             // work vector (second buffer of p)
-  float *wv = p2 + c;            // work vector (w of the rank-2 update)
   __shared__ double s_tr;
   __shared__ float s_scal[4];
   __shared__ int s_start[kMaxSmall + 1];
@@ -236,30 +289,36 @@ eig_tridiag32_kernel(const double *G, int c, double *U, const int *skip) {
   __syncthreads();
 
   // 1. tridiagonalization, two barriers per column. With p_k = beta_k A2 v_k
-  // known, K = beta_k/2 v_k^T p_k and w = p_k - K v_k; warp 0 updates column
-  // k + 1 (column 0 of A2) and forms reflector k + 1 while the other warps
-  // wait at the first barrier; then one pass over the trailing block both
-  // applies A2 -= v w^T + w v^T and accumulates p_{k+1} = beta_{k+1} A2' v_{k+1}
-  // (each element is read and written once per column). Row k + 1 right of
-  // the diagonal is never read again and is not updated.
+  // known, K = beta_k/2 v_k^T p_k and w = p_k - K v_k: warp 0 updates column
+  // k + 1 (column 0 of A2) and forms reflector k + 1 while warps 1..7 apply
+  // A2 -= v w^T + w v^T to the trailing block A2[1:, 1:]; after a barrier all
+  // warps form p_{k+1} = beta_{k+1} A2' v_{k+1}. Row k + 1 right of the
+  // diagonal is never read again and is not updated.
   {
     float *pc = p, *pn = p2;
-    if (warp == 0 && c > 2) householder_col(A, ld, c, 0, Vh, d, e, tau, lane);
-    __syncthreads();
-    if (c > 2) {                                            // p_0 = beta_0 A2 v_0
-      const int m = c - 1;
-      const float *v = Vh;
+    auto matvec = [&](int k1) {                             // pn = beta_k1 A2_k1 v_k1
+      const int m = c - k1 - 1;
+      const float *v = Vh + k1 * c;
       const int lanes = lanes_per_dot(m);
       const int i = tid / lanes, sub = tid % lanes;
-      float sacc = 0.0f;
+      float sacc = 0.0f, sacc2 = 0.0f;
       if (i < m) {
-        const float *row = A + (1 + i) * ld + 1;
-        for (int j = sub; j < m; j += lanes) sacc = fmaf(row[j], v[j], sacc);
+        const float *row = A + (k1 + 1 + i) * ld + (k1 + 1);
+        int j = sub;
+        for (; j + lanes < m; j += 2 * lanes) {
+          sacc = fmaf(row[j], v[j], sacc);
+          sacc2 = fmaf(row[j + lanes], v[j + lanes], sacc2);
+        }
+        if (j < m) sacc = fmaf(row[j], v[j], sacc);
       }
-      sacc = group_sum_f(sacc, lanes);
-      if (i < m && sub == 0) pc[i] = tau[0] * sacc;
-    }
+      sacc = group_sum_f(sacc + sacc2, lanes);
+      if (i < m && sub == 0) pn[i] = tau[k1] * sacc;
+    };
+    if (warp == 0 && c > 2) householder_col(A, ld, c, 0, Vh, d, e, tau, lane);
     __syncthreads();
+    if (c > 2) matvec(0);
+    __syncthreads();
+    { float *t = pc; pc = pn; pn = t; }
     for (int k = 0; k + 2 < c; ++k) {
       const int m = c - k - 1;
       const float *v = Vh + k * c;
@@ -267,7 +326,6 @@ eig_tridiag32_kernel(const double *G, int c, double *U, const int *skip) {
       float kd = 0.0f;                                      // K = beta/2 v^T p, every warp
       for (int r = lane; r < m; r += 32) kd = fmaf(v[r], pc[r], kd);
       const float K = 0.5f * beta * warp_sum_f(kd);
-      for (int r = tid; r < m; r += kEigThreads) wv[r] = pc[r] - K * v[r];
       if (warp == 0) {                                      // column k + 1, then reflector k + 1
         const float v0 = v[0], w0 = pc[0] - K * v0;
         for (int i = lane; i < m; i += 32) {
@@ -276,39 +334,28 @@ eig_tridiag32_kernel(const double *G, int c, double *U, const int *skip) {
         }
         __syncwarp();
         if (k + 3 < c) householder_col(A, ld, c, k + 1, Vh, d, e, tau, lane);
+      } else {                                              // trailing block, warps 1..7
+        const int mm = m - 1;
+        const int bt = tid - 32;
+        const int lanes = lanes_per_dot_n(mm, kEigThreads - 32);
+        const int r = bt / lanes, sub = bt % lanes;
+        if (r < mm) {
+          const float vi = v[r + 1], wi = pc[r + 1] - K * vi;
+          float *row = A + (k + 2 + r) * ld + (k + 2);
+          int j = sub;
+          for (; j + lanes < mm; j += 2 * lanes) {
+            const float wj = pc[j + 1] - K * v[j + 1], wj2 = pc[j + lanes + 1] - K * v[j + lanes + 1];
+            row[j] -= vi * wj + wi * v[j + 1];
+            row[j + lanes] -= vi * wj2 + wi * v[j + lanes + 1];
+          }
+          if (j < mm) {
+            const float wj = pc[j + 1] - K * v[j + 1];
+            row[j] -= vi * wj + wi * v[j + 1];
+          }
+        }
       }
       __syncthreads();
-      // trailing block A2[1:, 1:] (= the next A2), row i - 1 of it per lane group
-      const bool next = (k + 3 < c);
-      const float bnext = next ? tau[k + 1] : 0.0f;
-      const float *vn = Vh + (k + 1) * c;                   // v_{k+1}, length m - 1
-      const int mm = m - 1;
-      const int lanes = lanes_per_dot(mm);
-      const int r = tid / lanes, sub = tid % lanes;
-      float sacc = 0.0f;
-      if (r < mm) {
-        const float vi = v[r + 1], wi = wv[r + 1];
-        float *row = A + (k + 2 + r) * ld + (k + 2);
-        float sacc2 = 0.0f;
-        int j = sub;
-        for (; j + lanes < mm; j += 2 * lanes) {             // two independent elements per trip
-          const float a2 = row[j] - (vi * wv[j + 1] + wi * v[j + 1]);
-          const float b2 = row[j + lanes] - (vi * wv[j + lanes + 1] + wi * v[j + lanes + 1]);
-          row[j] = a2;
-          row[j + lanes] = b2;
-          sacc = fmaf(a2, vn[j], sacc);
-          sacc2 = fmaf(b2, vn[j + lanes], sacc2);
-        }
-        if (j < mm) {
-          const float a2 = row[j] - (vi * wv[j + 1] + wi * v[j + 1]);
-          row[j] = a2;
-          sacc = fmaf(a2, vn[j], sacc);
-        }
-        sacc += sacc2;
-        if (!next) sacc = 0.0f;
-      }
-      sacc = group_sum_f(sacc, lanes);
-      if (next && r < mm && sub == 0) pn[r] = bnext * sacc;
+      if (k + 3 < c) matvec(k + 1);
       __syncthreads();
       float *t = pc; pc = pn; pn = t;
     }
@@ -499,46 +546,8 @@ eig_tridiag32_kernel(const double *G, int c, double *U, const int *skip) {
   // the reflectors from the last to the first -- per reflector one warp sum
   // per column, no block barrier.
   for (int i0 = warp * kBtCols; i0 < c; i0 += (kEigThreads / 32) * kBtCols) {
-    float z[kBtCols][4];
-#pragma unroll
-    for (int q = 0; q < kBtCols; ++q)
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const int r = lane + 32 * t, i = i0 + q;
-        z[q][t] = (r < c && i < c) ? Z[r * ld + i] : 0.0f;
-      }
-    for (int k = c - 3; k >= 0; --k) {
-      const float beta = tau[k];
-      if (beta == 0.0f) continue;
-      const float *v = Vh + k * c;                // v[r - k - 1] for rows r > k
-      float vr[4];
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const int r = lane + 32 * t;
-        vr[t] = (r > k && r < c) ? v[r - k - 1] : 0.0f;
-      }
-      float dq[kBtCols];
-#pragma unroll
-      for (int q = 0; q < kBtCols; ++q)
-        dq[q] = fmaf(vr[3], z[q][3], fmaf(vr[2], z[q][2], fmaf(vr[1], z[q][1], vr[0] * z[q][0])));
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int q = 0; q < kBtCols; ++q) dq[q] += __shfl_xor_sync(0xffffffffu, dq[q], o);
-#pragma unroll
-      for (int q = 0; q < kBtCols; ++q) {
-        const float f = beta * dq[q];
-#pragma unroll
-        for (int t = 0; t < 4; ++t) z[q][t] = fmaf(-f, vr[t], z[q][t]);
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < kBtCols; ++q)
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const int r = lane + 32 * t, i = i0 + q;
-        if (r < c && i < c) Z[r * ld + i] = z[q][t];
-      }
+    if (c <= 64) back_transform_cols<2>(Z, ld, Vh, tau, c, i0, lane);
+    else back_transform_cols<4>(Z, ld, Vh, tau, c, i0, lane);
   }
   __syncthreads();
   for (int e2 = tid; e2 < c * c; e2 += kEigThreads) {
@@ -892,7 +901,7 @@ __global__ void set_ranks_kernel(RankTable t, long long *ranks) {
   for (int i = threadIdx.x; i < t.count; i += blockDim.x) ranks[i] = t.r[i];
 }
 
-size_t eig_smem(int c) { return ((size_t)2 * c * (c + 1) + (size_t)c * c + 7 * (size_t)c) * sizeof(float); }
+size_t eig_smem(int c) { return ((size_t)2 * c * (c + 1) + (size_t)c * c + 6 * (size_t)c) * sizeof(float); }
 
 struct Layout {
   double *G, *U0, *U1, *UtU, *T, *S, *E, *H, *V0, *V1, *B1, *e, *sigma, *K, *tmp, *gs, *scale;
