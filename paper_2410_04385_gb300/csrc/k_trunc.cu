@@ -128,23 +128,24 @@ __device__ __forceinline__ float start_entry(int i, int j) {
 // that do not depend on its own recurrence.
 __device__ void tridiag_shifted_solve(const float *d, const float *e, int c, float lam,
                                       float tiny, float *ua, float *udu, float *udu2, float *b) {
+  // the pivoting choice is made with selects, not branches: the lanes of a
+  // warp solve different systems and would otherwise run both paths
   float ac = d[0] - lam, duc = (c > 1) ? e[0] : 0.0f, bc = b[0];
   for (int j = 0; j + 1 < c; ++j) {
-    float an = d[j + 1] - lam, dun = (j + 2 < c) ? e[j + 1] : 0.0f, bn = b[j + 1];
+    const float an = d[j + 1] - lam, dun = (j + 2 < c) ? e[j + 1] : 0.0f, bn = b[j + 1];
     const float lo = e[j];                       // sub-diagonal entry of row j + 1
-    if (fabsf(ac) >= fabsf(lo)) {
-      if (ac == 0.0f) ac = tiny;
-      const float f = __fdividef(lo, ac);
-      an = fmaf(-f, duc, an);
-      bn = fmaf(-f, bc, bn);
-      ua[j] = ac; udu[j] = duc; udu2[j] = 0.0f; b[j] = bc;
-    } else {                                     // rows j and j + 1 swap
-      const float f = __fdividef(ac, lo);
-      ua[j] = lo; udu[j] = an; udu2[j] = dun; b[j] = bn;
-      const float a2 = fmaf(-f, an, duc), du2n = -f * dun, b2 = fmaf(-f, bn, bc);
-      an = a2; dun = du2n; bn = b2;
-    }
-    ac = an; duc = dun; bc = bn;
+    const bool keep = fabsf(ac) >= fabsf(lo);    // else rows j and j + 1 swap
+    const float acp = (ac == 0.0f) ? tiny : ac;
+    const float piv = keep ? acp : lo;
+    const float f = __fdividef(keep ? lo : ac, piv);
+    ua[j] = piv;
+    udu[j] = keep ? duc : an;
+    udu2[j] = keep ? 0.0f : dun;
+    b[j] = keep ? bc : bn;
+    const float na = keep ? fmaf(-f, duc, an) : fmaf(-f, an, duc);
+    const float nd = keep ? dun : -f * dun;
+    const float nb = keep ? fmaf(-f, bc, bn) : fmaf(-f, bn, bc);
+    ac = na; duc = nd; bc = nb;
   }
   ua[c - 1] = ac; udu[c - 1] = 0.0f; udu2[c - 1] = 0.0f; b[c - 1] = bc;
   // Back substitution. A shift equal to an eigenvalue leaves pivots near zero:
