@@ -210,12 +210,19 @@ chol_inv_kernel(const double *Gg, double *Ut_g, double *y_g, int c, int m, int *
     s_dev = d0;
     s_diag_max = d1;
     s_trace = d2;
-    // pivot scaling 2^-2k with the largest diagonal in [0.5, 2) after scaling
+    // pivot scaling 2^-2k with the largest diagonal in [0.5, 2) after scaling;
+    // the exponent is read off the bits (frexp / ldexp are long sequences on
+    // this chain), with frexp / ldexp kept for subnormal or extreme values
+    const long long bits = __double_as_longlong(d1);
+    const int be = (int)((bits >> 52) & 0x7ff);
     int ex = 0;
-    if (d1 > 0.0) frexp(d1, &ex);
+    if (be > 0) ex = be - 1022;                 // d1 = m 2^ex, m in [0.5, 1)
+    else if (d1 > 0.0) frexp(d1, &ex);
     const int k = ex / 2;
-    s_sc = ldexp(1.0, -2 * k);
-    s_unsc = ldexp(1.0, -k);
+    s_sc = (-2 * k + 1023 >= 1 && -2 * k + 1023 <= 2046)
+               ? __longlong_as_double((long long)(-2 * k + 1023) << 52) : ldexp(1.0, -2 * k);
+    s_unsc = (-k + 1023 >= 1 && -k + 1023 <= 2046)
+                 ? __longlong_as_double((long long)(-k + 1023) << 52) : ldexp(1.0, -k);
   }
   __syncthreads();
   const double u = 1.1102230246251565e-16;
@@ -223,14 +230,6 @@ chol_inv_kernel(const double *Gg, double *Ut_g, double *y_g, int c, int m, int *
   if (s_dev <= 8.0 * c * u) {              // already orthonormal: nothing to apply
     if (tid == 0) { flags[0] = 1; flags[1] = 1; }
     return;
-  }
-  if (tid == 0) {
-    flags[1] = 0;
-    flags[2] += 1;
-    // ||G - I||_max <= 0.1/c puts every eigenvalue of G in [0.9, 1.1]
-    // (Gerschgorin): one more Cholesky QR pass orthonormalizes to working
-    // accuracy, so this pass is the last one
-    if (s_dev <= 0.1 / c) flags[0] = 1;
   }
 
   // -- Cholesky: first unshifted, then shifted if a pivot is not safely positive.
@@ -294,6 +293,15 @@ chol_inv_kernel(const double *Gg, double *Ut_g, double *y_g, int c, int m, int *
       Ut_g[i * c + l] = (l > i) ? G[i * ld + l] * yi2 : (l == i ? 1.0 : 0.0);
   }
   for (int i = tid; i < c; i += kCholThreads) y_g[i] = s_rinv[i];
+  // this pass applies; ||G - I||_max <= 0.1/c puts every eigenvalue of G in
+  // [0.9, 1.1] (Gerschgorin): one more Cholesky QR pass orthonormalizes to
+  // working accuracy, so this pass is the last one. Written last: the
+  // read-modify-write would otherwise sit on the first pivot's path.
+  if (tid == 0) {
+    flags[1] = 0;
+    flags[2] += 1;
+    if (s_dev <= 0.1 / c) flags[0] = 1;
+  }
 }
 
 // Q = S R^{-1} = (S U~^{-1}) D^{-1}, one warp per row, in place. The unit

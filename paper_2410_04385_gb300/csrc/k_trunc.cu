@@ -793,24 +793,29 @@ rank_kernel(const double *e, int c, int cap, const double *delta2, long long *ra
             int *perm, double *sigma) {
   pdl_enter();
   __shared__ double sorted[kMaxSmall];
-  __shared__ double keys[kMaxSmall];
+  __shared__ double tails[kMaxSmall + 1];
+  __shared__ long long keys[kMaxSmall];
   const int tid = threadIdx.x;
   // sort key: the energy, or -1 when it is not finite (NaN compares false
   // with everything, so without the key equal positions could repeat and
-  // perm would not be a permutation); staged in shared memory once, so the
-  // counting loop below waits on no global load
+  // perm would not be a permutation); staged in shared memory once as the
+  // order-preserving integer image of the double (x >= 0: its bits; x < 0:
+  // the bits with the magnitude bits flipped), so the counting loop below
+  // waits on no global load and compares on the integer pipe
   for (int i = tid; i < c; i += kThreads) {
     const double v = e[i];
-    keys[i] = isfinite(v) ? v : -1.0;
+    const long long b = __double_as_longlong(isfinite(v) ? v : -1.0);
+    keys[i] = b ^ ((b >> 63) & 0x7fffffffffffffffLL);
   }
   __syncthreads();
   for (int i = tid; i < c; i += kThreads) {
-    const double ei = keys[i];
+    const long long ki = keys[i];
     int pos = 0;
     for (int j = 0; j < c; ++j) {
-      const double ej = keys[j];
-      pos += (ej > ei) || (ej == ei && j < i);
+      const long long kj = keys[j];
+      pos += (kj > ki) || (kj == ki && j < i);
     }
+    const double ei = isfinite(e[i]) ? e[i] : -1.0;
     perm[pos] = i;
     sorted[pos] = ei;
     sigma[pos] = sqrt(fmax(ei, 0.0));
@@ -821,10 +826,10 @@ rank_kernel(const double *e, int c, int cap, const double *delta2, long long *ra
     // tail[rho] = sum_{p >= rho} sorted[p]; smallest rho >= 1 with tail <= delta^2
     double tail = 0.0;
     int rho = c;
-    double tails[kMaxSmall + 1];
     tails[c] = 0.0;
     for (int p = c - 1; p >= 0; --p) {
-      tail += fmax(sorted[p], 0.0);
+      const double sp = sorted[p];
+      tail += (sp > 0.0) ? sp : 0.0;
       tails[p] = tail;
     }
     for (int cand = 1; cand <= c; ++cand) {
