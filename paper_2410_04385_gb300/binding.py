@@ -60,7 +60,7 @@ _lib = None
 EXPORTS = ("tt_hadamard_recompress_plan", "tt_hadamard_recompress", "tt_round_plan", "tt_round",
            "tt_round_ex_plan", "tt_round_ex",
            "tt_dot_plan", "tt_dot", "tt_dot_noalloc", "tt_norm", "tt_sketch_tt",
-           "tt_philox4x32_10", "tt_launch_count", "tt_kernel_timer_start",
+           "tt_philox4x32_10", "tt_launch_count", "tt_gemm_autotune", "tt_kernel_timer_start",
            "tt_kernel_timer_stop", "tt_kernel_timer_stop_ex", "tt_device_error", "tt_hadamard_recompress_batch_plan",
            "tt_hadamard_recompress_batch", "tt_scale", "tt_laplacian", "tt_lincomb",
            "tt_status_string", "tt_batched_plan_create", "tt_batched_plan_bind", "tt_batched_run",
@@ -104,6 +104,7 @@ def load(path: Optional[str] = None):
     lib.tt_launch_count.restype = ctypes.c_int64
     lib.tt_launch_count.argtypes = []
     lib.tt_kernel_timer_start.argtypes = [ctypes.c_int32]
+    lib.tt_gemm_autotune.argtypes = [ctypes.c_int32]
     lib.tt_device_error.argtypes = [P(ctypes.c_int32)]
     lib.tt_device_status.argtypes = [P(ctypes.c_int32)]
     lib.tt_scale.argtypes = [vp, ctypes.c_int64, vp, vp]
@@ -187,6 +188,11 @@ def device_error() -> int:
     v = ctypes.c_int32(0)
     _check("tt_device_error", load().tt_device_error(ctypes.byref(v)))
     return int(v.value)
+
+
+def gemm_autotune(enable: bool) -> None:
+    """First-use timing of FP64 GEMM tilings (tt_gemm_autotune); on by default."""
+    _check("tt_gemm_autotune", load().tt_gemm_autotune(1 if enable else 0))
 
 
 def kernel_timer_start(capacity: int) -> None:

@@ -1770,6 +1770,11 @@ int tt_device_status(int32_t *status) {
   return TT_OK;
 }
 
+int tt_gemm_autotune(int32_t enable) {
+  hatt::set_gemm_autotune(enable != 0);
+  return TT_OK;
+}
+
 int tt_kernel_timer_start(int32_t capacity) {
   if (capacity < 1 || capacity > (1 << 20)) return TT_ERR_ARG;
   std::lock_guard<std::mutex> lk(hatt::g_timer.mu);

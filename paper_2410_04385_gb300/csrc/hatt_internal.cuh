@@ -123,6 +123,8 @@ struct Gemm {
 
 // Doubles of split-K scratch this GEMM needs (0 if it runs unsplit).
 size_t gemm_scratch_doubles(const Gemm &g);
+// First-use timing of candidate GEMM plans (on by default; see k_gemm.cu).
+void set_gemm_autotune(bool on);
 // TF32 / BF16 products on the tensor cores (tcgen05, FP32 accumulator in
 // tensor memory); gemm_f64 dispatches to them by g.prec.
 bool gemm_tc_supported(const Gemm &g);

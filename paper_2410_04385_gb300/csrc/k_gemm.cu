@@ -21,6 +21,7 @@
 //     whichever block that is, so results are bitwise reproducible and no
 //     second kernel is launched.
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <type_traits>
 #include <vector>
@@ -37,6 +38,7 @@ constexpr int kTargetBlocks = 4 * 152;
 
 struct Launch {
   int bm, bn, tiles_m, tiles_n, ksplit, kchunk, out;
+  bool pair = false;                     // gemm_pair_kernel: slots of two adjacent columns
 };
 
 // Operand of a low-precision product: FP64 -> FP32 (round to nearest even),
@@ -199,6 +201,170 @@ gemm_f64_kernel(Gemm g, int bm, int bn, int tiles_n, int tiles_m, int ksplit, in
   }
 }
 
+// Pair variant (FP64 only): an output slot is a row and two adjacent columns,
+// so one shared-memory load of A and one 16-byte load of B feed two DFMAs
+// (one and a half loads per DFMA against two). On the short-K batched
+// products of the sweep it is the faster form; on long split-K products the
+// single form is. Which one a shape runs is decided by timing (gemm_f64's
+// first-use tuner).
+constexpr int kLdB2 = kMaxTile + 2;      // even row stride: 16-byte aligned B rows
+
+template <int NQ, int OUT>
+__device__ __forceinline__ void mac_pair_n(int kdepth, const double (*As)[kMaxTile + 1],
+                                           const double (*Bs)[kLdB2], const int (&om)[OUT],
+                                           const int (&on)[OUT], double (&a0)[OUT],
+                                           double (&a1)[OUT]) {
+  if (kdepth == kBK) {
+#pragma unroll 4
+    for (int kk = 0; kk < kBK; ++kk) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const double a = As[kk][om[q]];
+        const double2 bb = *reinterpret_cast<const double2 *>(&Bs[kk][on[q]]);
+        a0[q] = fma(a, bb.x, a0[q]);
+        a1[q] = fma(a, bb.y, a1[q]);
+      }
+    }
+  } else {
+    for (int kk = 0; kk < kdepth; ++kk) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const double a = As[kk][om[q]];
+        const double2 bb = *reinterpret_cast<const double2 *>(&Bs[kk][on[q]]);
+        a0[q] = fma(a, bb.x, a0[q]);
+        a1[q] = fma(a, bb.y, a1[q]);
+      }
+    }
+  }
+}
+
+template <int NQ, int OUT>
+__device__ __forceinline__ void mac_pair_slots(int nqw, int kdepth, const double (*As)[kMaxTile + 1],
+                                               const double (*Bs)[kLdB2], const int (&om)[OUT],
+                                               const int (&on)[OUT], double (&a0)[OUT],
+                                               double (&a1)[OUT]) {
+  if (nqw <= 0) return;
+  if (nqw == NQ) {
+    mac_pair_n<NQ, OUT>(kdepth, As, Bs, om, on, a0, a1);
+    return;
+  }
+  if constexpr (NQ < OUT) mac_pair_slots<NQ + 1, OUT>(nqw, kdepth, As, Bs, om, on, a0, a1);
+}
+
+template <int OUT>
+__global__ void __launch_bounds__(kThreads)
+gemm_pair_kernel(Gemm g, int bm, int bn, int tiles_n, int tiles_m, int ksplit, int kchunk,
+                 double *partial, int *counters) {
+  pdl_enter();
+  if (g.skip_dev && *g.skip_dev) return;
+  __shared__ double As[kBK][kMaxTile + 1];
+  __shared__ __align__(16) double Bs[kBK][kLdB2];
+  __shared__ int s_last;
+  const int tid = threadIdx.x;
+  long long blk = blockIdx.x;
+  const int tn_i = (int)(blk % tiles_n); blk /= tiles_n;
+  const int tm_i = (int)(blk % tiles_m); blk /= tiles_m;
+  const int ks = (int)(blk % ksplit);
+  const int b = (int)(blk / ksplit);
+  const int b1 = b / g.bdiv, b2 = b % g.bdiv;
+  const double *A = g.A + b1 * g.sA1 + b2 * g.sA2;
+  const double *B = g.B + b1 * g.sB1 + b2 * g.sB2;
+  const int m0 = tm_i * bm, n0 = tn_i * bn;
+  const int kbeg = ks * kchunk;
+  const int kend = min(g.K, kbeg + kchunk);
+  const int bn2 = (bn + 1) / 2, bnp = 2 * bn2;   // column pairs; an odd tail column pairs with zero
+  const int slots = bm * bn2;
+
+  int om[OUT], on[OUT];
+  double a0[OUT], a1[OUT];
+#pragma unroll
+  for (int q = 0; q < OUT; ++q) {
+    const int o = tid + kThreads * q;
+    om[q] = (o < slots) ? o / bn2 : 0;
+    on[q] = (o < slots) ? 2 * (o % bn2) : 0;
+    a0[q] = 0.0;
+    a1[q] = 0.0;
+  }
+  const int nq = (slots - tid + kThreads - 1) / kThreads;
+  const int nqw = __shfl_sync(0xffffffffu, nq, 0);
+
+  const bool a_kfast = (g.sAk == 1);
+  const bool b_nfast = (g.sBn == 1);
+  for (int kt = kbeg; kt < kend; kt += kBK) {
+    for (int e = tid; e < bm * kBK; e += kThreads) {
+      int mm, kk;
+      if (a_kfast) { mm = e / kBK; kk = e % kBK; } else { kk = e / bm; mm = e % bm; }
+      const int gm = m0 + mm, gk = kt + kk;
+      As[kk][mm] = (gm < g.M && gk < kend) ? A[gm * g.sAm + gk * g.sAk] : 0.0;
+    }
+    for (int e = tid; e < bnp * kBK; e += kThreads) {
+      int nn, kk;
+      if (b_nfast) { kk = e / bnp; nn = e % bnp; } else { nn = e / kBK; kk = e % kBK; }
+      const int gn = n0 + nn, gk = kt + kk;
+      Bs[kk][nn] = (nn < bn && gn < g.N && gk < kend) ? B[gk * g.sBk + gn * g.sBn] : 0.0;
+    }
+    __syncthreads();
+    mac_pair_slots<1, OUT>(nqw, min(kBK, kend - kt), As, Bs, om, on, a0, a1);
+    __syncthreads();
+  }
+
+  const double alpha = g.alpha * (g.alpha_dev ? *g.alpha_dev : 1.0);
+  double *C = g.C + b1 * g.sC1 + b2 * g.sC2;
+  if (ksplit > 1) {
+    const long long mn = (long long)g.M * g.N;
+    const double *P0 = partial + (long long)b * ksplit * mn;
+    double *P = partial + ((long long)b * ksplit + ks) * mn;
+#pragma unroll
+    for (int q = 0; q < OUT; ++q) {
+      if (q >= nq) break;
+      const int gm = m0 + om[q], gn = n0 + on[q];
+      if (gm >= g.M) continue;
+      if (on[q] < bn && gn < g.N) P[(long long)gm * g.N + gn] = a0[q];
+      if (on[q] + 1 < bn && gn + 1 < g.N) P[(long long)gm * g.N + gn + 1] = a1[q];
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+      const int t = (b * tiles_m + tm_i) * tiles_n + tn_i;
+      const int prev = atomicAdd(&counters[t], 1);
+      s_last = (prev == ksplit - 1);
+      if (s_last) counters[t] = 0;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+#pragma unroll
+    for (int q = 0; q < OUT; ++q) {
+      if (q >= nq) break;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int gm = m0 + om[q], gn = n0 + on[q] + h;
+        if (gm >= g.M || on[q] + h >= bn || gn >= g.N) continue;
+        const long long e = (long long)gm * g.N + gn;
+        const double own = h ? a1[q] : a0[q];
+        double sum = 0.0;
+        for (int k = 0; k < ksplit; ++k) sum += (k == ks) ? own : __ldcg(P0 + k * mn + e);
+        double *c = C + gm * g.sCm + gn * g.sCn;
+        const double v = alpha * sum;
+        *c = (g.beta != 0.0) ? fma(g.beta, *c, v) : v;
+      }
+    }
+    return;
+  }
+#pragma unroll
+  for (int q = 0; q < OUT; ++q) {
+    if (q >= nq) break;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int gm = m0 + om[q], gn = n0 + on[q] + h;
+      if (gm >= g.M || on[q] + h >= bn || gn >= g.N) continue;
+      double *c = C + gm * g.sCm + gn * g.sCn;
+      const double v = alpha * (h ? a1[q] : a0[q]);
+      *c = (g.beta != 0.0) ? fma(g.beta, *c, v) : v;
+    }
+  }
+}
+
 long long ceil_div(long long a, long long b) { return (a + b - 1) / b; }
 
 // Tile edge for a dimension X with edge cap `cap`: X itself if it fits, else
@@ -243,7 +409,7 @@ int out_slots(long long outs) {
 //   split-K: the last block of each tile re-reads the tile's ksplit partial
 //         sums from L2 (~64 bytes per clock per SM) before it writes C; the
 //         busiest SM does ceil(tiles / 152) such reductions.
-double model_clocks(const Gemm &g, int bm, int bn, long long ksplit) {
+double model_clocks(const Gemm &g, int bm, int bn, long long ksplit, bool pair = false) {
   const long long tiles = ceil_div(g.M, bm) * ceil_div(g.N, bn) * (long long)g.batch;
   const long long kchunk = ceil_div(ceil_div(g.K, ksplit), kBK) * kBK;
   const long long nsplit = ceil_div(g.K, kchunk);
@@ -251,10 +417,11 @@ double model_clocks(const Gemm &g, int bm, int bn, long long ksplit) {
   const long long per_sm = ceil_div(blocks, 152);
   const long long kdepth = std::min<long long>(kchunk, g.K);
   const long long outs = (long long)bm * bn;
-  const int out = out_slots(outs);
+  const long long slots = pair ? (long long)bm * ((bn + 1) / 2) : outs;
+  const int out = out_slots(slots);
   const int resident = out <= 4 ? 4 : out <= 8 ? 3 : 2;
   const double ktiles = (double)ceil_div(kdepth, kBK);
-  double t = per_sm * (double)kdepth * block_dfma_clocks(outs) +
+  double t = per_sm * (double)kdepth * block_dfma_clocks(slots) * (pair ? 2.0 : 1.0) +
              ceil_div(per_sm, resident) * ktiles * 450.0 + 1500.0;
   if (nsplit > 1)
     t += (double)ceil_div(tiles, 152) * (600.0 + (double)nsplit * outs * 8.0 / 64.0);
@@ -277,16 +444,33 @@ int edge_candidates(int X, int *out) {
   return n;
 }
 
-Launch plan_search(const Gemm &g) {
-  double best = 1e300;
+// Normalizes a (bm, bn, ksplit) choice: tile counts, output slots per
+// thread, the K chunk and the number of K slices that chunk gives.
+Launch finalize(const Gemm &g, int bm, int bn, long long ksplit, bool pair) {
   Launch L{};
+  L.bm = bm;
+  L.bn = bn;
+  L.pair = pair;
+  L.tiles_m = (int)ceil_div(g.M, bm);
+  L.tiles_n = (int)ceil_div(g.N, bn);
+  L.out = out_slots(pair ? (long long)bm * ((bn + 1) / 2) : (long long)bm * bn);
+  const long long kchunk = ceil_div(ceil_div(g.K, ksplit), kBK) * kBK;
+  L.kchunk = (int)std::max<long long>(kchunk, kBK);
+  L.ksplit = (int)ceil_div(g.K, L.kchunk);
+  return L;
+}
+
+// Every (tile, K split) candidate with its model clocks, single or pair form.
+void plan_candidates(const Gemm &g, bool pair, std::vector<std::pair<double, Launch>> &out) {
   int em[kMaxTile + 8], en[kMaxTile + 8];
   const int nm = edge_candidates(g.M, em), nn = edge_candidates(g.N, en);
   for (int j = 0; j < nn; ++j) {
     const int bn = en[j];
     for (int i = 0; i < nm; ++i) {
       const int bm = em[i];
-      if ((long long)bm * bn > (long long)kThreads * kMaxOut) continue;
+      const long long slots = pair ? (long long)bm * ((bn + 1) / 2) : (long long)bm * bn;
+      if (slots > (long long)kThreads * (pair ? 8 : kMaxOut)) continue;
+      if (pair && bn < 2) continue;
       const long long tiles = ceil_div(g.M, bm) * ceil_div(g.N, bn) * (long long)g.batch;
       const long long kmax = ceil_div(g.K, kBK);
       long long cands[12];
@@ -296,22 +480,22 @@ Launch plan_search(const Gemm &g) {
       cands[nc++] = std::min(kmax, std::max<long long>(1, ceil_div(152, tiles)));
       for (int c = 0; c < nc; ++c) {
         if (cands[c] > 1 && tiles > kTileCounters) continue;   // one counter per tile
-        const double t = model_clocks(g, bm, bn, cands[c]);
-        if (t < best) {
-          best = t;
-          L.bm = bm;
-          L.bn = bn;
-          L.ksplit = (int)cands[c];
-        }
+        out.push_back({model_clocks(g, bm, bn, cands[c], pair), finalize(g, bm, bn, cands[c], pair)});
       }
     }
   }
-  L.tiles_m = (int)ceil_div(g.M, L.bm);
-  L.tiles_n = (int)ceil_div(g.N, L.bn);
-  L.out = out_slots((long long)L.bm * L.bn);
-  const long long kchunk = ceil_div(ceil_div(g.K, L.ksplit), kBK) * kBK;
-  L.kchunk = (int)std::max<long long>(kchunk, kBK);
-  L.ksplit = (int)ceil_div(g.K, L.kchunk);
+}
+
+Launch plan_search(const Gemm &g) {
+  std::vector<std::pair<double, Launch>> c;
+  plan_candidates(g, false, c);
+  double best = 1e300;
+  Launch L{};
+  for (const auto &x : c)
+    if (x.first < best) {
+      best = x.first;
+      L = x.second;
+    }
   return L;
 }
 
@@ -344,7 +528,174 @@ void launch_tile(const Gemm &g, const Launch &L, double *scratch, int *counters,
   note_launch();
 }
 
+template <int OUT>
+void launch_pair(const Gemm &g, const Launch &L, double *scratch, int *counters, cudaStream_t st) {
+  const long long blocks = (long long)L.tiles_n * L.tiles_m * L.ksplit * g.batch;
+  launch_k(gemm_pair_kernel<OUT>, (unsigned)blocks, kThreads, 0, st,
+      g, L.bm, L.bn, L.tiles_n, L.tiles_m, L.ksplit, L.kchunk, scratch, counters);
+  note_launch();
+}
+
+void launch_plan(const Gemm &g, const Launch &L, double *scratch, int *counters, cudaStream_t st) {
+  if (L.pair) {
+    switch (L.out) {
+      case 1: launch_pair<1>(g, L, scratch, counters, st); break;
+      case 2: launch_pair<2>(g, L, scratch, counters, st); break;
+      case 4: launch_pair<4>(g, L, scratch, counters, st); break;
+      default: launch_pair<8>(g, L, scratch, counters, st); break;
+    }
+    return;
+  }
+  switch (L.out) {
+    case 1: launch_tile<1>(g, L, scratch, counters, st); break;
+    case 2: launch_tile<2>(g, L, scratch, counters, st); break;
+    case 4: launch_tile<4>(g, L, scratch, counters, st); break;
+    case 8: launch_tile<8>(g, L, scratch, counters, st); break;
+    case 12: launch_tile<12>(g, L, scratch, counters, st); break;
+    default: launch_tile<16>(g, L, scratch, counters, st); break;
+  }
+}
+
+size_t split_doubles(const Gemm &g, const Launch &L) {
+  return L.ksplit > 1 ? (size_t)L.ksplit * g.batch * (size_t)g.M * g.N : 0;
+}
+
+// First-use tuner. The model picks within a few per cent on most shapes but
+// misses the better form on others (a sweep of the step's shapes: the best
+// of single and pair forms 366 us against the model's 403 us for one core's
+// products). So the first time a shape runs on a stream that is not being
+// captured, the model's best single and pair candidates are timed (one
+// warm-up and three launches each, the real operands, a scratch output) and
+// the fastest is kept for every later launch of the shape in the process --
+// also inside captured graphs. Candidates never need more split-K scratch than
+// the model's plan, the size callers allocated. A shape first met inside a
+// capture keeps the model's plan, and so do products under 1e7 flops and
+// every shape after the first 256 tuned in the process. Off by
+// tt_gemm_autotune(0).
+std::atomic<bool> g_autotune{true};
+constexpr double kTuneMinFlops = 1e7;    // smaller products keep the model's plan
+constexpr int kTuneMaxShapes = 256;      // per process: bounds the tuning time
+int g_tuned_shapes = 0;                  // guarded by g_exec_mu
+double *g_tune_out = nullptr;            // scratch output, grown as needed, guarded
+size_t g_tune_out_doubles = 0;           //   by g_tune_mu
+std::mutex g_tune_mu;
+
+struct ExecKey {
+  int M, N, K, batch, bdiv, prec;
+  bool a_kfast, b_nfast;
+  bool operator==(const ExecKey &o) const {
+    return M == o.M && N == o.N && K == o.K && batch == o.batch && bdiv == o.bdiv &&
+           prec == o.prec && a_kfast == o.a_kfast && b_nfast == o.b_nfast;
+  }
+};
+std::mutex g_exec_mu;
+std::vector<std::pair<ExecKey, Launch>> g_exec;
+
+ExecKey exec_key(const Gemm &g) {
+  return {g.M, g.N, g.K, g.batch, g.bdiv, g.prec, g.sAk == 1, g.sBn == 1};
+}
+
+Launch tune(const Gemm &g, const Launch &Lm, double *scratch, int *counters, cudaStream_t st) {
+  std::vector<std::pair<double, Launch>> cs, cp, pick;
+  plan_candidates(g, false, cs);
+  plan_candidates(g, true, cp);
+  const size_t room = scratch ? split_doubles(g, Lm) : 0;
+  auto ok = [&](const Launch &L) {
+    return split_doubles(g, L) <= room && (L.ksplit == 1 || counters != nullptr);
+  };
+  for (auto *v : {&cs, &cp}) {
+    std::sort(v->begin(), v->end(), [](const std::pair<double, Launch> &a,
+                                       const std::pair<double, Launch> &b) { return a.first < b.first; });
+    int taken = 0;
+    for (const auto &x : *v) {
+      if (taken == 6) break;
+      if (!ok(x.second)) continue;
+      pick.push_back(x);
+      ++taken;
+    }
+  }
+  if (pick.size() < 2) return Lm;
+  // scratch output with the layout of C (one buffer for all tuning, grown)
+  const long long b1max = (g.batch - 1) / g.bdiv, b2max = std::min(g.bdiv, g.batch) - 1;
+  const long long extent = b1max * g.sC1 + b2max * g.sC2 + (long long)(g.M - 1) * g.sCm +
+                           (long long)(g.N - 1) * g.sCn + 1;
+  if (extent <= 0 || extent > (64LL << 20)) return Lm;
+  std::lock_guard<std::mutex> tlock(g_tune_mu);
+  if ((size_t)extent > g_tune_out_doubles) {
+    if (g_tune_out) {
+      cudaStreamSynchronize(st);
+      cudaFree(g_tune_out);
+    }
+    g_tune_out = nullptr;
+    g_tune_out_doubles = 0;
+    if (cudaMalloc(&g_tune_out, (size_t)extent * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      g_tune_out = nullptr;
+      return Lm;
+    }
+    g_tune_out_doubles = (size_t)extent;
+  }
+  double *tmp = g_tune_out;
+  Gemm gt = g;
+  gt.C = tmp;
+  gt.skip_dev = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  Launch best = Lm;
+  float best_ms = 1e30f;
+  bool fine = cudaMemsetAsync(tmp, 0, (size_t)extent * sizeof(double), st) == cudaSuccess &&
+              cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+  for (size_t i = 0; fine && i < pick.size(); ++i) {
+    const Launch &L = pick[i].second;
+    launch_plan(gt, L, scratch, counters, st);
+    fine = cudaEventRecord(e0, st) == cudaSuccess;
+    for (int r = 0; fine && r < 3; ++r) launch_plan(gt, L, scratch, counters, st);
+    fine = fine && cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+           cudaGetLastError() == cudaSuccess;
+    float ms = 0.0f;
+    if (fine && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best_ms) {
+      best_ms = ms;
+      best = L;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamSynchronize(st);
+  cudaGetLastError();
+  return fine ? best : Lm;
+}
+
+// The plan a shape runs with: the tuned one once the shape has run (see tune).
+Launch exec_plan(const Gemm &g, double *scratch, int *counters, cudaStream_t st) {
+  const ExecKey key = exec_key(g);
+  {
+    std::lock_guard<std::mutex> lock(g_exec_mu);
+    for (const auto &e : g_exec)
+      if (e.first == key) return e.second;
+  }
+  Launch L = plan(g);
+  bool try_tune = g_autotune.load(std::memory_order_relaxed) && g.prec == kPrecFP64 &&
+                  2.0 * g.M * g.N * (double)g.K * g.batch >= kTuneMinFlops;
+  if (try_tune) {
+    std::lock_guard<std::mutex> lock(g_exec_mu);
+    try_tune = g_tuned_shapes < kTuneMaxShapes;
+    if (try_tune) ++g_tuned_shapes;
+  }
+  if (try_tune) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusActive;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone)
+      L = tune(g, L, scratch, counters, st);
+    cudaGetLastError();
+  }
+  std::lock_guard<std::mutex> lock(g_exec_mu);
+  for (const auto &e : g_exec)
+    if (e.first == key) return e.second;   // another thread got there first
+  if (g_exec.size() < 4096) g_exec.push_back({key, L});
+  return L;
+}
+
 }  // namespace
+
+void set_gemm_autotune(bool on) { g_autotune.store(on); }
 
 size_t gemm_scratch_doubles(const Gemm &g) {
   if (g.M <= 0 || g.N <= 0 || g.K <= 0) return 0;
@@ -371,20 +722,15 @@ cudaError_t gemm_f64(const Gemm &g, double *scratch, cudaStream_t st) {
     timer_end(slot, st, 2.0 * g.M * g.N * (double)g.K * g.batch, g.role);
     return e;
   }
-  const Launch L = plan(g);
   int *counters = tile_counters();
+  const Launch Lm = plan(g);
+  if (Lm.ksplit > 1 && (scratch == nullptr || counters == nullptr)) return cudaErrorInvalidValue;
+  const Launch L = exec_plan(g, scratch, counters, st);
   if (L.ksplit > 1 && (scratch == nullptr || counters == nullptr)) return cudaErrorInvalidValue;
   if ((long long)L.tiles_n * L.tiles_m * L.ksplit * g.batch >= (1LL << 31))
     return cudaErrorInvalidConfiguration;
   const int slot = timer_begin(st);
-  switch (L.out) {
-    case 1: launch_tile<1>(g, L, scratch, counters, st); break;
-    case 2: launch_tile<2>(g, L, scratch, counters, st); break;
-    case 4: launch_tile<4>(g, L, scratch, counters, st); break;
-    case 8: launch_tile<8>(g, L, scratch, counters, st); break;
-    case 12: launch_tile<12>(g, L, scratch, counters, st); break;
-    default: launch_tile<16>(g, L, scratch, counters, st); break;
-  }
+  launch_plan(g, L, scratch, counters, st);
   timer_end(slot, st, 2.0 * g.M * g.N * (double)g.K * g.batch, g.role);
   return cudaGetLastError();
 }
