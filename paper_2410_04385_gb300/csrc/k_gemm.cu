@@ -21,6 +21,8 @@
 //     whichever block that is, so results are bitwise reproducible and no
 //     second kernel is launched.
 #include <algorithm>
+#include <unordered_map>
+#include <array>
 #include <cstdlib>
 #include <cstring>
 #include <atomic>
@@ -501,19 +503,30 @@ Launch plan_search(const Gemm &g) {
   return L;
 }
 
-// Plans are cached per shape (the HaTT sequence repeats a few dozen shapes).
+// Plans are cached per shape in hash maps: launch-bound callers (power
+// iteration, small eager recompressions) look a plan up for every GEMM, and a
+// batch of uneven pairs brings thousands of shapes.
+struct ShapeHash {
+  size_t operator()(const std::array<int, 8> &k) const {
+    size_t h = 1469598103934665603ull;
+    for (int v : k) h = (h ^ (size_t)(unsigned)v) * 1099511628211ull;
+    return h;
+  }
+};
+using ShapeKey = std::array<int, 8>;
+
 Launch plan(const Gemm &g) {
-  struct Entry { int M, N, K, batch; Launch L; };
   static std::mutex mu;
-  static std::vector<Entry> cache;
+  static std::unordered_map<ShapeKey, Launch, ShapeHash> cache;
+  const ShapeKey key{g.M, g.N, g.K, g.batch, 0, 0, 0, 0};
   {
     std::lock_guard<std::mutex> lock(mu);
-    for (const Entry &e : cache)
-      if (e.M == g.M && e.N == g.N && e.K == g.K && e.batch == g.batch) return e.L;
+    const auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
   }
   const Launch L = plan_search(g);
   std::lock_guard<std::mutex> lock(mu);
-  if (cache.size() < 4096) cache.push_back({g.M, g.N, g.K, g.batch, L});
+  if (cache.size() < (1u << 16)) cache.emplace(key, L);
   return L;
 }
 
@@ -582,19 +595,11 @@ double *g_tune_out = nullptr;            // scratch output, grown as needed, gua
 size_t g_tune_out_doubles = 0;           //   by g_tune_mu
 std::mutex g_tune_mu;
 
-struct ExecKey {
-  int M, N, K, batch, bdiv, prec;
-  bool a_kfast, b_nfast;
-  bool operator==(const ExecKey &o) const {
-    return M == o.M && N == o.N && K == o.K && batch == o.batch && bdiv == o.bdiv &&
-           prec == o.prec && a_kfast == o.a_kfast && b_nfast == o.b_nfast;
-  }
-};
 std::mutex g_exec_mu;
-std::vector<std::pair<ExecKey, Launch>> g_exec;
+std::unordered_map<ShapeKey, Launch, ShapeHash> g_exec;
 
-ExecKey exec_key(const Gemm &g) {
-  return {g.M, g.N, g.K, g.batch, g.bdiv, g.prec, g.sAk == 1, g.sBn == 1};
+ShapeKey exec_key(const Gemm &g) {
+  return {g.M, g.N, g.K, g.batch, g.bdiv, g.prec, g.sAk == 1 ? 1 : 0, g.sBn == 1 ? 1 : 0};
 }
 
 Launch tune(const Gemm &g, const Launch &Lm, double *scratch, int *counters, cudaStream_t st) {
@@ -668,11 +673,11 @@ Launch tune(const Gemm &g, const Launch &Lm, double *scratch, int *counters, cud
 
 // The plan a shape runs with: the tuned one once the shape has run (see tune).
 Launch exec_plan(const Gemm &g, double *scratch, int *counters, cudaStream_t st) {
-  const ExecKey key = exec_key(g);
+  const ShapeKey key = exec_key(g);
   {
     std::lock_guard<std::mutex> lock(g_exec_mu);
-    for (const auto &e : g_exec)
-      if (e.first == key) return e.second;
+    const auto it = g_exec.find(key);
+    if (it != g_exec.end()) return it->second;
   }
   Launch L = plan(g);
   // HATT_GEMM_FORM=pair (read once): every FP64 shape takes the model's best
@@ -708,9 +713,9 @@ Launch exec_plan(const Gemm &g, double *scratch, int *counters, cudaStream_t st)
     cudaGetLastError();
   }
   std::lock_guard<std::mutex> lock(g_exec_mu);
-  for (const auto &e : g_exec)
-    if (e.first == key) return e.second;   // another thread got there first
-  if (g_exec.size() < 4096) g_exec.push_back({key, L});
+  const auto it = g_exec.find(key);
+  if (it != g_exec.end()) return it->second;   // another thread got there first
+  if (g_exec.size() < (1u << 16)) g_exec.emplace(key, L);
   return L;
 }
 
