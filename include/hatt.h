@@ -339,14 +339,17 @@ int tt_batched_tune_cache(const char *path, int32_t save);
 /* FP64 GEMM plan tuning, an implementation detail with no counterpart in the
  * paper. The first time a GEMM shape (sizes, batch, operand layout) runs on a
  * stream that is not being captured, the library times its model's best
- * candidate tilings (single and paired-column forms, real operands, a scratch
- * output, ~20 launches) and keeps the fastest for every later launch of that
- * shape in the process, including inside captured graphs; a shape first met
- * during a capture keeps the model's choice, and so do products under 1e7
- * flops and shapes beyond the first 256 tuned. Results differ between tilings
- * only by the order of FP64 rounding. tt_gemm_autotune(0) turns the timing
- * off for shapes not yet run (they keep the model's choice), 1 turns it on
- * (the default). Returns TT_OK; the setting is process-wide. */
+ * candidate tilings (single and paired-column forms, ~50 launches on the
+ * call's own operands and output) and keeps the fastest for every later
+ * launch of that shape in the process, including inside captured graphs.
+ * This synchronizes the caller's stream once per tuned shape and allocates
+ * nothing. A shape first met during a capture keeps the model's choice, and
+ * so do products under 1e7 flops, products that accumulate into their output
+ * or carry a device skip flag, and shapes beyond the first 256 tuned. Results
+ * differ between tilings only by the order of FP64 rounding.
+ * tt_gemm_autotune(0) turns the timing off for shapes not yet run (they keep
+ * the model's choice), 1 turns it on (the default). Returns TT_OK; the
+ * setting is process-wide. */
 int tt_gemm_autotune(int32_t enable);
 
 /* Kernel timer, a diagnostic with no counterpart in the paper: between

@@ -580,20 +580,43 @@ size_t split_doubles(const Gemm &g, const Launch &L) {
 // of single and pair forms 366 us against the model's 403 us for one core's
 // products). So the first time a shape runs on a stream that is not being
 // captured, the model's best single and pair candidates are timed (one
-// warm-up and three launches each, the real operands, a scratch output) and
-// the fastest is kept for every later launch of the shape in the process --
-// also inside captured graphs. Candidates never need more split-K scratch than
-// the model's plan, the size callers allocated. A shape first met inside a
-// capture keeps the model's plan, and so do products under 1e7 flops and
-// every shape after the first 256 tuned in the process. Off by
-// tt_gemm_autotune(0).
+// warm-up and three launches each, on the call's own operands and output)
+// and the fastest is kept for every later launch of the shape in the
+// process -- also inside captured graphs. Candidates never need more split-K
+// scratch than the model's plan, the size callers allocated; nothing is
+// allocated; the stream is synchronized once per tuned shape. A shape first
+// met inside a capture keeps the model's plan, and so do products under 1e7
+// flops, products that accumulate into C or carry a skip flag or whose C
+// overlaps an operand, and every shape after the first 256 tuned in the
+// process. Off by tt_gemm_autotune(0).
 std::atomic<bool> g_autotune{true};
 constexpr double kTuneMinFlops = 1e7;    // smaller products keep the model's plan
 constexpr int kTuneMaxShapes = 256;      // per process: bounds the tuning time
 int g_tuned_shapes = 0;                  // guarded by g_exec_mu
-double *g_tune_out = nullptr;            // scratch output, grown as needed, guarded
-size_t g_tune_out_doubles = 0;           //   by g_tune_mu
-std::mutex g_tune_mu;
+
+// Elements spanned by an operand with the given strides (all non-negative).
+long long span(const Gemm &g, long long s1, long long s2, long long sr, long long sc, int rows,
+               int cols) {
+  const long long b1max = (g.batch - 1) / g.bdiv, b2max = std::min(g.bdiv, g.batch) - 1;
+  return b1max * s1 + b2max * s2 + (long long)(rows - 1) * sr + (long long)(cols - 1) * sc + 1;
+}
+
+// Products the tuner may run repeatedly with C as their output.
+bool tunable(const Gemm &g) {
+  if (g.beta != 0.0 || g.skip_dev != nullptr || g.C == nullptr) return false;
+  if (g.sA1 < 0 || g.sA2 < 0 || g.sAm < 0 || g.sAk < 0 || g.sB1 < 0 || g.sB2 < 0 || g.sBk < 0 ||
+      g.sBn < 0 || g.sC1 < 0 || g.sC2 < 0 || g.sCm < 0 || g.sCn < 0)
+    return false;
+  const char *c0 = reinterpret_cast<const char *>(g.C);
+  const char *c1 = c0 + span(g, g.sC1, g.sC2, g.sCm, g.sCn, g.M, g.N) * (long long)sizeof(double);
+  auto apart = [&](const double *x, long long n) {
+    const char *x0 = reinterpret_cast<const char *>(x);
+    const char *x1 = x0 + n * (long long)sizeof(double);
+    return x == nullptr || x1 <= c0 || c1 <= x0;
+  };
+  return apart(g.A, span(g, g.sA1, g.sA2, g.sAm, g.sAk, g.M, g.K)) &&
+         apart(g.B, span(g, g.sB1, g.sB2, g.sBk, g.sBn, g.K, g.N));
+}
 
 std::mutex g_exec_mu;
 std::unordered_map<ShapeKey, Launch, ShapeHash> g_exec;
@@ -622,35 +645,14 @@ Launch tune(const Gemm &g, const Launch &Lm, double *scratch, int *counters, cud
     }
   }
   if (pick.size() < 2) return Lm;
-  // scratch output with the layout of C (one buffer for all tuning, grown)
-  const long long b1max = (g.batch - 1) / g.bdiv, b2max = std::min(g.bdiv, g.batch) - 1;
-  const long long extent = b1max * g.sC1 + b2max * g.sC2 + (long long)(g.M - 1) * g.sCm +
-                           (long long)(g.N - 1) * g.sCn + 1;
-  if (extent <= 0 || extent > (64LL << 20)) return Lm;
-  std::lock_guard<std::mutex> tlock(g_tune_mu);
-  if ((size_t)extent > g_tune_out_doubles) {
-    if (g_tune_out) {
-      cudaStreamSynchronize(st);
-      cudaFree(g_tune_out);
-    }
-    g_tune_out = nullptr;
-    g_tune_out_doubles = 0;
-    if (cudaMalloc(&g_tune_out, (size_t)extent * sizeof(double)) != cudaSuccess) {
-      cudaGetLastError();
-      g_tune_out = nullptr;
-      return Lm;
-    }
-    g_tune_out_doubles = (size_t)extent;
-  }
-  double *tmp = g_tune_out;
+  // the candidates write C itself: every one computes the same product of
+  // the same operands (exec_plan tunes only products with beta = 0, no skip
+  // flag and C apart from A and B), and the chosen plan's launch follows
   Gemm gt = g;
-  gt.C = tmp;
-  gt.skip_dev = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   Launch best = Lm;
   float best_ms = 1e30f;
-  bool fine = cudaMemsetAsync(tmp, 0, (size_t)extent * sizeof(double), st) == cudaSuccess &&
-              cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+  bool fine = cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
   for (size_t i = 0; fine && i < pick.size(); ++i) {
     const Launch &L = pick[i].second;
     launch_plan(gt, L, scratch, counters, st);
@@ -700,7 +702,8 @@ Launch exec_plan(const Gemm &g, double *scratch, int *counters, cudaStream_t st)
       }
   }
   bool try_tune = !force_pair && g_autotune.load(std::memory_order_relaxed) &&
-                  g.prec == kPrecFP64 && 2.0 * g.M * g.N * (double)g.K * g.batch >= kTuneMinFlops;
+                  g.prec == kPrecFP64 && 2.0 * g.M * g.N * (double)g.K * g.batch >= kTuneMinFlops &&
+                  tunable(g);
   if (try_tune) {
     std::lock_guard<std::mutex> lock(g_exec_mu);
     try_tune = g_tuned_shapes < kTuneMaxShapes;
