@@ -367,9 +367,10 @@ def run_hatt2_example1b(binding, workloads, dev, samples=20000, reps=5):
     """Example 1b: y = sum_{j<=60} a_j sin(j t), z = sum_j b_j cos(j t), a, b ~
     U[0.1, 10.1] (seeded), t on 20^7 points folded to a d = 7, n = 20 TT and
     rounded to 1e-14 (tt_round); HaTT-1 against HaTT-2 at l = 20 over the
-    paper's ep values, and over l = 10..60 at ep = 1e-3. Wall time per call
-    (eager: HaTT-2 synchronizes once per core) and the relative error on
-    sampled entries against the closed form y(t) z(t)."""
+    paper's ep values, and over l = 10..60 at ep = 1e-3. Wall time per call,
+    eager and as a CUDA-graph replay (both variants keep their ranks on the
+    device), and the relative error on sampled entries against the closed
+    form y(t) z(t)."""
     import numpy as np
     import torch
     d, n, J = 7, 20, 60
@@ -397,8 +398,20 @@ def run_hatt2_example1b(binding, workloads, dev, samples=20000, reps=5):
             ts.append(time.perf_counter() - t0)
         x = sampled_entries([c.cpu().numpy() for c in h.result()], idx)
         err = float(np.sqrt(np.sum((x - exact) ** 2) / np.sum(exact ** 2)))
+        h.capture()
+        h.replay()
+        torch.cuda.synchronize()
+        tg = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            h.replay()
+            torch.cuda.synchronize()
+            tg.append(time.perf_counter() - t0)
+        xg = sampled_entries([c.cpu().numpy() for c in h.result()], idx)
         return {"variant": variant, "ep": ep if variant == 2 else None, "ell": ell,
-                "ms_per_call": 1000.0 * float(np.median(ts)), "rel_error_sampled": err}
+                "ms_per_call": 1000.0 * float(np.median(ts)),
+                "ms_per_graph_replay": 1000.0 * float(np.median(tg)), "rel_error_sampled": err,
+                "graph_equals_eager": bool(np.array_equal(x, xg))}
 
     rows = [one(20, 1, 0.0)] + [one(20, 2, ep) for ep in (0.95, 1e-1, 4e-2, 1e-3, 1e-5, 1e-10, 1e-14)]
     sweep = [one(ell, v, 1e-3) for ell in (10, 20, 30, 40, 50, 60) for v in (1, 2)]

@@ -103,10 +103,11 @@ typedef enum {
  *                contraction runs on R_k <= l_{k+1} columns. The singular
  *                values come from the Gram matrix W^T W (FP64), so directions
  *                below ~1e-8 sigma_max are not resolved and ep < 1e-8 keeps
- *                them (the result is then HaTT-1's up to rounding). R_k is read
- *                on the host: the call synchronizes `stream` once per core and
- *                returns TT_ERR_ARG while the stream is being captured; the
- *                batched entry point rejects it.
+ *                them (the result is then HaTT-1's up to rounding). R_k stays
+ *                in device memory (the contractions read it there), so the
+ *                call does not synchronize and can be captured; the
+ *                workspace is planned for R_k = l_{k+1}. The batched entry
+ *                point takes it; the persistent engine does not.
  *   ep           HaTT-2 truncation threshold, 0 <= ep < 1 (ignored by variant 1)
  *   fixed_ranks  0 = the output cores are compacted to the ranks the truncation kept and
  *                X->r is written from the device by an asynchronous copy (valid once the
@@ -172,8 +173,7 @@ int tt_hadamard_recompress_plan(const tt_t *Y, const tt_t *Z, const tt_opts *opt
  * Synchronization: with tol > 0 and a stream that is not being captured, the
  * truncation sweep reads one device flag per cluster level (a short
  * synchronization of `stream`) to stop launching levels that would be skipped;
- * a captured stream gets every level instead. Variant 2 synchronizes once per
- * core (see tt_opts). */
+ * a captured stream gets every level instead. */
 int tt_hadamard_recompress(const tt_t *Y, const tt_t *Z, const tt_opts *opts, tt_t *X,
                            void *workspace, size_t workspace_bytes, void *stream);
 

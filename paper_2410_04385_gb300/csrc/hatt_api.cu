@@ -141,6 +141,7 @@ struct Runner {
   }
   void gemm(const Gemm &g) {
     if (rec) {
+      if (g.dyn_dev) err = cudaErrorInvalidValue;   // the engine takes host extents only
       RecOp o{RecOp::kGemm};
       o.g = g;
       rec->push_back(o);
@@ -384,12 +385,15 @@ HattBufs carve_hatt(Ws &ws, const HattArgs &a) {
 //   G = W^T W, V = eig(G), U S = W V / ||W||  (right singular vectors from the
 //   Gram matrix; column norms of W V are the singular values),
 //   keep the R columns with sigma > ep * sigma_max, then with R terms
-//   Rv[l][i][g]       = sum_c R_k[l][i][c] V_R[c][g]
+//   Rv[l][g][i]       = sum_c R_k[l][i][c] V_R[c][g]
 //   P2[i][a'][b][g]   = sum_b' Z_k[b][i][b'] (U S)_R[a' s1 + b'][g]
-//   P3[a][b][i][g]    = sum_a' Y_k[a][i][a'] P2[i][a'][b][g]
-//   W^{(k)}[a s0 + b][l] = sum_{i,g} P3[a][b][i][g] Rv[l][i][g]
-// (the W_L W_R^T form: W_L = P3, W_R = Rv). R is read on the host, so this
-// variant synchronizes the stream once per core.
+//   P3[a][b][g][i]    = sum_a' Y_k[a][i][a'] P2[i][a'][b][g]
+//   W^{(k)}[a s0 + b][l] = sum_{g,i} P3[a][b][g][i] Rv[l][g][i]
+// (the W_L W_R^T form: W_L = P3, W_R = Rv). R stays in device memory: the
+// buffers are laid out for R = c (leading dimension c for g), the products
+// run over the first R columns (Rv, P2, P3) and the first n_k R terms of the
+// last one (g outer, i inner, so the live terms are a prefix), all read R
+// on the device. No host synchronization: the step can be captured.
 void hpcrl2_step(Runner &run, const HattArgs &a, const HattBufs &b, int k, double *Wnext,
                  double *Wout) {
   const auto &n = a.n;
@@ -400,6 +404,7 @@ void hpcrl2_step(Runner &run, const HattArgs &a, const HattBufs &b, int k, doubl
   const int l0 = (int)l[k], c = (int)l[k + 1], nk = (int)n[k];
   const int x = r1 * s1;
   const double *Rk = run.exec ? b.R + b.Roff[k] : nullptr;
+  const int *Rdev = run.exec ? b.Rdev : nullptr;
   {   // G = W^T W
     Gemm g;
     g.M = c; g.N = c; g.K = x;
@@ -422,65 +427,54 @@ void hpcrl2_step(Runner &run, const HattArgs &a, const HattBufs &b, int k, doubl
     g.alpha_dev = run.exec ? b.winv + (k + 1) : nullptr;
     run.gemm(g);
   }
-  auto contract = [&](int R) {
-    {   // Rv = R_k V_R
-      Gemm g;
-      g.role = hatt::kRoleMethod;
-      g.M = l0 * nk; g.N = R; g.K = c;
-      g.A = Rk; g.sAm = c; g.sAk = 1;
-      g.B = b.VR; g.sBk = R; g.sBn = 1;
-      g.C = b.Rv; g.sCm = R; g.sCn = 1;
-      g.prec = a.prec;
-      run.gemm(g);
-    }
-    {   // P2, batched over (i, a')
-      Gemm g;
-      g.role = hatt::kRoleMethod;
-      g.M = s0; g.N = R; g.K = s1;
-      g.batch = nk * r1; g.bdiv = r1;
-      g.A = a.Z ? a.Z[k] : nullptr; g.sA1 = s1; g.sA2 = 0; g.sAm = (ll)nk * s1; g.sAk = 1;
-      g.B = b.UR; g.sB1 = 0; g.sB2 = (ll)s1 * R; g.sBk = R; g.sBn = 1;
-      g.C = b.P2; g.sC1 = (ll)r1 * s0 * R; g.sC2 = (ll)s0 * R; g.sCm = R; g.sCn = 1;
-      g.prec = a.prec;
-      run.gemm(g);
-    }
-    {   // P3, batched over (i, b)
-      Gemm g;
-      g.role = hatt::kRoleMethod;
-      g.M = r0; g.N = R; g.K = r1;
-      g.batch = nk * s0; g.bdiv = s0;
-      g.A = a.Y ? a.Y[k] : nullptr; g.sA1 = r1; g.sA2 = 0; g.sAm = (ll)nk * r1; g.sAk = 1;
-      g.B = b.P2; g.sB1 = (ll)r1 * s0 * R; g.sB2 = R; g.sBk = (ll)s0 * R; g.sBn = 1;
-      g.C = b.P3; g.sC1 = R; g.sC2 = (ll)nk * R; g.sCm = (ll)s0 * nk * R; g.sCn = 1;
-      g.prec = a.prec;
-      run.gemm(g);
-    }
-    {   // W^{(k)} = W_L W_R^T
-      Gemm g;
-      g.role = hatt::kRoleMethod;
-      g.M = r0 * s0; g.N = l0; g.K = nk * R;
-      g.A = b.P3; g.sAm = (ll)nk * R; g.sAk = 1;
-      g.B = b.Rv; g.sBk = 1; g.sBn = (ll)nk * R;
-      g.C = Wout; g.sCm = l0; g.sCn = 1;
-      g.prec = a.prec;
-      run.gemm(g);
-    }
-  };
-  if (!run.exec) {   // planning: every R the selection can return
-    for (int R = 1; R <= c; ++R) contract(R);
-    return;
+  if (run.live()) run.check(hatt::select_directions(b.Uf, b.V2, x, c, a.ep, b.UR, b.VR, b.Rdev, run.st));
+  {   // Rv = R_k V_R, batched over l
+    Gemm g;
+    g.role = hatt::kRoleMethod;
+    g.M = nk; g.N = c; g.K = c;
+    g.batch = l0; g.bdiv = 1;
+    g.A = Rk; g.sA1 = (ll)nk * c; g.sAm = c; g.sAk = 1;
+    g.B = b.VR; g.sBk = c; g.sBn = 1;
+    g.C = b.Rv; g.sC1 = (ll)c * nk; g.sCm = 1; g.sCn = nk;
+    g.dyn_dev = Rdev; g.dyn_n = 1;
+    g.prec = a.prec;
+    run.gemm(g);
   }
-  if (!run.live()) return;
-  run.check(hatt::select_directions(b.Uf, b.V2, x, c, a.ep, b.UR, b.VR, b.Rdev, run.st));
-  int R = 0;
-  run.check(cudaMemcpyAsync(&R, b.Rdev, sizeof(int), cudaMemcpyDeviceToHost, run.st));
-  run.check(cudaStreamSynchronize(run.st));
-  if (!run.live()) return;
-  if (R < 1 || R > c) {
-    run.check(cudaErrorUnknown);
-    return;
+  {   // P2, batched over (i, a')
+    Gemm g;
+    g.role = hatt::kRoleMethod;
+    g.M = s0; g.N = c; g.K = s1;
+    g.batch = nk * r1; g.bdiv = r1;
+    g.A = a.Z ? a.Z[k] : nullptr; g.sA1 = s1; g.sA2 = 0; g.sAm = (ll)nk * s1; g.sAk = 1;
+    g.B = b.UR; g.sB1 = 0; g.sB2 = (ll)s1 * c; g.sBk = c; g.sBn = 1;
+    g.C = b.P2; g.sC1 = (ll)r1 * s0 * c; g.sC2 = (ll)s0 * c; g.sCm = c; g.sCn = 1;
+    g.dyn_dev = Rdev; g.dyn_n = 1;
+    g.prec = a.prec;
+    run.gemm(g);
   }
-  contract(R);
+  {   // P3, batched over (i, b)
+    Gemm g;
+    g.role = hatt::kRoleMethod;
+    g.M = r0; g.N = c; g.K = r1;
+    g.batch = nk * s0; g.bdiv = s0;
+    g.A = a.Y ? a.Y[k] : nullptr; g.sA1 = r1; g.sA2 = 0; g.sAm = (ll)nk * r1; g.sAk = 1;
+    g.B = b.P2; g.sB1 = (ll)r1 * s0 * c; g.sB2 = c; g.sBk = (ll)s0 * c; g.sBn = 1;
+    g.C = b.P3; g.sC1 = 1; g.sC2 = (ll)c * nk; g.sCm = (ll)s0 * c * nk; g.sCn = nk;
+    g.dyn_dev = Rdev; g.dyn_n = 1;
+    g.prec = a.prec;
+    run.gemm(g);
+  }
+  {   // W^{(k)} = W_L W_R^T over the n_k R live terms
+    Gemm g;
+    g.role = hatt::kRoleMethod;
+    g.M = r0 * s0; g.N = l0; g.K = nk * c;
+    g.A = b.P3; g.sAm = (ll)c * nk; g.sAk = 1;
+    g.B = b.Rv; g.sBk = 1; g.sBn = (ll)c * nk;
+    g.C = Wout; g.sCm = l0; g.sCn = 1;
+    g.dyn_dev = Rdev; g.dyn_k = nk;
+    g.prec = a.prec;
+    run.gemm(g);
+  }
 }
 
 void run_hatt(Runner &run, const HattArgs &a, const HattBufs &b) {
@@ -1418,11 +1412,6 @@ int tt_hadamard_recompress(const tt_t *Y, const tt_t *Z, const tt_opts *opts, tt
   a.Z = Z->cores;
   a.Xout = X->cores;
   cudaStream_t strm = (cudaStream_t)stream;
-  if (a.variant == 2) {   // the kept ranks are read on the host: no stream capture
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(strm, &cs) != cudaSuccess) return from_cuda(cudaGetLastError());
-    if (cs != cudaStreamCaptureStatusNone) return TT_ERR_ARG;
-  }
   Fp64TcScope tc(opts->precision == TT_FP64_TC);
   HattBufs bufs_for_ranks;
   st = execute(workspace, workspace_bytes, strm,
@@ -1484,7 +1473,6 @@ int batch_layout(int count, const tt_t *Y, const tt_t *Z, const tt_opts *opts, i
   if (count > 0 && (!Y || !Z || !opts)) return TT_ERR_ARG;
   lane_bytes.assign(lanes, 0);
   for (int j = 0; j < count; ++j) {
-    if (opts[j].variant == 2) return TT_ERR_ARG;   // reads ranks on the host: one pair per call
     std::vector<int64_t> bound((size_t)std::max(Y[j].d, 0) + 1);
     size_t b = 0;
     const int st = tt_hadamard_recompress_plan(&Y[j], &Z[j], &opts[j], bound.data(), &b);

@@ -117,6 +117,13 @@ struct Gemm {
   double alpha = 1.0, beta = 0.0;
   const double *alpha_dev = nullptr;
   const int *skip_dev = nullptr;   // if set and *skip_dev != 0 the launch does nothing
+  // Live extents from device memory (a rank the device chose): with dyn_dev
+  // set and R = max(*dyn_dev, 0), the product runs over min(N, dyn_n R)
+  // columns if dyn_n > 0 and min(K, dyn_k R) terms if dyn_k > 0; outputs in
+  // the columns beyond are not written. Plans and scratch are sized for
+  // (M, N, K); such products run on the FP64 / emulated-format SIMT kernels.
+  const int *dyn_dev = nullptr;
+  int dyn_n = 0, dyn_k = 0;
   int prec = 0;                    // kPrecFP64, or the operand type of a low-precision product
   int role = kRoleAux;             // kernel-timer tag: kRoleMethod for the HaTT contractions
 };

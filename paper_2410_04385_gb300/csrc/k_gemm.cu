@@ -91,6 +91,17 @@ __device__ __forceinline__ void mac_slots(int nqw, int kdepth, const T (*As)[kMa
   if constexpr (NQ < OUT) mac_slots<NQ + 1, OUT, T>(nqw, kdepth, As, Bs, om, on, acc);
 }
 
+// Live column count and depth of a product whose extents depend on a rank in
+// device memory (Gemm::dyn_dev); the planned (g.N, g.K) otherwise.
+__device__ __forceinline__ void live_extents(const Gemm &g, int &N, int &K) {
+  N = g.N;
+  K = g.K;
+  if (g.dyn_dev == nullptr) return;
+  const long long R = max(*g.dyn_dev, 0);
+  if (g.dyn_n > 0) N = (int)min((long long)N, g.dyn_n * R);
+  if (g.dyn_k > 0) K = (int)min((long long)K, g.dyn_k * R);
+}
+
 // LOWP = false: FP64 operands and accumulators. LOWP = true: operands rounded
 // to g.prec as they are staged (above) and FP32 accumulators; the result is
 // written in FP64 (scaled by alpha in FP64).
@@ -116,8 +127,11 @@ gemm_f64_kernel(Gemm g, int bm, int bn, int tiles_n, int tiles_m, int ksplit, in
   const double *A = g.A + b1 * g.sA1 + b2 * g.sA2;
   const double *B = g.B + b1 * g.sB1 + b2 * g.sB2;
   const int m0 = tm_i * bm, n0 = tn_i * bn;
+  int N, K;
+  live_extents(g, N, K);
+  if (n0 >= N) return;   // a tile past the live columns: every K split of it leaves here
   const int kbeg = ks * kchunk;
-  const int kend = min(g.K, kbeg + kchunk);
+  const int kend = min(K, kbeg + kchunk);
   const int outs = bm * bn;
 
   int om[OUT], on[OUT];
@@ -147,7 +161,7 @@ gemm_f64_kernel(Gemm g, int bm, int bn, int tiles_n, int tiles_m, int ksplit, in
       int nn, kk;
       if (b_nfast) { kk = e / bn; nn = e % bn; } else { nn = e / kBK; kk = e % kBK; }
       const int gn = n0 + nn, gk = kt + kk;
-      const double v = (gn < g.N && gk < kend) ? B[gk * g.sBk + gn * g.sBn] : 0.0;
+      const double v = (gn < N && gk < kend) ? B[gk * g.sBk + gn * g.sBn] : 0.0;
       if (LOWP) Bs[kk][nn] = round_operand(v, prec); else Bs[kk][nn] = v;
     }
     __syncthreads();
@@ -166,7 +180,7 @@ gemm_f64_kernel(Gemm g, int bm, int bn, int tiles_n, int tiles_m, int ksplit, in
     for (int q = 0; q < OUT; ++q) {
       if (q >= nq) break;
       const int gm = m0 + om[q], gn = n0 + on[q];
-      if (gm < g.M && gn < g.N) P[(long long)gm * g.N + gn] = (double)acc[q];
+      if (gm < g.M && gn < N) P[(long long)gm * g.N + gn] = (double)acc[q];
     }
     // publish this partial, then let the last of the tile's ksplit blocks sum
     __threadfence();
@@ -184,7 +198,7 @@ gemm_f64_kernel(Gemm g, int bm, int bn, int tiles_n, int tiles_m, int ksplit, in
     for (int q = 0; q < OUT; ++q) {
       if (q >= nq) break;
       const int gm = m0 + om[q], gn = n0 + on[q];
-      if (gm >= g.M || gn >= g.N) continue;
+      if (gm >= g.M || gn >= N) continue;
       const long long e = (long long)gm * g.N + gn;
       double sum = 0.0;
       for (int k = 0; k < ksplit; ++k) sum += (k == ks) ? (double)acc[q] : __ldcg(P0 + k * mn + e);
@@ -198,7 +212,7 @@ gemm_f64_kernel(Gemm g, int bm, int bn, int tiles_n, int tiles_m, int ksplit, in
   for (int q = 0; q < OUT; ++q) {
     if (q >= nq) break;
     const int gm = m0 + om[q], gn = n0 + on[q];
-    if (gm >= g.M || gn >= g.N) continue;
+    if (gm >= g.M || gn >= N) continue;
     double *c = C + gm * g.sCm + gn * g.sCn;
     const double v = alpha * (double)acc[q];
     *c = (g.beta != 0.0) ? fma(g.beta, *c, v) : v;
@@ -274,8 +288,11 @@ gemm_pair_kernel(Gemm g, int bm, int bn, int tiles_n, int tiles_m, int ksplit, i
   const double *A = g.A + b1 * g.sA1 + b2 * g.sA2;
   const double *B = g.B + b1 * g.sB1 + b2 * g.sB2;
   const int m0 = tm_i * bm, n0 = tn_i * bn;
+  int N, K;
+  live_extents(g, N, K);
+  if (n0 >= N) return;   // a tile past the live columns: every K split of it leaves here
   const int kbeg = ks * kchunk;
-  const int kend = min(g.K, kbeg + kchunk);
+  const int kend = min(K, kbeg + kchunk);
   const int bn2 = (bn + 1) / 2, bnp = 2 * bn2;   // column pairs; an odd tail column pairs with zero
   const int slots = bm * bn2;
 
@@ -305,7 +322,7 @@ gemm_pair_kernel(Gemm g, int bm, int bn, int tiles_n, int tiles_m, int ksplit, i
       int nn, kk;
       if (b_nfast) { kk = e / bnp; nn = e % bnp; } else { nn = e / kBK; kk = e % kBK; }
       const int gn = n0 + nn, gk = kt + kk;
-      Bs[kk][nn] = (nn < bn && gn < g.N && gk < kend) ? B[gk * g.sBk + gn * g.sBn] : 0.0;
+      Bs[kk][nn] = (nn < bn && gn < N && gk < kend) ? B[gk * g.sBk + gn * g.sBn] : 0.0;
     }
     __syncthreads();
     mac_pair_slots<1, OUT>(nqw, min(kBK, kend - kt), As, Bs, om, on, a0, a1);
@@ -323,8 +340,8 @@ gemm_pair_kernel(Gemm g, int bm, int bn, int tiles_n, int tiles_m, int ksplit, i
       if (q >= nq) break;
       const int gm = m0 + om[q], gn = n0 + on[q];
       if (gm >= g.M) continue;
-      if (on[q] < bn && gn < g.N) P[(long long)gm * g.N + gn] = a0[q];
-      if (on[q] + 1 < bn && gn + 1 < g.N) P[(long long)gm * g.N + gn + 1] = a1[q];
+      if (on[q] < bn && gn < N) P[(long long)gm * g.N + gn] = a0[q];
+      if (on[q] + 1 < bn && gn + 1 < N) P[(long long)gm * g.N + gn + 1] = a1[q];
     }
     __threadfence();
     __syncthreads();
@@ -343,7 +360,7 @@ gemm_pair_kernel(Gemm g, int bm, int bn, int tiles_n, int tiles_m, int ksplit, i
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int gm = m0 + om[q], gn = n0 + on[q] + h;
-        if (gm >= g.M || on[q] + h >= bn || gn >= g.N) continue;
+        if (gm >= g.M || on[q] + h >= bn || gn >= N) continue;
         const long long e = (long long)gm * g.N + gn;
         const double own = h ? a1[q] : a0[q];
         double sum = 0.0;
@@ -361,7 +378,7 @@ gemm_pair_kernel(Gemm g, int bm, int bn, int tiles_n, int tiles_m, int ksplit, i
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int gm = m0 + om[q], gn = n0 + on[q] + h;
-      if (gm >= g.M || on[q] + h >= bn || gn >= g.N) continue;
+      if (gm >= g.M || on[q] + h >= bn || gn >= N) continue;
       double *c = C + gm * g.sCm + gn * g.sCn;
       const double v = alpha * (h ? a1[q] : a0[q]);
       *c = (g.beta != 0.0) ? fma(g.beta, *c, v) : v;
@@ -586,9 +603,9 @@ size_t split_doubles(const Gemm &g, const Launch &L) {
 // scratch than the model's plan, the size callers allocated; nothing is
 // allocated; the stream is synchronized once per tuned shape. A shape first
 // met inside a capture keeps the model's plan, and so do products under 1e7
-// flops, products that accumulate into C or carry a skip flag or whose C
-// overlaps an operand, and every shape after the first 256 tuned in the
-// process. Off by tt_gemm_autotune(0).
+// flops, products that accumulate into C, carry a skip flag, have
+// device-side extents or whose C overlaps an operand, and every shape after
+// the first 256 tuned in the process. Off by tt_gemm_autotune(0).
 std::atomic<bool> g_autotune{true};
 constexpr double kTuneMinFlops = 1e7;    // smaller products keep the model's plan
 constexpr int kTuneMaxShapes = 256;      // per process: bounds the tuning time
@@ -603,7 +620,7 @@ long long span(const Gemm &g, long long s1, long long s2, long long sr, long lon
 
 // Products the tuner may run repeatedly with C as their output.
 bool tunable(const Gemm &g) {
-  if (g.beta != 0.0 || g.skip_dev != nullptr || g.C == nullptr) return false;
+  if (g.beta != 0.0 || g.skip_dev != nullptr || g.dyn_dev != nullptr || g.C == nullptr) return false;
   if (g.sA1 < 0 || g.sA2 < 0 || g.sAm < 0 || g.sAk < 0 || g.sB1 < 0 || g.sB2 < 0 || g.sBk < 0 ||
       g.sBn < 0 || g.sC1 < 0 || g.sC2 < 0 || g.sCm < 0 || g.sCn < 0)
     return false;
@@ -752,6 +769,9 @@ cudaError_t gemm_f64(const Gemm &g, double *scratch, cudaStream_t st) {
     return e;
   }
   int *counters = tile_counters();
+  // a product with device-side extents is credited no flops: the host does
+  // not know how many it does
+  const double flops = g.dyn_dev ? 0.0 : 2.0 * g.M * g.N * (double)g.K * g.batch;
   const Launch Lm = plan(g);
   if (Lm.ksplit > 1 && (scratch == nullptr || counters == nullptr)) return cudaErrorInvalidValue;
   const Launch L = exec_plan(g, scratch, counters, st);
@@ -760,7 +780,7 @@ cudaError_t gemm_f64(const Gemm &g, double *scratch, cudaStream_t st) {
     return cudaErrorInvalidConfiguration;
   const int slot = timer_begin(st);
   launch_plan(g, L, scratch, counters, st);
-  timer_end(slot, st, 2.0 * g.M * g.N * (double)g.K * g.batch, g.role);
+  timer_end(slot, st, flops, g.role);
   return cudaGetLastError();
 }
 

@@ -294,7 +294,7 @@ thread_local bool t_fp64_tc = false;
 void set_fp64_tensor_cores(bool on) { t_fp64_tc = on; }
 
 bool gemm_oz_applicable(const Gemm &g) {
-  if (!t_fp64_tc || g.prec != kPrecFP64) return false;
+  if (!t_fp64_tc || g.prec != kPrecFP64 || g.dyn_dev != nullptr) return false;
   const double flops = 2.0 * g.M * g.N * (double)g.K * g.batch;
   return std::max(g.M, g.N) >= 128 && g.K >= 128 && flops >= 2e7;
 }

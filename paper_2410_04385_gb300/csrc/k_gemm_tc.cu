@@ -296,7 +296,8 @@ cudaError_t clear_device_error() {
 }
 
 bool gemm_tc_supported(const Gemm &g) {
-  return g.prec == kPrecTF32 || g.prec == kPrecBF16;
+  // device-side extents (Gemm::dyn_dev) run on the emulated-format SIMT kernel
+  return (g.prec == kPrecTF32 || g.prec == kPrecBF16) && g.dyn_dev == nullptr;
 }
 
 size_t gemm_tc_scratch_doubles(const Gemm &g) {

@@ -72,8 +72,11 @@ __global__ void put_block_kernel(const double *src, int a, int n, int b, double 
 // HPCRL-2 selection. Uf = W V (x rows, c columns) holds W's right singular
 // directions scaled by their singular values: column j has squared norm
 // e_j = sigma_j^2. Keeps the columns with sigma_j > ep * sigma_max (at least
-// one), in descending order of e_j (ties by index), and writes them packed
-// with leading dimension R: UR (x x R) = U_R S_R and VR (c x R) = V_R.
+// one), in descending order of e_j (ties by index), and writes them into the
+// first R columns of UR (x x c) = U_R S_R and VR (c x c) = V_R, leading
+// dimension c; R goes to device memory, where the contractions that follow
+// read it (their extents in R are device-side), so nothing waits on the host.
+// Columns R .. c - 1 are left as they are: nothing reads them.
 // One block: warp w sums the columns w, w + 32, ... in a fixed order, so the
 // decision is the same on every run.
 constexpr int kSelThreads = 1024;
@@ -84,7 +87,6 @@ select_directions_kernel(const double *Uf, const double *V, long long x, int c, 
   pdl_enter();
   __shared__ double e[kMaxSmall];
   __shared__ int pos[kMaxSmall];
-  __shared__ int s_R;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int j = warp; j < c; j += kSelThreads / 32) {
     double acc = 0.0;
@@ -118,18 +120,15 @@ select_directions_kernel(const double *Uf, const double *V, long long x, int c, 
   if (tid == 0) {
     int R = 0;
     for (int j = 0; j < c; ++j) R += pos[j] >= 0;
-    s_R = R;
     *Rout = R;
   }
-  __syncthreads();
-  const int R = s_R;
   for (long long t = tid; t < x * c; t += kSelThreads) {
     const int j = (int)(t % c);
-    if (pos[j] >= 0) UR[(t / c) * R + pos[j]] = Uf[t];
+    if (pos[j] >= 0) UR[(t / c) * c + pos[j]] = Uf[t];
   }
   for (int t = tid; t < c * c; t += kSelThreads) {
     const int j = t % c;
-    if (pos[j] >= 0) VR[(t / c) * R + pos[j]] = V[t];
+    if (pos[j] >= 0) VR[(t / c) * c + pos[j]] = V[t];
   }
 }
 

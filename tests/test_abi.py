@@ -253,10 +253,10 @@ def test_precision_range_is_checked_on_the_host(lib):
         assert lib.tt_hadamard_recompress_plan(Y.ref(), Z.ref(), ctypes.byref(o), bound, ctypes.byref(ws)) == expect
 
 
-def test_hatt2_plan_and_batch_rejection(lib):
+def test_hatt2_plan_and_batch_plan(lib):
     """HaTT-2 plans the same output bound as HaTT-1 and a workspace that also
-    holds its own buffers; the batched entry point rejects it (it reads the
-    kept ranks on the host)."""
+    holds its own buffers; the batched entry point takes it (the kept ranks
+    stay on the device), with a lane at least as large as the single plan."""
     n = [6] * 5
     Yr, Zr = [1, 4, 5, 5, 3, 1], [1, 3, 4, 2, 3, 1]
     st1, b1, w1 = _plan(Yr, Zr, n, sketch_rank=9)
@@ -267,7 +267,8 @@ def test_hatt2_plan_and_batch_rejection(lib):
     Zs = (B.TTStruct * 1)(Zd.s)
     o = (B.OptsStruct * 1)(B.make_opts(sketch_rank=9, variant=2, ep=1e-3))
     bound = ctypes.c_size_t()
-    assert B.load().tt_hadamard_recompress_batch_plan(1, Ys, Zs, o, 1, ctypes.byref(bound)) == 3
+    assert B.load().tt_hadamard_recompress_batch_plan(1, Ys, Zs, o, 1, ctypes.byref(bound)) == 0
+    assert bound.value >= w2
 
 
 def test_fixed_ranks_plan_bounds(lib):

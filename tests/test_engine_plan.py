@@ -79,7 +79,7 @@ def test_workspace_grows_linearly_with_the_batch(lib):
     (dict(sketch_rank=8, max_rank=4), 3),          # needs the truncation sweep
     (dict(sketch_rank=8, tol=1e-10), 3),           # tolerance: truncation sweep
     (dict(sketch_rank=8, precision=2), 3),         # TF32 tensor-core products
-    (dict(sketch_rank=8, variant=2, ep=0.1), 3),   # HaTT-2 reads ranks on the host
+    (dict(sketch_rank=8, variant=2, ep=0.1), 3),   # HaTT-2: device-side ranks, not in the engine
     (dict(sketch_rank=8, precision=1), 0),         # FP32 sketch products
 ])
 def test_plan_refusals(lib, opts, expect):

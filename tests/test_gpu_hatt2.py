@@ -137,20 +137,51 @@ def test_hatt2_several_tiles_with_truncation(B):
     assert rel_diff(X, A) <= REL_TOL
 
 
-def test_hatt2_refuses_stream_capture(B):
-    """The kept ranks are read on the host, so a capturing stream is refused
-    before anything is enqueued (status TT_ERR_ARG)."""
+def test_hatt2_captured_replays_equal_eager(B):
+    """The kept ranks R_k stay in device memory (the contractions read them
+    there), so a call can be captured in a CUDA graph: replays give the eager
+    result, which matches the oracle. The workspace is filled with NaN before
+    each run, so a contraction that read a column past R_k (the buffers are
+    laid out for R_k = l_{k+1}) would show."""
     Y, Z = small_random()
-    h = B.HadamardRecompressor(to_gpu(Y), to_gpu(Z), sketch_rank=12, variant=2, ep=0.3)
+    ep = 0.3
+    margin, kept, cond = cut_margin(Y, Z, 12, 0, ep)
+    assert margin > 1e-3 and cond < 1e6 and min(kept[2:-1]) < 12
+    h = B.HadamardRecompressor(to_gpu(Y), to_gpu(Z), sketch_rank=12, seed=0, variant=2, ep=ep)
+    h.workspace.fill_(255)
     h.run()
     torch.cuda.synchronize()
-    g = torch.cuda.CUDAGraph()
-    status = None
-    with torch.cuda.graph(g):
-        try:
-            h.run()
-        except B.HattError as e:
-            status = e.status
-    assert status == 3
-    h.run()          # still usable afterwards
+    X_eager = [c.cpu().numpy().copy() for c in h.result()]
+    A = ohatt.hadamard_recompress(Y, Z, sketch_rank=12, seed=0, variant=2, ep=ep)
+    assert rel_diff(X_eager, A) <= REL_TOL
+    h.capture()
+    for _ in range(2):
+        h.workspace.fill_(255)
+        for t in h.out_bufs:
+            t.fill_(float("nan"))
+        h.replay()
+        torch.cuda.synchronize()
+        X = [c.cpu().numpy() for c in h.result()]
+        assert rel_diff(X, X_eager) <= 1e-13
+
+
+def test_hatt2_in_the_stream_lane_batch(B):
+    """Variant 2 pairs (and a HaTT-1 pair) in one batched call over library
+    streams: each equals its oracle result."""
+    Y1, Z1 = small_random()
+    Y2, Z2, _ = wl.workload_small_sin_times_random()
+    cases = [(Y1, Z1, dict(sketch_rank=12, seed=0, variant=2, ep=0.3)),
+             (Y2, Z2, dict(sketch_rank=12, seed=1, variant=2, ep=3e-2)),
+             (Y1, Z1, dict(sketch_rank=12, seed=1)),
+             (Y2, Z2, dict(sketch_rank=6, seed=0, variant=2, ep=0.3))]
+    for Y, Z, o in cases:
+        if o.get("variant") == 2:
+            margin, _, cond = cut_margin(Y, Z, o["sketch_rank"], o["seed"], o["ep"])
+            assert margin > 1e-3 and cond < 1e6
+    h = B.BatchRecompressor([(to_gpu(Y), to_gpu(Z), o) for Y, Z, o in cases], lanes=3)
+    h.run()
     torch.cuda.synchronize()
+    for j, (Y, Z, o) in enumerate(cases):
+        X = [c.cpu().numpy() for c in h.result(j)]
+        A = ohatt.hadamard_recompress(Y, Z, **o)
+        assert rel_diff(X, A) <= REL_TOL
