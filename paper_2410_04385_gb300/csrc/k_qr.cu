@@ -24,10 +24,23 @@
 // leaves Q far from orthonormal, and the projection Q Q^T C of the callers
 // then loses about 1e-9 of C.
 //
-// All passes are launched unconditionally (fixed launch sequence, capturable
-// in a CUDA graph); a device flag set by the convergence test turns the
-// remaining launches into no-ops.
+// Two launch forms, the same passes:
+//  * fused (qr_fused_kernel): all passes in one cooperative launch, one block
+//    per SM, each block owning a contiguous slice of the rows of S. Grid
+//    barriers separate the Gram partial sums, their reduction, the
+//    factorization (block 0) and the apply; a converged QR stops at once, so
+//    no launch and no no-op pass follows the convergence test. Used on
+//    calls whose stream runs alone (single recompressions, rounding);
+//  * launch per step: per pass the Gram shares, their sum, the
+//    factorization and the apply, all passes launched unconditionally (fixed
+//    launch sequence); a device flag set by the convergence test turns the
+//    remaining launches into no-ops. Used by the batched entry point, whose
+//    many streams would serialize on whole-GPU cooperative grids.
+// Both run the same device code on the same row partition, so they give
+// bitwise the same Q; both are capturable in a CUDA graph.
 #include <algorithm>
+#include <cstdlib>
+#include <cstring>
 #include "hatt_internal.cuh"
 
 namespace hatt {
@@ -108,8 +121,9 @@ __device__ __forceinline__ void chol_pivot(double *G, int ld, int j, const unsig
 // Flag words (reset at the start of every QR):
 //   flags[0] done:      no further pass is needed (read by the Gram GEMM and
 //                       this kernel at the start of every later pass)
-//   flags[1] skip_apply: the S <- S R^{-1} launch of this pass is a no-op
+//   flags[1] skip_apply: the S <- S R^{-1} step of this pass is a no-op
 //   flags[2] passes applied, flags[3] shifted passes (diagnostics)
+//   flags[4] grid-barrier arrivals, flags[5] abort (fused form only)
 //
 // One block: convergence test of G = S^T S, then the Cholesky factor R of G
 // (shifted if the plain factorization breaks down), published as the unit
@@ -121,15 +135,10 @@ __device__ __forceinline__ void chol_pivot(double *G, int ld, int j, const unsig
 // while the other warps update the rest, so each column costs one barrier and
 // the pivot's dependent FP64 chain overlaps the bulk of the update. Rows of R
 // are not scaled in place: the update subtracts (G_ji y_j^2) G_jl, and the
-// publication scales row j by y_j^2.
-__global__ void __launch_bounds__(kCholThreads)
-chol_inv_kernel(const double *Gg, double *Ut_g, double *y_g, int c, int m, int *flags) {
-  pdl_enter();
-  if (flags[0]) {
-    if (threadIdx.x == 0) flags[1] = 1;
-    return;
-  }
-  extern __shared__ double sm[];
+// publication scales row j by y_j^2. G is read through L2 (__ldcg): in the
+// fused form other blocks of the same launch wrote it.
+__device__ __forceinline__ void chol_factor(const double *Gg, double *Ut_g, double *y_g, int c,
+                                            int m, int *flags, double *sm) {
   const int ld = c + 1;
   double *G = sm;                                   // c x ld, upper triangle is updated
   __shared__ double s_red[3][kCholThreads / 32];
@@ -158,7 +167,7 @@ chol_inv_kernel(const double *Gg, double *Ut_g, double *y_g, int c, int m, int *
 #pragma unroll
     for (int q = 0; q < 4; ++q) {         // four loads in flight per thread
       const int e = e0 + q * kCholThreads;
-      v[q] = e < n ? Gg[e] : 0.0;
+      v[q] = e < n ? __ldcg(Gg + e) : 0.0;
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -243,7 +252,7 @@ chol_inv_kernel(const double *Gg, double *Ut_g, double *y_g, int c, int m, int *
       if (!(shift > 0.0)) shift = 1e-300;
       for (int e = tid; e < c * c; e += kCholThreads) {
         const int i = e / c, j = e % c;
-        G[i * ld + j] = Gg[e] + (i == j ? shift : 0.0);
+        G[i * ld + j] = __ldcg(Gg + e) + (i == j ? shift : 0.0);
       }
       if (tid == 0) flags[3] += 1;
     }
@@ -304,24 +313,26 @@ chol_inv_kernel(const double *Gg, double *Ut_g, double *y_g, int c, int m, int *
   }
 }
 
+__global__ void __launch_bounds__(kCholThreads)
+chol_inv_kernel(const double *Gg, double *Ut_g, double *y_g, int c, int m, int *flags) {
+  pdl_enter();
+  if (flags[0]) {
+    if (threadIdx.x == 0) flags[1] = 1;
+    return;
+  }
+  extern __shared__ double sm[];
+  chol_factor(Gg, Ut_g, y_g, c, m, flags, sm);
+}
+
 // Q = S R^{-1} = (S U~^{-1}) D^{-1}, one warp per row, in place. The unit
 // diagonal keeps divisions out of the chain; the final scaling by y = D^{-1}
-// is one multiply per entry.
-__global__ void __launch_bounds__(kTrsmThreads)
-trsm_rows_kernel(double *S, int m, int c, long long ldS, const double *Ut, const double *y,
-                 const int *flags) {
-  pdl_enter();
-  if (flags[1]) return;
-  extern __shared__ double sm[];
-  double *Us = sm;                       // c x c
-  double *ys = sm + c * c;               // c
-  for (int e = threadIdx.x; e < c * c; e += kTrsmThreads) Us[e] = Ut[e];
-  for (int e = threadIdx.x; e < c; e += kTrsmThreads) ys[e] = y[e];
-  __syncthreads();
+// is one multiply per entry. Rows r_first, r_first + r_step, ... < r_end of
+// this warp; U~ (Us) and y (ys) in shared memory.
+__device__ __forceinline__ void apply_rows(double *S, long long ldS, int c, const double *Us,
+                                           const double *ys, int r_first, int r_end, int r_step) {
   const int lane = threadIdx.x & 31;
-  const int warps = kTrsmThreads / 32;
   const int ns = (c + 31) / 32;          // column slots in use (c <= 128)
-  for (int r = blockIdx.x * warps + (threadIdx.x >> 5); r < m; r += gridDim.x * warps) {
+  for (int r = r_first; r < r_end; r += r_step) {
     double *row = S + (long long)r * ldS;
     double x[4];
 #pragma unroll
@@ -340,18 +351,272 @@ trsm_rows_kernel(double *S, int m, int c, long long ldS, const double *Ut, const
   }
 }
 
+__global__ void __launch_bounds__(kTrsmThreads)
+trsm_rows_kernel(double *S, int m, int c, long long ldS, const double *Ut, const double *y,
+                 const int *flags) {
+  pdl_enter();
+  if (flags[1]) return;
+  extern __shared__ double sm[];
+  double *Us = sm;                       // c x c
+  double *ys = sm + c * c;               // c
+  for (int e = threadIdx.x; e < c * c; e += kTrsmThreads) Us[e] = Ut[e];
+  for (int e = threadIdx.x; e < c; e += kTrsmThreads) ys[e] = y[e];
+  __syncthreads();
+  const int warps = kTrsmThreads / 32;
+  apply_rows(S, ldS, c, Us, ys, blockIdx.x * warps + (threadIdx.x >> 5), m, gridDim.x * warps);
+}
+
+// ------------------------------------------------------- the Gram matrix ---
+// G = S^T S from per-block shares: block b of nb sums the rows [b p, b p + p)
+// of S, p = ceil(m / nb), into the upper triangle (i <= j, c (c + 1) / 2
+// entries) of its own share, and a warp then sums each entry over the nb
+// shares. Both forms of the QR run these same device functions with the
+// same nb (qr_blocks), so they compute bitwise the same G, and the same QR.
+constexpr int kQrMaxBlocks = 160;       // >= the SMs of the device (152 on GB300)
+constexpr int kQrRowTile = 16;          // rows of S staged per Gram step
+constexpr int kQrMinRows = 4;           // rows per block at least (small m: fewer blocks)
+constexpr int kQrMaxSlots = (kMaxSmall * (kMaxSmall + 1) / 2 + kCholThreads - 1) / kCholThreads;
+constexpr long long kQrSpinCap = 1LL << 21;   // polls of one barrier wait (seconds)
+
+// Row i and column j >= i of entry o of the upper triangle of a c x c matrix
+// stored by rows (row i starts at i c - i (i - 1) / 2): the root of the
+// quadratic, then exact integer correction.
+__device__ __forceinline__ void upper_index(int o, int c, int &i, int &j) {
+  const float b = 2.0f * c + 1.0f;
+  i = (int)((b - sqrtf(b * b - 8.0f * o)) * 0.5f);
+  i = max(0, min(i, c - 1));
+  while (i + 1 < c && (i + 1) * c - (i + 1) * i / 2 <= o) ++i;
+  while (i > 0 && i * c - i * (i - 1) / 2 > o) --i;
+  j = i + (o - (i * c - i * (i - 1) / 2));
+}
+
+// Entries of a share this thread sums: t, t + 256, ... (nq of them, packed
+// as i << 8 | j); nqw = the most any lane of the warp has (lane 0's). Each
+// warp runs the multiply-adds of nqw slots by warp-uniform branches, as the
+// GEMM does (a predicated-off DFMA costs as much as a full one).
+struct GramSlots {
+  int pk[kQrMaxSlots];
+  int nq, nqw;
+};
+
+__device__ __forceinline__ void gram_slots(int c, GramSlots &g) {
+  const int tid = threadIdx.x;
+  const int T = c * (c + 1) / 2;
+  g.nq = max(0, (T - tid + kCholThreads - 1) / kCholThreads);
+  g.nqw = __shfl_sync(0xffffffffu, g.nq, 0);
+#pragma unroll
+  for (int q = 0; q < kQrMaxSlots; ++q) {
+    int i = 0, j = 0;
+    if (q < g.nq) upper_index(tid + kCholThreads * q, c, i, j);
+    g.pk[q] = (i << 8) | j;
+  }
+}
+
+// This block's share of the rows [r0, r1) of S, into mine (T entries); sm
+// holds kQrRowTile rows of S. S is read through L2 (another block of the
+// fused launch may have written it).
+__device__ __forceinline__ void gram_share(const double *S, long long ldS, int c, int r0, int r1,
+                                           const GramSlots &g, double *mine, double *sm) {
+  const int tid = threadIdx.x;
+  double acc[kQrMaxSlots];
+#pragma unroll
+  for (int q = 0; q < kQrMaxSlots; ++q) acc[q] = 0.0;
+  for (int rt = r0; rt < r1; rt += kQrRowTile) {
+    const int rows = min(kQrRowTile, r1 - rt);
+    for (int e = tid; e < rows * c; e += kCholThreads) {
+      const int rr = e / c;
+      sm[e] = __ldcg(S + (long long)(rt + rr) * ldS + (e - rr * c));
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kQrMaxSlots; ++q) {
+      if (q < g.nqw) {
+        const double *a = sm + (g.pk[q] >> 8), *b = sm + (g.pk[q] & 255);
+        double v = acc[q];
+        for (int r = 0; r < rows; ++r) v = fma(a[r * c], b[r * c], v);
+        acc[q] = v;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < kQrMaxSlots; ++q)
+    if (q < g.nq) mine[tid + kCholThreads * q] = acc[q];
+}
+
+// Entry t of G summed over the nb shares by one warp: lanes over shares in
+// order, then a fixed shuffle tree; lane 0 writes G(i, j) and G(j, i).
+__device__ __forceinline__ void gram_entry(const double *part, int nb, int c, int t, double *G) {
+  const int lane = threadIdx.x & 31;
+  const int T = c * (c + 1) / 2;
+  double v = 0.0;
+  for (int p = lane; p < nb; p += 32) v += __ldcg(part + (long long)p * T + t);
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) {
+    int i, j;
+    upper_index(t, c, i, j);
+    G[i * c + j] = v;
+    G[j * c + i] = v;
+  }
+}
+
+// Launch per step: the shares (nb blocks), then their sum. Both do nothing
+// once the QR has converged.
+__global__ void __launch_bounds__(kCholThreads)
+gram_share_kernel(const double *S, long long ldS, int m, int c, double *part, const int *flags) {
+  pdl_enter();
+  if (flags[0]) return;
+  extern __shared__ double sm[];
+  GramSlots g;
+  gram_slots(c, g);
+  const int per = (m + gridDim.x - 1) / gridDim.x;
+  const int r0 = min(m, (int)blockIdx.x * per), r1 = min(m, r0 + per);
+  gram_share(S, ldS, c, r0, r1, g, part + (long long)blockIdx.x * (c * (c + 1) / 2), sm);
+}
+
+__global__ void __launch_bounds__(kCholThreads)
+gram_sum_kernel(const double *part, int nb, int c, double *G, const int *flags) {
+  pdl_enter();
+  if (flags[0]) return;
+  const int T = c * (c + 1) / 2;
+  const int warps = gridDim.x * (kCholThreads / 32);
+  for (int t = blockIdx.x * (kCholThreads / 32) + (threadIdx.x >> 5); t < T; t += warps)
+    gram_entry(part, nb, c, t, G);
+}
+
+// ------------------------------------------------------------ fused form ---
+// Grid barrier of the fused QR (cooperative launch: every block is resident).
+// Arrivals count up in bar[0] (zero at the start of the QR); the e-th barrier
+// waits for e * gridDim.x of them. A wait gives up after spin_cap polls,
+// sets the timeout health bit and bar[1] (abort), and every block that sees
+// bar[1] gives up too: the QR then stops with S partly processed, and the
+// device status reports the timeout. Returns false in that case.
+__device__ __forceinline__ bool grid_barrier(int *bar, int &epoch, long long spin_cap) {
+  ++epoch;
+  __syncthreads();
+  int ok = 1;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(&bar[0], 1);
+    const int target = epoch * (int)gridDim.x;
+    volatile int *vb = bar;
+    long long polls = 0;
+    while (vb[0] < target) {
+      if (vb[1] != 0) { ok = 0; break; }
+      if (++polls > spin_cap) {
+        atomicOr(&g_qr_health, kHealthTimeout);
+        atomicExch(&bar[1], 1);
+        ok = 0;
+        break;
+      }
+      __nanosleep(32);
+    }
+    __threadfence();
+  }
+  return __syncthreads_and(ok) != 0;
+}
+
+// All passes of one Cholesky QR of S (m x c, leading dimension ldS) in one
+// launch of nb blocks, block b owning the rows [b p, b p + p) of S. A pass:
+//   1. the block's Gram share -> part[b];
+//   2. barrier; each warp sums entries of G over the shares (gram_entry);
+//   3. barrier; block 0: convergence test and factorization (chol_factor);
+//   4. barrier; unless the pass found S orthonormal (or G non-finite),
+//      R^{-1} applied to the block's own rows; if the factorization marked
+//      the pass as the last, the QR ends here, else a barrier and the next
+//      pass.
+// The passes, G, tests and factorization are those of the launch-per-step
+// form, bit for bit.
+__global__ void __launch_bounds__(kCholThreads, 1)
+qr_fused_kernel(double *S, int m, int c, long long ldS, double *G, double *Ut, double *y,
+                double *part, int *flags, long long spin_cap) {
+  pdl_enter();
+  extern __shared__ double sm[];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  constexpr int kWarps = kCholThreads / 32;
+  const int nb = gridDim.x, bid = blockIdx.x;
+  const int per = (m + nb - 1) / nb;
+  const int r0 = min(m, bid * per), r1 = min(m, r0 + per);
+  const int T = c * (c + 1) / 2;
+  GramSlots g;
+  gram_slots(c, g);
+  int *bar = flags + 4;
+  int epoch = 0;
+  for (int pass = 0; pass < kPasses; ++pass) {
+    gram_share(S, ldS, c, r0, r1, g, part + (long long)bid * T, sm);
+    if (!grid_barrier(bar, epoch, spin_cap)) return;
+    for (int t = bid * kWarps + warp; t < T; t += nb * kWarps) gram_entry(part, nb, c, t, G);
+    if (!grid_barrier(bar, epoch, spin_cap)) return;
+    if (bid == 0) chol_factor(G, Ut, y, c, m, flags, sm);
+    if (!grid_barrier(bar, epoch, spin_cap)) return;
+    const int done = __ldcg(flags), skip = __ldcg(flags + 1);
+    if (skip) return;                      // orthonormal already (or a non-finite G)
+    for (int e = tid; e < c * c; e += kCholThreads) sm[e] = __ldcg(Ut + e);
+    for (int e = tid; e < c; e += kCholThreads) sm[c * c + e] = __ldcg(y + e);
+    __syncthreads();
+    apply_rows(S, ldS, c, sm, sm + c * c, r0 + warp, r1, kWarps);
+    if (done) return;                      // this pass was the last one
+    if (!grid_barrier(bar, epoch, spin_cap)) return;
+  }
+}
+
+// SMs and cooperative-launch support of the current device, cached per
+// device (0 SMs: unknown device).
+void device_info(int &sms, bool &coop) {
+  static int s_sms[64] = {};
+  static signed char s_coop[64] = {};
+  sms = 0;
+  coop = false;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return;
+  }
+  if (s_sms[dev] == 0) {
+    int n = 0, co = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&co, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || n <= 0) {
+      cudaGetLastError();
+      return;
+    }
+    s_coop[dev] = co ? 1 : 0;
+    s_sms[dev] = n;
+  }
+  sms = s_sms[dev];
+  coop = s_coop[dev] != 0;
+}
+
+// Blocks (Gram shares) of a QR of m rows: at least kQrMinRows rows each, at
+// most one per SM (the fused form keeps every block resident).
+int qr_blocks(int m, int sms) {
+  const int want = (m + kQrMinRows - 1) / kQrMinRows;
+  return std::max(1, std::min({want, std::max(sms, 1), kQrMaxBlocks}));
+}
+
+// Test hooks, read once: HATT_QR_FORM=steps makes single calls use the
+// launch-per-step form; HATT_QR_SPIN_CAP=<n> bounds each grid-barrier wait of
+// the fused form to n polls (a small n makes the waits run out: the timeout
+// status without a hang).
+bool force_qr_steps() {
+  static const bool v = [] {
+    const char *e = getenv("HATT_QR_FORM");
+    return e != nullptr && strcmp(e, "steps") == 0;
+  }();
+  return v;
+}
+
+long long qr_spin_cap() {
+  static const long long v = [] {
+    const char *e = getenv("HATT_QR_SPIN_CAP");
+    const long long n = e ? atoll(e) : 0;
+    return n > 0 ? n : kQrSpinCap;
+  }();
+  return v;
+}
+
 size_t chol_smem(int c) { return (size_t)c * (c + 1) * sizeof(double); }
 size_t trsm_smem(int c) { return (size_t)(c * c + c) * sizeof(double); }
-
-Gemm gram_desc(double *S, int m, int c, long long ldS, double *G, const int *flags) {
-  Gemm g;
-  g.M = c; g.N = c; g.K = m;
-  g.A = S; g.sAm = 1; g.sAk = ldS;       // A(i, k) = S[k][i]
-  g.B = S; g.sBk = ldS; g.sBn = 1;       // B(k, j) = S[k][j]
-  g.C = G; g.sCm = c; g.sCn = 1;
-  g.skip_dev = flags;
-  return g;
-}
+size_t gram_smem(int c) { return (size_t)kQrRowTile * c * sizeof(double); }
 
 }  // namespace
 
@@ -364,9 +629,10 @@ cudaError_t qr_health_word(int *value, bool clear) {
   return e;
 }
 
+// G, U~, y, then the blocks' Gram shares.
 size_t qr_scratch_doubles(int m, int c) {
-  Gemm g = gram_desc(nullptr, m, c, c, nullptr, nullptr);
-  return (size_t)2 * c * c + c + gemm_scratch_doubles(g);
+  (void)m;
+  return (size_t)2 * c * c + c + (size_t)kQrMaxBlocks * c * (c + 1) / 2;
 }
 
 cudaError_t qr_inplace(double *S, int m, int c, long long ldS, double *scratch, int *flags,
@@ -376,24 +642,50 @@ cudaError_t qr_inplace(double *S, int m, int c, long long ldS, double *scratch, 
   double *G = scratch;
   double *Ut = scratch + (size_t)c * c;
   double *y = scratch + (size_t)2 * c * c;
-  double *gs = scratch + (size_t)2 * c * c + c;
-  cudaError_t e = cudaMemsetAsync(flags, 0, 4 * sizeof(int), st);
+  double *part = scratch + (size_t)2 * c * c + c;
+  int sms = 0;
+  bool coop = false;
+  device_info(sms, coop);
+  if (sms <= 0) return cudaErrorInvalidDevice;
+  const int nb = qr_blocks(m, sms);
+  cudaError_t e = cudaMemsetAsync(flags, 0, 6 * sizeof(int), st);
   if (e != cudaSuccess) return e;
+  if (coop && programmatic_launch() && !force_qr_steps()) {
+    e = cudaFuncSetAttribute(qr_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)chol_smem(kMaxSmall));
+    if (e != cudaSuccess) return e;
+    const size_t smem = std::max({chol_smem(c), trsm_smem(c), gram_smem(c)});
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nb);
+    cfg.blockDim = dim3(kCholThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, qr_fused_kernel, S, m, c, ldS, G, Ut, y, part, flags,
+                           qr_spin_cap());
+    note_launch();
+    return e;
+  }
   e = cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)chol_smem(kMaxSmall));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(trsm_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)trsm_smem(kMaxSmall));
   if (e != cudaSuccess) return e;
-  const Gemm gd = gram_desc(S, m, c, ldS, G, flags);
-  const int blocks = std::max(1, std::min((m + kTrsmThreads / 32 - 1) / (kTrsmThreads / 32), 2 * 152));
+  const int T = c * (c + 1) / 2;
+  const int sum_blocks = std::max(1, std::min((T + 7) / 8, 2 * sms));
+  const int blocks = std::max(1, std::min((m + kTrsmThreads / 32 - 1) / (kTrsmThreads / 32), 2 * sms));
   for (int p = 0; p < kPasses; ++p) {
-    e = gemm_f64(gd, gs, st);
-    if (e != cudaSuccess) return e;
+    launch_k(gram_share_kernel, nb, kCholThreads, gram_smem(c), st, S, ldS, m, c, part, flags);
+    note_launch();
+    launch_k(gram_sum_kernel, sum_blocks, kCholThreads, 0, st, part, nb, c, G, flags);
+    note_launch();
     launch_k(chol_inv_kernel, 1, kCholThreads, chol_smem(c), st, G, Ut, y, c, m, flags);
     note_launch();
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
     launch_k(trsm_rows_kernel, blocks, kTrsmThreads, trsm_smem(c), st, S, m, c, ldS, Ut, y, flags);
     note_launch();
     e = cudaGetLastError();

@@ -1,8 +1,11 @@
-"""Subprocess body of tests/test_gpu_gemm_forms.py: runs HaTT and TT rounding
-through the C ABI with the FP64 GEMM form chosen by the environment
-(HATT_GEMM_FORM=pair: the paired-column kernel on every product) or with the
-first-use tuner switched off (argument "model": the model's plan only), and
-prints one JSON line of relative differences to the FP64 oracle."""
+"""Subprocess body of tests/test_gpu_gemm_forms.py and tests/test_gpu_qr_forms.py:
+runs HaTT and TT rounding through the C ABI with the FP64 GEMM form chosen by
+the environment (HATT_GEMM_FORM=pair: the paired-column kernel on every
+product), or with the first-use tuner switched off (argument "model": the
+model's plan only), and the Cholesky QR form chosen by the environment
+(HATT_QR_FORM=steps: a launch per step), and prints one JSON line of relative
+differences to the FP64 oracle and a SHA-256 of the d = 20 result."""
+import hashlib
 import json
 import os
 import sys
@@ -43,6 +46,7 @@ def main():
     X = host(h.result())
     Xo, info = ohatt.hadamard_recompress(Y, Z, seed=9, return_info=True, **o)
     out["d20_rel"] = rel(X, Xo)
+    out["d20_sha"] = hashlib.sha256(b"".join(np.ascontiguousarray(c).tobytes() for c in X)).hexdigest()
     out["d20_ranks_equal"] = ott.ranks(X) == info["ranks"]
     # truncation by tolerance (Gram, eigen-solve and truncation products)
     n = [6] * 6
