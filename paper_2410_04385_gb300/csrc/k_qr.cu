@@ -328,25 +328,68 @@ chol_inv_kernel(const double *Gg, double *Ut_g, double *y_g, int c, int m, int *
 // diagonal keeps divisions out of the chain; the final scaling by y = D^{-1}
 // is one multiply per entry. Rows r_first, r_first + r_step, ... < r_end of
 // this warp; U~ (Us) and y (ys) in shared memory.
+// Two rows at once, their chains interleaved (the same operations on each
+// row as trsm_row, so a row's result does not depend on its partner).
+template <int NS>
+__device__ __forceinline__ void trsm_row2(double (&x)[4], double (&z)[4], const double *Us, int c,
+                                          int lane) {
+#pragma unroll
+  for (int s0 = 0; s0 < NS; ++s0) {
+    const int lend = min(c, 32 * (s0 + 1));
+    for (int l = 32 * s0; l < lend; ++l) {
+      const double xl = __shfl_sync(0xffffffffu, x[s0], l & 31);
+      const double zl = __shfl_sync(0xffffffffu, z[s0], l & 31);
+      const double *u = Us + l * c;
+#pragma unroll
+      for (int s = s0; s < NS; ++s) {
+        const int col = lane + 32 * s;
+        if (col > l && col < c) {
+          const double uv = u[col];
+          x[s] = fma(-xl, uv, x[s]);
+          z[s] = fma(-zl, uv, z[s]);
+        }
+      }
+    }
+  }
+}
+
 __device__ __forceinline__ void apply_rows(double *S, long long ldS, int c, const double *Us,
                                            const double *ys, int r_first, int r_end, int r_step) {
   const int lane = threadIdx.x & 31;
   const int ns = (c + 31) / 32;          // column slots in use (c <= 128)
-  for (int r = r_first; r < r_end; r += r_step) {
+  for (int r = r_first; r < r_end; r += 2 * r_step) {
     double *row = S + (long long)r * ldS;
-    double x[4];
+    double *row2 = S + (long long)(r + r_step) * ldS;
+    const bool two = r + r_step < r_end;   // the warp's next row: solved alongside
+    double x[4], z[4];
 #pragma unroll
-    for (int s = 0; s < 4; ++s) x[s] = (s < ns && lane + 32 * s < c) ? row[lane + 32 * s] : 0.0;
-    switch (ns) {
-      case 1: trsm_row<1>(x, Us, c, lane); break;
-      case 2: trsm_row<2>(x, Us, c, lane); break;
-      case 3: trsm_row<3>(x, Us, c, lane); break;
-      default: trsm_row<4>(x, Us, c, lane); break;
+    for (int s = 0; s < 4; ++s) {
+      const bool in = s < ns && lane + 32 * s < c;
+      x[s] = in ? row[lane + 32 * s] : 0.0;
+      z[s] = (in && two) ? row2[lane + 32 * s] : 0.0;
+    }
+    if (two) {
+      switch (ns) {
+        case 1: trsm_row2<1>(x, z, Us, c, lane); break;
+        case 2: trsm_row2<2>(x, z, Us, c, lane); break;
+        case 3: trsm_row2<3>(x, z, Us, c, lane); break;
+        default: trsm_row2<4>(x, z, Us, c, lane); break;
+      }
+    } else {
+      switch (ns) {
+        case 1: trsm_row<1>(x, Us, c, lane); break;
+        case 2: trsm_row<2>(x, Us, c, lane); break;
+        case 3: trsm_row<3>(x, Us, c, lane); break;
+        default: trsm_row<4>(x, Us, c, lane); break;
+      }
     }
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
       const int col = lane + 32 * s;
-      if (s < ns && col < c) row[col] = x[s] * ys[col];
+      if (s < ns && col < c) {
+        row[col] = x[s] * ys[col];
+        if (two) row2[col] = z[s] * ys[col];
+      }
     }
   }
 }
@@ -433,6 +476,7 @@ __device__ __forceinline__ void gram_share(const double *S, long long ldS, int c
       if (q < g.nqw) {
         const double *a = sm + (g.pk[q] >> 8), *b = sm + (g.pk[q] & 255);
         double v = acc[q];
+#pragma unroll 4
         for (int r = 0; r < rows; ++r) v = fma(a[r * c], b[r * c], v);
         acc[q] = v;
       }
@@ -449,8 +493,16 @@ __device__ __forceinline__ void gram_share(const double *S, long long ldS, int c
 __device__ __forceinline__ void gram_entry(const double *part, int nb, int c, int t, double *G) {
   const int lane = threadIdx.x & 31;
   const int T = c * (c + 1) / 2;
+  constexpr int kPer = (kQrMaxBlocks + 31) / 32;
+  double sh[kPer];                        // all loads in flight, then summed in share order
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const int p = lane + 32 * k;
+    sh[k] = p < nb ? __ldcg(part + (long long)p * T + t) : 0.0;
+  }
   double v = 0.0;
-  for (int p = lane; p < nb; p += 32) v += __ldcg(part + (long long)p * T + t);
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) v += sh[k];
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   if (lane == 0) {
     int i, j;
