@@ -720,8 +720,9 @@ def main():
     timed_steps_ms = sum(a.elapsed_time(b) for a, b in zip(t_s, t_e))
     gemm_ms = sum(g_ms)
     # the dominant kernel's roofline counts only the launches that compute the
-    # HaTT contractions (always real work); the QR / truncation / refinement
-    # products, which a device flag can turn into no-ops, are reported apart
+    # HaTT contractions (always real work); the truncation products (Gram
+    # matrices, projections; refinement products for c > 96, which a device
+    # flag can turn into no-ops) are reported apart
     m_idx = [i for i, ro in enumerate(g_role) if ro == binding.TT_ROLE_METHOD]
     a_idx = [i for i, ro in enumerate(g_role) if ro != binding.TT_ROLE_METHOD]
     meth_ms = sum(g_ms[i] for i in m_idx)
@@ -768,8 +769,9 @@ def main():
                      "timing": "CUDA events around every launch on its own stream (library kernel "
                                "timer), eager steps queued behind a GPU sleep",
                      "peak_source": FP64_PEAK_NOTE},
-        "gemm_aux": {"kernel": "gemm_f64_kernel, all other launches (QR Gram matrices, truncation, "
-                               "eigen refinement; converged passes run as no-ops)",
+        "gemm_aux": {"kernel": "gemm_f64_kernel, all other launches (truncation Gram matrices and "
+                               "projections; the Cholesky QR computes its Gram matrix in its own "
+                               "kernel)",
                      "launches_per_step": len(a_idx) / GEMM_TIMING_STEPS,
                      "share_of_step": aux_ms / timed_steps_ms,
                      "all_gemm_share_of_step": gemm_ms / timed_steps_ms},
