@@ -336,6 +336,29 @@ int tt_batched_profile(tt_batch_plan *plan, void *stream, int64_t *out);
 int tt_batched_plan_destroy(tt_batch_plan *plan);
 int tt_batched_tune_cache(const char *path, int32_t save);
 
+/* One batched product C_b = alpha A_b B_b, b < batch, through the library's
+ * contraction kernels: the FP64 kernels for TT_FP64; for TT_MIXED_FP32 the
+ * SIMT kernel with FP32-rounded operands and FP32 accumulation; for
+ * TT_MIXED_TF32 / TT_MIXED_BF16 the tcgen05 tensor-core kernel, operands
+ * rounded to the format (as tt_precision states) and FP32 accumulation per
+ * K slice, slices summed in FP64; for TT_FP64_TC the FP64-accurate BF16
+ * tensor-core products where the size qualifies. No counterpart in the
+ * paper: it exposes the kernels of Eq. (3.6)'s contractions to
+ * product-level checks.
+ *   A  device, batch x M x K, row-major (leading dimension K)
+ *   B  device, batch x K x N, row-major (leading dimension N)
+ *   C  device, batch x M x N, row-major; written, never read; must not
+ *      overlap A or B
+ *   M, N, batch >= 0, K >= 1; M K, K N, M N < 2^31 (TT_ERR_SHAPE)
+ *   workspace  device, 256-byte aligned, tt_gemm_plan's size
+ * Enqueued on `stream`; FP64 products may be timed once per new shape
+ * (tt_gemm_autotune). */
+int tt_gemm_plan(int32_t precision, int64_t M, int64_t N, int64_t K, int64_t batch,
+                 size_t *workspace_bytes);
+int tt_gemm(int32_t precision, int64_t M, int64_t N, int64_t K, int64_t batch, const double *A,
+            const double *B, double *C, double alpha, void *workspace, size_t workspace_bytes,
+            void *stream);
+
 /* FP64 GEMM plan tuning, an implementation detail with no counterpart in the
  * paper. The first time a GEMM shape (sizes, batch, operand layout) runs on a
  * stream that is not being captured, the library times its model's best

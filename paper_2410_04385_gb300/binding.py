@@ -65,7 +65,8 @@ EXPORTS = ("tt_hadamard_recompress_plan", "tt_hadamard_recompress", "tt_round_pl
            "tt_hadamard_recompress_batch", "tt_scale", "tt_laplacian", "tt_lincomb",
            "tt_status_string", "tt_batched_plan_create", "tt_batched_plan_bind", "tt_batched_run",
            "tt_batched_status", "tt_batched_plan_info", "tt_batched_plan_destroy",
-           "tt_batched_tune_cache", "tt_device_status", "tt_batched_profile")
+           "tt_batched_tune_cache", "tt_device_status", "tt_batched_profile", "tt_gemm_plan",
+           "tt_gemm")
 
 
 def load(path: Optional[str] = None):
@@ -94,6 +95,10 @@ def load(path: Optional[str] = None):
                                      P(ctypes.c_int64), P(ctypes.c_size_t)]
     lib.tt_round_ex.argtypes = [P(TTStruct), ctypes.c_int64, ctypes.c_double, ctypes.c_int32,
                                 P(TTStruct), vp, ctypes.c_size_t, vp]
+    lib.tt_gemm_plan.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                 ctypes.c_int64, P(ctypes.c_size_t)]
+    lib.tt_gemm.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                            ctypes.c_int64, vp, vp, vp, ctypes.c_double, vp, ctypes.c_size_t, vp]
     lib.tt_dot_plan.argtypes = [P(TTStruct), P(TTStruct), P(ctypes.c_size_t)]
     lib.tt_dot.argtypes = [P(TTStruct), P(TTStruct), vp, vp, ctypes.c_size_t, vp]
     lib.tt_dot_noalloc.argtypes = [P(TTStruct), P(TTStruct), vp, vp]
@@ -139,6 +144,36 @@ def load(path: Optional[str] = None):
 def launch_count() -> int:
     """Kernels enqueued by libhatt in this process so far."""
     return int(load().tt_launch_count())
+
+
+def gemm(A: torch.Tensor, B: torch.Tensor, precision=0, alpha=1.0, stream=None) -> torch.Tensor:
+    """C = alpha A B through tt_gemm (A: [batch,] M x K, B: [batch,] K x N,
+    contiguous CUDA float64); precision as tt_precision. Returns C (allocated
+    here, with the workspace; enqueued on `stream`)."""
+    for t in (A, B):
+        if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+            raise ValueError("A and B must be contiguous CUDA float64 tensors")
+    squeeze = A.dim() == 2
+    A3 = A.unsqueeze(0) if squeeze else A
+    B3 = B.unsqueeze(0) if squeeze else B
+    if A3.dim() != 3 or B3.dim() != 3 or A3.shape[0] != B3.shape[0] or A3.shape[2] != B3.shape[1]:
+        raise ValueError("shapes do not chain")
+    nb, M, K = (int(v) for v in A3.shape)
+    N = int(B3.shape[2])
+    lib = load()
+    ws = ctypes.c_size_t()
+    _check("tt_gemm_plan", lib.tt_gemm_plan(int(precision), M, N, K, nb, ctypes.byref(ws)))
+    with torch.cuda.device(A.device):
+        work = torch.empty(max(int(ws.value), 1), dtype=torch.uint8, device=A.device)
+        C = torch.empty((nb, M, N), dtype=torch.float64, device=A.device)
+        _check("tt_gemm", lib.tt_gemm(int(precision), M, N, K, nb, ctypes.c_void_p(A3.data_ptr()),
+                                      ctypes.c_void_p(B3.data_ptr()), ctypes.c_void_p(C.data_ptr()),
+                                      float(alpha), ctypes.c_void_p(work.data_ptr()), int(ws.value),
+                                      _stream_ptr(stream)))
+        if stream is not None:
+            work.record_stream(stream)
+            C.record_stream(stream)
+    return C[0] if squeeze else C
 
 
 def tt_scale(x: torch.Tensor, divisor: torch.Tensor, stream=None) -> None:

@@ -1758,6 +1758,58 @@ int tt_device_status(int32_t *status) {
   return TT_OK;
 }
 
+// ------------------------------------------------------ one product ---
+namespace {
+struct NoBufs {};
+
+int gemm_args(int32_t precision, int64_t M, int64_t N, int64_t K, int64_t batch, hatt::Gemm &g) {
+  if (precision < TT_FP64 || precision > TT_FP64_TC) return TT_ERR_ARG;
+  if (M < 0 || N < 0 || K < 1 || batch < 0) return TT_ERR_ARG;
+  if (M > kIntMax || N > kIntMax || K > kIntMax || batch > kIntMax) return TT_ERR_SHAPE;
+  if (M * K > kIntMax || K * N > kIntMax || M * N > kIntMax) return TT_ERR_SHAPE;
+  g.M = (int)M;
+  g.N = (int)N;
+  g.K = (int)K;
+  g.batch = (int)batch;
+  g.bdiv = 1;
+  g.sA1 = M * K; g.sAm = K; g.sAk = 1;
+  g.sB1 = K * N; g.sBk = N; g.sBn = 1;
+  g.sC1 = M * N; g.sCm = N; g.sCn = 1;
+  g.prec = precision == TT_FP64_TC ? hatt::kPrecFP64 : precision;
+  return TT_OK;
+}
+}  // namespace
+
+int tt_gemm_plan(int32_t precision, int64_t M, int64_t N, int64_t K, int64_t batch,
+                 size_t *workspace_bytes) {
+  if (!workspace_bytes) return TT_ERR_ARG;
+  hatt::Gemm g;
+  const int st = gemm_args(precision, M, N, K, batch, g);
+  if (st != TT_OK) return st;
+  Fp64TcScope tc(precision == TT_FP64_TC);
+  *workspace_bytes = measure([&](Ws &) { return NoBufs{}; },
+                             [&](Runner &run, const NoBufs &) { run.gemm(g); });
+  return TT_OK;
+}
+
+int tt_gemm(int32_t precision, int64_t M, int64_t N, int64_t K, int64_t batch, const double *A,
+            const double *B, double *C, double alpha, void *workspace, size_t workspace_bytes,
+            void *stream) {
+  hatt::Gemm g;
+  const int st = gemm_args(precision, M, N, K, batch, g);
+  if (st != TT_OK) return st;
+  if (M == 0 || N == 0 || batch == 0) return TT_OK;
+  if (!A || !B || !C) return TT_ERR_ARG;
+  if (!workspace || !aligned(workspace)) return TT_ERR_WORKSPACE;
+  g.A = A;
+  g.B = B;
+  g.C = C;
+  g.alpha = alpha;
+  Fp64TcScope tc(precision == TT_FP64_TC);
+  return execute(workspace, workspace_bytes, (cudaStream_t)stream, [&](Ws &) { return NoBufs{}; },
+                 [&](Runner &run, const NoBufs &) { run.gemm(g); });
+}
+
 int tt_gemm_autotune(int32_t enable) {
   hatt::set_gemm_autotune(enable != 0);
   return TT_OK;

@@ -330,3 +330,18 @@ def test_plan_edge_shapes_every_variant(lib, n, Yr, Zr, variant, fixed):
     for k in range(1, d):
         left = int(np.prod(n[:k]))
         assert 1 <= bound[k] <= left
+
+
+def test_gemm_plan_arguments(lib):
+    """tt_gemm_plan (host only): a workspace for the tile counters and any
+    split-K scratch; unknown precision, K < 1, negative sizes and a null
+    output are refused with TT_ERR_ARG, sizes past 2^31 with TT_ERR_SHAPE."""
+    ws = ctypes.c_size_t()
+    for prec in range(5):
+        assert lib.tt_gemm_plan(prec, 300, 77, 4096, 1, ctypes.byref(ws)) == 0 and ws.value > 16384
+    assert lib.tt_gemm_plan(5, 4, 4, 4, 1, ctypes.byref(ws)) == 3
+    assert lib.tt_gemm_plan(-1, 4, 4, 4, 1, ctypes.byref(ws)) == 3
+    assert lib.tt_gemm_plan(0, 4, 4, 0, 1, ctypes.byref(ws)) == 3
+    assert lib.tt_gemm_plan(0, -4, 4, 4, 1, ctypes.byref(ws)) == 3
+    assert lib.tt_gemm_plan(0, 4, 4, 4, 1, None) == 3
+    assert lib.tt_gemm_plan(0, 1 << 20, 1 << 12, 4, 1, ctypes.byref(ws)) == 1
