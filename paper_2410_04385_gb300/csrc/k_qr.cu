@@ -80,6 +80,22 @@ __device__ __forceinline__ double rsqrt_scaled(double x) {
   return y;
 }
 
+// 1/x for x in [1e-30, 1e30] (a pivot pre-scaled by an even power of two):
+// an FP32 reciprocal seed (rcp.approx, relative error below 2^-22), then two
+// Newton-Raphson steps r <- r + r (1 - x r) in FP64, each two fused
+// multiply-adds (the error squares per step: 2^-22 -> 2^-44 -> FP64
+// rounding). Two dependent FP64 instructions fewer than rsqrt_scaled, and its
+// result is the multiplier 1/R_jj^2 the trailing update uses directly.
+__device__ __forceinline__ double rcp_scaled(double x) {
+  float f;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(f) : "f"((float)x));
+  double r = (double)f;
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+
 // Warp reduction of the three convergence statistics; lane 0 holds the
 // result. dev and dmax are maxima of non-negative doubles, taken on their bit
 // patterns (integer order equals numeric order there), which keeps them off
@@ -92,8 +108,11 @@ __device__ __forceinline__ void warp_stats(long long &dev, long long &dmax, doub
   }
 }
 
-// Pivot step of column j (thread 0 only): R_jj = sqrt(pivot) as y_j = 1/R_jj.
-// An exactly zero column of S (zero Gram diagonal) gets R_jj = 1, which
+// Pivot step of column j (thread 0 only): R_jj = sqrt(pivot), stored as
+// rinv2_j = 1/R_jj^2 = 1/pivot, the multiplier of the trailing update, and
+// the pivot itself; 1/R_jj is formed at publication, for all j at once and off
+// the column chain. An exactly zero column of S (zero Gram diagonal) gets
+// R_jj = 1, which
 // leaves Q_j = 0 and couples nothing; sending it to the shifted attempt
 // instead would make every pass shifted and leave ||Q^T Q - I|| at the shift
 // (~1e-11) on an otherwise benign S. A pivot not safely positive fails the
@@ -103,9 +122,10 @@ __device__ __forceinline__ void warp_stats(long long &dev, long long &dmax, doub
 // pivot above the failure floor is a normal FP32 number once scaled.
 __device__ __forceinline__ void chol_pivot(double *G, int ld, int j, const unsigned char *zero_col,
                                            double floor_piv, double shift, int attempt, double sc,
-                                           double unsc, double *rinv, unsigned char *fail) {
+                                           double *rinv2, double *pivots, unsigned char *fail) {
   if (zero_col[j]) {
-    rinv[j] = 1.0;
+    rinv2[j] = 1.0;
+    pivots[j] = 1.0;
     return;
   }
   double piv = G[j * ld + j];
@@ -114,8 +134,9 @@ __device__ __forceinline__ void chol_pivot(double *G, int ld, int j, const unsig
     else atomicOr(&g_qr_health, kHealthBreakdown);
     piv = fmax(shift, 1e-300);
   }
+  pivots[j] = piv;
   const double ps = piv * sc;
-  rinv[j] = (ps >= 1e-30 && ps <= 1e30) ? rsqrt_scaled(ps) * unsc : rsqrt_newton(piv);
+  rinv2[j] = (ps >= 1e-30 && ps <= 1e30) ? rcp_scaled(ps) * sc : 1.0 / piv;
 }
 
 // Flag words (reset at the start of every QR):
@@ -143,7 +164,8 @@ __device__ __forceinline__ void chol_factor(const double *Gg, double *Ut_g, doub
   double *G = sm;                                   // c x ld, upper triangle is updated
   __shared__ double s_red[3][kCholThreads / 32];
   __shared__ double s_diag_max, s_trace, s_dev, s_sc, s_unsc;
-  __shared__ double s_rinv[kMaxSmall];              // 1 / R_jj
+  __shared__ double s_rinv2[kMaxSmall];             // 1 / R_jj^2
+  __shared__ double s_piv[kMaxSmall];               // R_jj^2
   __shared__ unsigned char s_zero[kMaxSmall];       // column j of S is exactly zero
   __shared__ unsigned char s_failc[kMaxSmall];      // unshifted pivot j not safely positive
   const int tid = threadIdx.x;
@@ -259,7 +281,7 @@ __device__ __forceinline__ void chol_factor(const double *Gg, double *Ut_g, doub
     for (int j = tid; j < c; j += kCholThreads) s_failc[j] = 0;
     __syncthreads();
     const double floor_piv = (attempt == 0) ? (double)c * u * s_diag_max : 0.0;
-    if (tid == 0) chol_pivot(G, ld, 0, s_zero, floor_piv, shift, attempt, sc, unsc, s_rinv, s_failc);
+    if (tid == 0) chol_pivot(G, ld, 0, s_zero, floor_piv, shift, attempt, sc, s_rinv2, s_piv, s_failc);
     __syncthreads();
     bool failed = false;
     for (int j = 0; j < c; ++j) {
@@ -267,15 +289,14 @@ __device__ __forceinline__ void chol_factor(const double *Gg, double *Ut_g, doub
         failed = true;
         break;
       }
-      const double yj = s_rinv[j];
-      const double y2 = yj * yj;
+      const double y2 = s_rinv2[j];
       const double *rowj = G + j * ld;
       if (warp == 0 && j + 1 < c) {       // look-ahead: row j + 1, then its pivot
         const int i = j + 1;
         const double rji = rowj[i] * y2;
         for (int l = i + lane; l < c; l += 32) G[i * ld + l] = fma(-rji, rowj[l], G[i * ld + l]);
         __syncwarp();
-        if (lane == 0) chol_pivot(G, ld, i, s_zero, floor_piv, shift, attempt, sc, unsc, s_rinv, s_failc);
+        if (lane == 0) chol_pivot(G, ld, i, s_zero, floor_piv, shift, attempt, sc, s_rinv2, s_piv, s_failc);
       }
       // trailing update of the rows below by warps 1..7 on a 14 x 16 grid:
       // warp 0 carries the pivot chain and takes no share of it
@@ -297,11 +318,18 @@ __device__ __forceinline__ void chol_factor(const double *Gg, double *Ut_g, doub
   // kernel solves with them, so no serial triangular inverse is formed in
   // this single block
   for (int i = ty; i < c; i += 16) {
-    const double yi2 = s_rinv[i] * s_rinv[i];
+    const double yi2 = s_rinv2[i];
     for (int l = tx; l < c; l += 16)
       Ut_g[i * c + l] = (l > i) ? G[i * ld + l] * yi2 : (l == i ? 1.0 : 0.0);
   }
-  for (int i = tid; i < c; i += kCholThreads) y_g[i] = s_rinv[i];
+  for (int i = tid; i < c; i += kCholThreads) {
+    double yi = 1.0;                      // 1 / R_ii (1 for an exactly zero column)
+    if (!s_zero[i]) {
+      const double piv = s_piv[i], ps = piv * sc;
+      yi = (ps >= 1e-30 && ps <= 1e30) ? rsqrt_scaled(ps) * unsc : rsqrt_newton(piv);
+    }
+    y_g[i] = yi;
+  }
   // this pass applies; ||G - I||_max <= 0.1/c puts every eigenvalue of G in
   // [0.9, 1.1] (Gerschgorin): one more Cholesky QR pass orthonormalizes to
   // working accuracy, so this pass is the last one. Written last: the
