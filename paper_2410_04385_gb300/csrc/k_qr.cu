@@ -109,19 +109,20 @@ __device__ __forceinline__ void warp_stats(long long &dev, long long &dmax, doub
 }
 
 // Pivot step of column j (thread 0 only): R_jj = sqrt(pivot), stored as
-// rinv2_j = 1/R_jj^2 = 1/pivot, the multiplier of the trailing update, and
-// the pivot itself; 1/R_jj is formed at publication, for all j at once and off
-// the column chain. An exactly zero column of S (zero Gram diagonal) gets
-// R_jj = 1, which
-// leaves Q_j = 0 and couples nothing; sending it to the shifted attempt
+// rinv2_j = 1/pivot, the multiplier of the trailing update, and the pivot
+// itself; 1/R_jj is formed at publication, for all j at once and off the
+// column chain. An exactly zero column of S (zero Gram diagonal) gets R_jj = 1,
+// which leaves Q_j = 0 and couples nothing; sending it to the shifted attempt
 // instead would make every pass shifted and leave ||Q^T Q - I|| at the shift
 // (~1e-11) on an otherwise benign S. A pivot not safely positive fails the
 // unshifted attempt; in the shifted attempt it sets the breakdown bit and is
 // clamped so that nothing divides by zero.
-// sc = 2^-2k and unsc = 2^-k put the largest Gram diagonal near 1, so every
-// pivot above the failure floor is a normal FP32 number once scaled.
+// G is factorized scaled by sc = 2^-2k, which puts the largest Gram diagonal
+// near 1 (exact: a power of two), so every pivot above the failure floor is a
+// normal FP32 number and the chain carries no scaling; floor_piv and clamp
+// (the value a failed pivot takes) are scaled alike.
 __device__ __forceinline__ void chol_pivot(double *G, int ld, int j, const unsigned char *zero_col,
-                                           double floor_piv, double shift, int attempt, double sc,
+                                           double floor_piv, double clamp, int attempt,
                                            double *rinv2, double *pivots, unsigned char *fail) {
   if (zero_col[j]) {
     rinv2[j] = 1.0;
@@ -132,11 +133,10 @@ __device__ __forceinline__ void chol_pivot(double *G, int ld, int j, const unsig
   if (!(piv > floor_piv)) {
     if (attempt == 0) fail[j] = 1;
     else atomicOr(&g_qr_health, kHealthBreakdown);
-    piv = fmax(shift, 1e-300);
+    piv = clamp;
   }
   pivots[j] = piv;
-  const double ps = piv * sc;
-  rinv2[j] = (ps >= 1e-30 && ps <= 1e30) ? rcp_scaled(ps) * sc : 1.0 / piv;
+  rinv2[j] = (piv >= 1e-30 && piv <= 1e30) ? rcp_scaled(piv) : 1.0 / piv;
 }
 
 // Flag words (reset at the start of every QR):
@@ -164,8 +164,8 @@ __device__ __forceinline__ void chol_factor(const double *Gg, double *Ut_g, doub
   double *G = sm;                                   // c x ld, upper triangle is updated
   __shared__ double s_red[3][kCholThreads / 32];
   __shared__ double s_diag_max, s_trace, s_dev, s_sc, s_unsc;
-  __shared__ double s_rinv2[kMaxSmall];             // 1 / R_jj^2
-  __shared__ double s_piv[kMaxSmall];               // R_jj^2
+  __shared__ double s_rinv2[kMaxSmall];             // 1 / (sc R_jj^2)
+  __shared__ double s_piv[kMaxSmall];               // sc R_jj^2 (the scaled pivot)
   __shared__ unsigned char s_zero[kMaxSmall];       // column j of S is exactly zero
   __shared__ unsigned char s_failc[kMaxSmall];      // unshifted pivot j not safely positive
   const int tid = threadIdx.x;
@@ -262,6 +262,8 @@ __device__ __forceinline__ void chol_factor(const double *Gg, double *Ut_g, doub
     if (tid == 0) { flags[0] = 1; flags[1] = 1; }
     return;
   }
+  for (int i = ty; i < c; i += 16)         // the factorization runs on sc G
+    for (int j = tx; j < c; j += 16) G[i * ld + j] *= sc;
 
   // -- Cholesky: first unshifted, then shifted if a pivot is not safely positive.
   // A failed pivot of column j is recorded in s_failc[j] while column j - 1
@@ -274,14 +276,15 @@ __device__ __forceinline__ void chol_factor(const double *Gg, double *Ut_g, doub
       if (!(shift > 0.0)) shift = 1e-300;
       for (int e = tid; e < c * c; e += kCholThreads) {
         const int i = e / c, j = e % c;
-        G[i * ld + j] = __ldcg(Gg + e) + (i == j ? shift : 0.0);
+        G[i * ld + j] = (__ldcg(Gg + e) + (i == j ? shift : 0.0)) * sc;
       }
       if (tid == 0) flags[3] += 1;
     }
     for (int j = tid; j < c; j += kCholThreads) s_failc[j] = 0;
     __syncthreads();
-    const double floor_piv = (attempt == 0) ? (double)c * u * s_diag_max : 0.0;
-    if (tid == 0) chol_pivot(G, ld, 0, s_zero, floor_piv, shift, attempt, sc, s_rinv2, s_piv, s_failc);
+    const double floor_piv = (attempt == 0) ? (double)c * u * s_diag_max * sc : 0.0;
+    const double clamp = fmax(shift, 1e-300) * sc;
+    if (tid == 0) chol_pivot(G, ld, 0, s_zero, floor_piv, clamp, attempt, s_rinv2, s_piv, s_failc);
     __syncthreads();
     bool failed = false;
     for (int j = 0; j < c; ++j) {
@@ -296,7 +299,7 @@ __device__ __forceinline__ void chol_factor(const double *Gg, double *Ut_g, doub
         const double rji = rowj[i] * y2;
         for (int l = i + lane; l < c; l += 32) G[i * ld + l] = fma(-rji, rowj[l], G[i * ld + l]);
         __syncwarp();
-        if (lane == 0) chol_pivot(G, ld, i, s_zero, floor_piv, shift, attempt, sc, s_rinv2, s_piv, s_failc);
+        if (lane == 0) chol_pivot(G, ld, i, s_zero, floor_piv, clamp, attempt, s_rinv2, s_piv, s_failc);
       }
       // trailing update of the rows below by warps 1..7 on a 14 x 16 grid:
       // warp 0 carries the pivot chain and takes no share of it
@@ -314,7 +317,8 @@ __device__ __forceinline__ void chol_factor(const double *Gg, double *Ut_g, doub
   }
 
   // -- publish R = D U~ as the unit upper triangle U~ (U~_jl = R_jl / R_jj =
-  // G_jl y_j^2 with G the updated Gram row) and y_j = 1 / R_jj; the apply
+  // G_jl / G_jj with G the updated, scaled Gram row: the scale cancels) and
+  // y_j = 1 / R_jj; the apply
   // kernel solves with them, so no serial triangular inverse is formed in
   // this single block
   for (int i = ty; i < c; i += 16) {
@@ -324,9 +328,9 @@ __device__ __forceinline__ void chol_factor(const double *Gg, double *Ut_g, doub
   }
   for (int i = tid; i < c; i += kCholThreads) {
     double yi = 1.0;                      // 1 / R_ii (1 for an exactly zero column)
-    if (!s_zero[i]) {
-      const double piv = s_piv[i], ps = piv * sc;
-      yi = (ps >= 1e-30 && ps <= 1e30) ? rsqrt_scaled(ps) * unsc : rsqrt_newton(piv);
+    if (!s_zero[i]) {                     // the pivot is sc R_ii^2, sc = unsc^2
+      const double ps = s_piv[i];
+      yi = ((ps >= 1e-30 && ps <= 1e30) ? rsqrt_scaled(ps) : rsqrt_newton(ps)) * unsc;
     }
     y_g[i] = yi;
   }
@@ -446,6 +450,9 @@ trsm_rows_kernel(double *S, int m, int c, long long ldS, const double *Ut, const
 constexpr int kQrMaxBlocks = 160;       // >= the SMs of the device (152 on GB300)
 constexpr int kQrRowTile = 16;          // rows of S staged per Gram step
 constexpr int kQrMinRows = 4;           // rows per block at least (small m: fewer blocks)
+// Gram entries a thread owns at most: c <= 64 and c <= kMaxSmall (two
+// instantiations, so the common small case carries a quarter of the slots)
+constexpr int kQrSlots64 = (64 * 65 / 2 + kCholThreads - 1) / kCholThreads;
 constexpr int kQrMaxSlots = (kMaxSmall * (kMaxSmall + 1) / 2 + kCholThreads - 1) / kCholThreads;
 constexpr long long kQrSpinCap = 1LL << 21;   // polls of one barrier wait (seconds)
 
@@ -465,18 +472,20 @@ __device__ __forceinline__ void upper_index(int o, int c, int &i, int &j) {
 // as i << 8 | j); nqw = the most any lane of the warp has (lane 0's). Each
 // warp runs the multiply-adds of nqw slots by warp-uniform branches, as the
 // GEMM does (a predicated-off DFMA costs as much as a full one).
+template <int MAXQ>
 struct GramSlots {
-  int pk[kQrMaxSlots];
+  int pk[MAXQ];
   int nq, nqw;
 };
 
-__device__ __forceinline__ void gram_slots(int c, GramSlots &g) {
+template <int MAXQ>
+__device__ __forceinline__ void gram_slots(int c, GramSlots<MAXQ> &g) {
   const int tid = threadIdx.x;
   const int T = c * (c + 1) / 2;
   g.nq = max(0, (T - tid + kCholThreads - 1) / kCholThreads);
   g.nqw = __shfl_sync(0xffffffffu, g.nq, 0);
 #pragma unroll
-  for (int q = 0; q < kQrMaxSlots; ++q) {
+  for (int q = 0; q < MAXQ; ++q) {
     int i = 0, j = 0;
     if (q < g.nq) upper_index(tid + kCholThreads * q, c, i, j);
     g.pk[q] = (i << 8) | j;
@@ -486,12 +495,13 @@ __device__ __forceinline__ void gram_slots(int c, GramSlots &g) {
 // This block's share of the rows [r0, r1) of S, into mine (T entries); sm
 // holds kQrRowTile rows of S. S is read through L2 (another block of the
 // fused launch may have written it).
+template <int MAXQ>
 __device__ __forceinline__ void gram_share(const double *S, long long ldS, int c, int r0, int r1,
-                                           const GramSlots &g, double *mine, double *sm) {
+                                           const GramSlots<MAXQ> &g, double *mine, double *sm) {
   const int tid = threadIdx.x;
-  double acc[kQrMaxSlots];
+  double acc[MAXQ];
 #pragma unroll
-  for (int q = 0; q < kQrMaxSlots; ++q) acc[q] = 0.0;
+  for (int q = 0; q < MAXQ; ++q) acc[q] = 0.0;
   for (int rt = r0; rt < r1; rt += kQrRowTile) {
     const int rows = min(kQrRowTile, r1 - rt);
     for (int e = tid; e < rows * c; e += kCholThreads) {
@@ -500,7 +510,7 @@ __device__ __forceinline__ void gram_share(const double *S, long long ldS, int c
     }
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < kQrMaxSlots; ++q) {
+    for (int q = 0; q < MAXQ; ++q) {
       if (q < g.nqw) {
         const double *a = sm + (g.pk[q] >> 8), *b = sm + (g.pk[q] & 255);
         double v = acc[q];
@@ -512,7 +522,7 @@ __device__ __forceinline__ void gram_share(const double *S, long long ldS, int c
     __syncthreads();
   }
 #pragma unroll
-  for (int q = 0; q < kQrMaxSlots; ++q)
+  for (int q = 0; q < MAXQ; ++q)
     if (q < g.nq) mine[tid + kCholThreads * q] = acc[q];
 }
 
@@ -542,12 +552,13 @@ __device__ __forceinline__ void gram_entry(const double *part, int nb, int c, in
 
 // Launch per step: the shares (nb blocks), then their sum. Both do nothing
 // once the QR has converged.
+template <int MAXQ>
 __global__ void __launch_bounds__(kCholThreads)
 gram_share_kernel(const double *S, long long ldS, int m, int c, double *part, const int *flags) {
   pdl_enter();
   if (flags[0]) return;
   extern __shared__ double sm[];
-  GramSlots g;
+  GramSlots<MAXQ> g;
   gram_slots(c, g);
   const int per = (m + gridDim.x - 1) / gridDim.x;
   const int r0 = min(m, (int)blockIdx.x * per), r1 = min(m, r0 + per);
@@ -607,6 +618,7 @@ __device__ __forceinline__ bool grid_barrier(int *bar, int &epoch, long long spi
 //      pass.
 // The passes, G, tests and factorization are those of the launch-per-step
 // form, bit for bit.
+template <int MAXQ>
 __global__ void __launch_bounds__(kCholThreads, 1)
 qr_fused_kernel(double *S, int m, int c, long long ldS, double *G, double *Ut, double *y,
                 double *part, int *flags, long long spin_cap) {
@@ -618,7 +630,7 @@ qr_fused_kernel(double *S, int m, int c, long long ldS, double *G, double *Ut, d
   const int per = (m + nb - 1) / nb;
   const int r0 = min(m, bid * per), r1 = min(m, r0 + per);
   const int T = c * (c + 1) / 2;
-  GramSlots g;
+  GramSlots<MAXQ> g;
   gram_slots(c, g);
   int *bar = flags + 4;
   int epoch = 0;
@@ -730,8 +742,10 @@ cudaError_t qr_inplace(double *S, int m, int c, long long ldS, double *scratch, 
   const int nb = qr_blocks(m, sms);
   cudaError_t e = cudaMemsetAsync(flags, 0, 6 * sizeof(int), st);
   if (e != cudaSuccess) return e;
+  const bool small = c <= 64;               // the kQrSlots64 instantiations
   if (coop && programmatic_launch() && !force_qr_steps()) {
-    e = cudaFuncSetAttribute(qr_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    auto kernel = small ? qr_fused_kernel<kQrSlots64> : qr_fused_kernel<kQrMaxSlots>;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)chol_smem(kMaxSmall));
     if (e != cudaSuccess) return e;
     const size_t smem = std::max({chol_smem(c), trsm_smem(c), gram_smem(c)});
@@ -745,8 +759,7 @@ cudaError_t qr_inplace(double *S, int m, int c, long long ldS, double *scratch, 
     cfg.stream = st;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, qr_fused_kernel, S, m, c, ldS, G, Ut, y, part, flags,
-                           qr_spin_cap());
+    e = cudaLaunchKernelEx(&cfg, kernel, S, m, c, ldS, G, Ut, y, part, flags, qr_spin_cap());
     note_launch();
     return e;
   }
@@ -760,7 +773,8 @@ cudaError_t qr_inplace(double *S, int m, int c, long long ldS, double *scratch, 
   const int sum_blocks = std::max(1, std::min((T + 7) / 8, 2 * sms));
   const int blocks = std::max(1, std::min((m + kTrsmThreads / 32 - 1) / (kTrsmThreads / 32), 2 * sms));
   for (int p = 0; p < kPasses; ++p) {
-    launch_k(gram_share_kernel, nb, kCholThreads, gram_smem(c), st, S, ldS, m, c, part, flags);
+    launch_k(small ? gram_share_kernel<kQrSlots64> : gram_share_kernel<kQrMaxSlots>, nb,
+             kCholThreads, gram_smem(c), st, S, ldS, m, c, part, flags);
     note_launch();
     launch_k(gram_sum_kernel, sum_blocks, kCholThreads, 0, st, part, nb, c, G, flags);
     note_launch();
